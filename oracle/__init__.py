@@ -1,0 +1,243 @@
+"""FP64 CPU oracle of the Hermite-4 block-step integrator -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
+legs of ``bench.py`` may import this package.  The product path (the CUDA
+library behind ``include/gravidy.h`` and its Python binding) never calls it.
+
+The arithmetic lives in ``hermite_oracle.c`` (plain single-threaded C,
+compiled without FMA contraction); this module compiles it on first use with
+gcc and wraps it with ctypes.  Every function cites the part of GraviDy
+(arXiv 1702.00440) it follows in the C source.
+
+Conventions: positions/velocities/accelerations/jerks are ``float64`` arrays of
+shape ``(n, 3)``; times are integer ticks of ``dt_min``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hermite_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+CFLAGS = ["-O2", "-fno-fast-math", "-ffp-contract=off", "-fPIC", "-shared", "-std=c99"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``hermite_oracle.c`` into ``_build/liboracle.so`` (gcc)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        sig = {
+            "or_force": (None, [_I64, _P, _P, _P, _D, _I64, _P, _P, _P]),
+            "or_force_absnorm": (None, [_I64, _P, _P, _P, _D, _I64, _P, _P, _P]),
+            "or_energy": (None, [_I64, _P, _P, _P, _D, _P, _P]),
+            "or_active": (_I64, [_I64, _P, _P, _P]),
+            "or_predict_one": (None, [_P, _P, _P, _P, _D, _P, _P]),
+            "or_hermite_derivs": (None, [_P, _P, _P, _P, _D, _P, _P]),
+            "or_correct_one": (None, [_P, _P, _P, _P, _D, _P, _P]),
+            "or_aarseth_dt": (_D, [_P, _P, _P, _P, _D]),
+            "or_quantise_init": (_I64, [_D, _D, _I64]),
+            "or_quantise": (_I64, [_D, _I64, _I64, _D, _I64]),
+            "or_sim_new": (_P, [_I64, _P, _P, _P, _D, _D, _D, _D, _I64]),
+            "or_sim_free": (None, [_P]),
+            "or_sim_step": (_I64, [_P, _P, _P]),
+            "or_sim_replay": (None, [_P, _I64, _I64, _P]),
+            "or_sim_evolve": (_I64, [_P, _I64]),
+            "or_sim_energy": (None, [_P, _P, _P]),
+            "or_sim_get": (None, [_P, _P, _P, _P, _P, _P, _P]),
+            "or_sim_stats": (None, [_P, _P, _P, _P, _P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def force(m, x, v, eps, idx=None):
+    """Softened acceleration and jerk of particles ``idx`` (default: all)."""
+    lib = _load()
+    m = _f64(m)
+    n = m.shape[0]
+    x = _f64(x, (n, 3))
+    v = _f64(v, (n, 3))
+    idx = np.arange(n, dtype=np.int32) if idx is None else np.ascontiguousarray(idx, np.int32)
+    k = idx.shape[0]
+    acc = np.zeros((k, 3))
+    jrk = np.zeros((k, 3))
+    lib.or_force(n, _ptr(m), _ptr(x), _ptr(v), float(eps) ** 2, k, _ptr(idx), _ptr(acc), _ptr(jrk))
+    return acc, jrk
+
+
+def force_absnorm(m, x, v, eps, idx=None):
+    """Per-particle sums of term magnitudes (tolerance scales)."""
+    lib = _load()
+    m = _f64(m)
+    n = m.shape[0]
+    x = _f64(x, (n, 3))
+    v = _f64(v, (n, 3))
+    idx = np.arange(n, dtype=np.int32) if idx is None else np.ascontiguousarray(idx, np.int32)
+    k = idx.shape[0]
+    an = np.zeros(k)
+    jn = np.zeros(k)
+    lib.or_force_absnorm(n, _ptr(m), _ptr(x), _ptr(v), float(eps) ** 2, k, _ptr(idx), _ptr(an), _ptr(jn))
+    return an, jn
+
+
+def energy(m, x, v, eps):
+    """(K, U) with the softened potential."""
+    lib = _load()
+    m = _f64(m)
+    n = m.shape[0]
+    x = _f64(x, (n, 3))
+    v = _f64(v, (n, 3))
+    K = ctypes.c_double()
+    U = ctypes.c_double()
+    lib.or_energy(n, _ptr(m), _ptr(x), _ptr(v), float(eps) ** 2, ctypes.byref(K), ctypes.byref(U))
+    return K.value, U.value
+
+
+def active(tnext):
+    """(ascending active indices, t_next) for an int64 next-time array."""
+    lib = _load()
+    t = np.ascontiguousarray(tnext, dtype=np.int64)
+    idx = np.zeros(t.shape[0], np.int32)
+    tn = ctypes.c_int64()
+    c = lib.or_active(t.shape[0], _ptr(t), _ptr(idx), ctypes.byref(tn))
+    return idx[:c].copy(), tn.value
+
+
+def predict_one(x, v, a, j, dt):
+    lib = _load()
+    xp = np.zeros(3)
+    vp = np.zeros(3)
+    lib.or_predict_one(_ptr(_f64(x)), _ptr(_f64(v)), _ptr(_f64(a)), _ptr(_f64(j)), float(dt), _ptr(xp), _ptr(vp))
+    return xp, vp
+
+
+def hermite_derivs(a0, j0, a1, j1, dt):
+    lib = _load()
+    a2 = np.zeros(3)
+    a3 = np.zeros(3)
+    lib.or_hermite_derivs(_ptr(_f64(a0)), _ptr(_f64(j0)), _ptr(_f64(a1)), _ptr(_f64(j1)), float(dt), _ptr(a2), _ptr(a3))
+    return a2, a3
+
+
+def correct_one(xp, vp, a2, a3, dt):
+    lib = _load()
+    x1 = np.zeros(3)
+    v1 = np.zeros(3)
+    lib.or_correct_one(_ptr(_f64(xp)), _ptr(_f64(vp)), _ptr(_f64(a2)), _ptr(_f64(a3)), float(dt), _ptr(x1), _ptr(v1))
+    return x1, v1
+
+
+def aarseth_dt(a1, j1, a2e, a3e, eta):
+    lib = _load()
+    return lib.or_aarseth_dt(_ptr(_f64(a1)), _ptr(_f64(j1)), _ptr(_f64(a2e)), _ptr(_f64(a3e)), float(eta))
+
+
+def quantise_init(dt, dt_min, dtau_max):
+    return _load().or_quantise_init(float(dt), float(dt_min), int(dtau_max))
+
+
+def quantise(dt_new, dtau_old, tick_now, dt_min, dtau_max):
+    return _load().or_quantise(float(dt_new), int(dtau_old), int(tick_now), float(dt_min), int(dtau_max))
+
+
+class Sim:
+    """The oracle integrator (GraviDy Sec. 2.4 steps 1-7)."""
+
+    def __init__(self, m, x, v, eps, eta, dt_min=2.0 ** -22, dt_max=0.125, fixed_dtau=0):
+        self._lib = _load()
+        m = _f64(m)
+        self.n = n = m.shape[0]
+        self.dt_min = float(dt_min)
+        self.dt_max = float(dt_max)
+        x = _f64(x, (n, 3))
+        v = _f64(v, (n, 3))
+        h = self._lib.or_sim_new(n, _ptr(m), _ptr(x), _ptr(v), float(eps), float(eta), self.dt_min, self.dt_max, int(fixed_dtau))
+        if not h:
+            raise ValueError("oracle rejected the arguments")
+        self._h = ctypes.c_void_p(h)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.or_sim_free(h)
+            self._h = None
+
+    def step(self):
+        """One free-running block step -> (tick, ascending active indices)."""
+        idx = np.zeros(self.n, np.int32)
+        t = ctypes.c_int64()
+        c = self._lib.or_sim_step(self._h, ctypes.byref(t), _ptr(idx))
+        return t.value, idx[:c].copy()
+
+    def replay(self, tick, idx):
+        idx = np.ascontiguousarray(idx, np.int32)
+        self._lib.or_sim_replay(self._h, int(tick), idx.shape[0], _ptr(idx))
+
+    def evolve_ticks(self, tick_end):
+        return self._lib.or_sim_evolve(self._h, int(tick_end))
+
+    def evolve(self, t_end):
+        return self.evolve_ticks(int(round(t_end / self.dt_min)))
+
+    def energy(self):
+        K = ctypes.c_double()
+        U = ctypes.c_double()
+        self._lib.or_sim_energy(self._h, ctypes.byref(K), ctypes.byref(U))
+        return K.value, U.value
+
+    def state(self):
+        n = self.n
+        x, v, a, j = (np.zeros((n, 3)) for _ in range(4))
+        tau = np.zeros(n, np.int64)
+        dtau = np.zeros(n, np.int64)
+        self._lib.or_sim_get(self._h, _ptr(x), _ptr(v), _ptr(a), _ptr(j), _ptr(tau), _ptr(dtau))
+        return dict(x=x, v=v, a=a, j=j, tau=tau, dtau=dtau)
+
+    def stats(self):
+        t = ctypes.c_int64()
+        nb = ctypes.c_int64()
+        ns = ctypes.c_int64()
+        it = ctypes.c_double()
+        self._lib.or_sim_stats(self._h, ctypes.byref(t), ctypes.byref(nb), ctypes.byref(ns), ctypes.byref(it))
+        return dict(tick=t.value, nblock=nb.value, nsteps=ns.value, interactions=it.value)
