@@ -1,0 +1,161 @@
+/*
+ * gravidy.h -- C ABI of the GB300 Hermite-4 block-time-step N-body library
+ * (libgravidy_gb300.so).
+ *
+ * The library integrates the Newtonian N-body problem with Plummer softening
+ * (GraviDy, arXiv 1702.00440, Sec. 2.1 Eq. 1 and its softened form in
+ * Sec. 2.4) by the 4th-order Hermite predictor-corrector (Sec. 2.1) with
+ * power-of-two block time steps (Sec. 2.4) and Aarseth's time-step criterion
+ * with parameter eta (Sec. 3.2).  One block step follows Sec. 2.4 steps 5-7:
+ * find the active particles, predict all N particles, compute the force and
+ * jerk of the active ones against all N predicted ones (the O(N_act N) part,
+ * Sec. 2.5), correct the active particles and give them new steps.  Every
+ * step runs on the GPU; the host only launches work and reads results.
+ *
+ * Conventions
+ *   - G = 1.  Units are whatever the caller uses (N-body units in the tests).
+ *   - Host arrays at this boundary are AoS: x, v, a, jerk are n*3 doubles
+ *     (x0 y0 z0 x1 y1 z1 ...); m is n doubles.  Inside, the library keeps
+ *     structure-of-arrays copies on the device.
+ *   - Time is kept as integer ticks of dt_min (a power of two): a particle's
+ *     time is tau * dt_min and its step dtau * dt_min, dtau a power of two.
+ *   - Ownership: the caller owns every host array; the library copies in and
+ *     out and never keeps a caller pointer.  gd_ctx owns all device memory.
+ *   - Errors: every int-returning call returns GD_OK (0) or a negative
+ *     gd_status; gd_last_error() gives a message.  Faults found on the device
+ *     (a non-finite value, a bounded wait that ran out) are recorded in a
+ *     device flag and returned by the next call that synchronises.
+ *   - Threading: a gd_ctx is not thread-safe; distinct contexts are
+ *     independent.
+ */
+#ifndef GRAVIDY_H
+#define GRAVIDY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gd_status {
+    GD_OK = 0,
+    GD_EINVAL = -1,      /* bad argument */
+    GD_ENOMEM = -2,      /* device or host allocation failed */
+    GD_ECUDA = -3,       /* a CUDA runtime call failed */
+    GD_ENONFINITE = -4,  /* a corrected state or step was NaN/Inf */
+    GD_ETIMEOUT = -5,    /* a bounded device-side wait gave up */
+    GD_ESTATE = -6       /* call not valid in the current state */
+} gd_status;
+
+typedef enum gd_precision {
+    /* all pair arithmetic in FP64 */
+    GD_FP64 = 0,
+    /* pair arithmetic in FP32 on double-single (hi+lo float) positions, sums
+     * folded into FP64; prediction, correction, steps and energy in FP64
+     * (the mixed-precision alternative of Sec. 2.3) */
+    GD_MIXED = 1
+} gd_precision;
+
+typedef struct gd_opts {
+    double dt_min;      /* smallest block step, a power of two (default 2^-22) */
+    double dt_max;      /* largest block step, a power of two >= dt_min (default 1/8) */
+    int32_t precision;  /* gd_precision (default GD_MIXED) */
+    int32_t device;     /* CUDA device ordinal (default 0) */
+    void *stream;       /* cudaStream_t to run on; NULL = a stream owned by the context */
+    int32_t use_graph;  /* 1 = run gd_evolve through a captured CUDA graph (default 1) */
+    int32_t graph_steps;/* block steps per graph launch, a multiple of 1..64 (default 16) */
+    int32_t jsplit;     /* > 0 forces the j-split factor of the force kernel; 0 = tuned */
+    int32_t mode_cut;   /* active count at/above which the i-parallel force mode is used;
+                           0 = tuned default */
+    int32_t time_force; /* 1 = record CUDA events around every force launch (gd_kernel_time) */
+} gd_opts;
+
+typedef struct gd_stats {
+    int64_t tick;          /* time of the last block step, in ticks */
+    int64_t block_steps;   /* block steps taken (Sec. 2.4 "Iter") */
+    int64_t particle_steps;/* sum of N_act over block steps ("Nsteps") */
+    double interactions;   /* sum of N_act * N over all force evaluations */
+    int64_t last_nact;     /* N_act of the last block step */
+} gd_stats;
+
+typedef struct gd_ctx gd_ctx;
+
+/* Fill *o with the defaults listed in gd_opts. */
+void gd_opts_default(gd_opts *o);
+
+/* Sec. 2.4 steps 1-4: allocate the device store, copy m, x, v in, compute the
+ * initial force and jerk of all n particles (O(n^2)) and the first block step
+ * of each, dt = eta |a| / |jerk| rounded down to a power of two in
+ * [dt_min, dt_max].  eps is the Plummer softening length (>= 0; eps = 0 gives
+ * the unsoftened Eq. 1 with the self term excluded), eta > 0.  opt may be
+ * NULL for the defaults.  On success *out is a new context (time 0). */
+int gd_init(gd_ctx **out, int64_t n, const double *m, const double *x, const double *v,
+            double eps, double eta, const gd_opts *opt);
+
+/* Advance by block steps (Sec. 2.4 steps 5-7) until no particle's next time
+ * is <= t_end.  With t_end a multiple of dt_max every particle ends exactly
+ * at t_end (synchronised).  t_end must not be below the current time. */
+int gd_evolve(gd_ctx *c, double t_end);
+
+/* One block step; *t_out (nullable) receives its time and *nact_out
+ * (nullable) its number of active particles. */
+int gd_step_block(gd_ctx *c, double *t_out, int64_t *nact_out);
+
+/* Kinetic and potential energy (Sec. 2.1 Eq. 2, with the potential softened
+ * like the force: -sum_{i<j} m_i m_j / sqrt(r_ij^2 + eps^2)) at the time of
+ * the last block step; particles behind it are predicted to it first. The
+ * pair sums run in FP64 in both precisions. */
+int gd_energy(gd_ctx *c, double *K, double *U);
+
+/* Copy the state out: x, v, a, jerk as n*3 AoS doubles (each particle at its
+ * own time), tau and dtau as n int64 ticks.  Any pointer may be NULL. */
+int gd_get_state(gd_ctx *c, double *x, double *v, double *a, double *jerk, int64_t *tau,
+                 int64_t *dtau);
+
+/* Replace the state (checkpoint restart); same layouts as gd_get_state.  All
+ * pointers are required.  Every dtau must be a power of two in
+ * [1, dt_max/dt_min] and every tau a non-negative multiple of its dtau. */
+int gd_set_state(gd_ctx *c, const double *x, const double *v, const double *a,
+                 const double *jerk, const int64_t *tau, const int64_t *dtau);
+
+/* Counters since gd_init. */
+int gd_get_stats(gd_ctx *c, gd_stats *s);
+
+/* Average device time of the force launches recorded since the last call
+ * (needs opts.time_force = 1): *ms_total, *launches. */
+int gd_kernel_time(gd_ctx *c, double *ms_total, int64_t *launches);
+
+void gd_free(gd_ctx *c);
+
+/* Message of the last error on c (or of the last failed gd_init if c is NULL). */
+const char *gd_last_error(const gd_ctx *c);
+
+/* ---- hooks for tests and measurement (no integration state changes) ---- */
+
+/* Force and jerk (Sec. 2.4, softened Eq. 1 and its time derivative) of the
+ * nact particles idx[] (host int32, each in [0, n), duplicates allowed)
+ * against all n particles predicted to tick; acc and jerk are nact*3 host
+ * doubles in the order of idx.  State is unchanged. */
+int gd_force(gd_ctx *c, int64_t tick, const int32_t *idx, int64_t nact, double *acc,
+             double *jerk);
+
+/* Positions and velocities of all n particles predicted to tick (Sec. 2.4
+ * step 7a), n*3 AoS doubles each; either pointer may be NULL. */
+int gd_predict(gd_ctx *c, int64_t tick, double *xp, double *vp);
+
+/* The active set of the next block step (Sec. 2.4 step 5) without taking it:
+ * idx (host, n int32) receives the active indices in ascending order,
+ * *nact their count, *tick_next the block time. */
+int gd_active(gd_ctx *c, int32_t *idx, int64_t *nact, int64_t *tick_next);
+
+/* One block step with a given block time and active list (host int32,
+ * ascending, distinct, each particle's next time must not be before
+ * tick_next): used to replay another integrator's schedule.  The new steps
+ * are computed and stored as usual but the block times come from the caller. */
+int gd_replay_step(gd_ctx *c, int64_t tick_next, const int32_t *idx, int64_t nact);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRAVIDY_H */

@@ -1,0 +1,300 @@
+"""ctypes binding of libgravidy_gb300.so (C ABI in include/gravidy.h).
+
+Argument marshalling only: every step of the integration runs in the CUDA
+kernels behind the ABI.  The module-level functions carry the C names
+(gd_init, gd_evolve, gd_step_block, gd_energy, gd_get_state, ...);
+``Integrator`` wraps a context with the same operations.  Host arrays are numpy
+float64 of shape (n, 3) for vectors and (n,) for masses; times are ticks of
+dt_min for the hooks.  A missing or unloadable library raises -- there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+GD_OK, GD_EINVAL, GD_ENOMEM, GD_ECUDA, GD_ENONFINITE, GD_ETIMEOUT, GD_ESTATE = 0, -1, -2, -3, -4, -5, -6
+GD_FP64, GD_MIXED = 0, 1
+_PRECISION = {"fp64": GD_FP64, "mixed": GD_MIXED, GD_FP64: GD_FP64, GD_MIXED: GD_MIXED}
+
+# every entry point the header declares
+EXPORTS = (
+    "gd_opts_default", "gd_init", "gd_evolve", "gd_step_block", "gd_energy", "gd_get_state",
+    "gd_set_state", "gd_get_stats", "gd_kernel_time", "gd_free", "gd_last_error", "gd_force",
+    "gd_predict", "gd_active", "gd_replay_step",
+)
+
+
+class GravidyError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (status %d)" % (msg, code))
+        self.code = code
+
+
+class gd_opts(ctypes.Structure):
+    _fields_ = [
+        ("dt_min", ctypes.c_double),
+        ("dt_max", ctypes.c_double),
+        ("precision", ctypes.c_int32),
+        ("device", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+        ("use_graph", ctypes.c_int32),
+        ("graph_steps", ctypes.c_int32),
+        ("jsplit", ctypes.c_int32),
+        ("mode_cut", ctypes.c_int32),
+        ("time_force", ctypes.c_int32),
+    ]
+
+
+class gd_stats(ctypes.Structure):
+    _fields_ = [
+        ("tick", ctypes.c_int64),
+        ("block_steps", ctypes.c_int64),
+        ("particle_steps", ctypes.c_int64),
+        ("interactions", ctypes.c_double),
+        ("last_nact", ctypes.c_int64),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load the CUDA library (building it first when allowed).  Raises if it
+    cannot be loaded."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise GravidyError(GD_ESTATE, "libgravidy_gb300.so is not built (%s)" % _build.LIB)
+        lib = ctypes.CDLL(_build.LIB)
+        P, I64, D, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int32
+        sig = {
+            "gd_opts_default": (None, [P]),
+            "gd_init": (ctypes.c_int, [P, I64, P, P, P, D, D, P]),
+            "gd_evolve": (ctypes.c_int, [P, D]),
+            "gd_step_block": (ctypes.c_int, [P, P, P]),
+            "gd_energy": (ctypes.c_int, [P, P, P]),
+            "gd_get_state": (ctypes.c_int, [P, P, P, P, P, P, P]),
+            "gd_set_state": (ctypes.c_int, [P, P, P, P, P, P, P]),
+            "gd_get_stats": (ctypes.c_int, [P, P]),
+            "gd_kernel_time": (ctypes.c_int, [P, P, P]),
+            "gd_free": (None, [P]),
+            "gd_last_error": (ctypes.c_char_p, [P]),
+            "gd_force": (ctypes.c_int, [P, I64, P, I64, P, P]),
+            "gd_predict": (ctypes.c_int, [P, I64, P, P]),
+            "gd_active": (ctypes.c_int, [P, P, P, P]),
+            "gd_replay_step": (ctypes.c_int, [P, I64, P, I64]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _f64(a, shape):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(shape))
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc, ctx=None):
+    if rc != GD_OK:
+        msg = load().gd_last_error(ctx)
+        raise GravidyError(rc, msg.decode() if msg else "error")
+
+
+def make_opts(dt_min=2.0 ** -22, dt_max=0.125, precision="mixed", device=0, stream=None, use_graph=True,
+              graph_steps=16, jsplit=0, mode_cut=0, time_force=False):
+    o = gd_opts()
+    load().gd_opts_default(ctypes.byref(o))
+    o.dt_min = float(dt_min)
+    o.dt_max = float(dt_max)
+    o.precision = _PRECISION[precision]
+    o.device = int(device)
+    o.stream = stream
+    o.use_graph = 1 if use_graph else 0
+    o.graph_steps = int(graph_steps)
+    o.jsplit = int(jsplit)
+    o.mode_cut = int(mode_cut)
+    o.time_force = 1 if time_force else 0
+    return o
+
+
+# ---- module-level functions with the C names -------------------------------
+
+def gd_init(m, x, v, eps, eta, **opts):
+    lib = load()
+    m = np.ascontiguousarray(np.asarray(m, dtype=np.float64))
+    n = m.shape[0]
+    x = _f64(x, (n, 3))
+    v = _f64(v, (n, 3))
+    o = make_opts(**opts)
+    h = ctypes.c_void_p()
+    _check(lib.gd_init(ctypes.byref(h), n, _p(m), _p(x), _p(v), float(eps), float(eta), ctypes.byref(o)))
+    return h
+
+
+def gd_evolve(ctx, t_end):
+    _check(load().gd_evolve(ctx, float(t_end)), ctx)
+
+
+def gd_step_block(ctx):
+    t = ctypes.c_double()
+    k = ctypes.c_int64()
+    _check(load().gd_step_block(ctx, ctypes.byref(t), ctypes.byref(k)), ctx)
+    return t.value, k.value
+
+
+def gd_energy(ctx):
+    K = ctypes.c_double()
+    U = ctypes.c_double()
+    _check(load().gd_energy(ctx, ctypes.byref(K), ctypes.byref(U)), ctx)
+    return K.value, U.value
+
+
+def gd_get_state(ctx, n, out=None):
+    """dict of x, v, a, j (n, 3) and tau, dtau (n,) int64; ``out`` may supply
+    preallocated (e.g. pinned) arrays with those keys."""
+    o = out if out is not None else {}
+    for k in ("x", "v", "a", "j"):
+        if k not in o:
+            o[k] = np.empty((n, 3))
+    for k in ("tau", "dtau"):
+        if k not in o:
+            o[k] = np.empty(n, np.int64)
+    _check(load().gd_get_state(ctx, _p(o["x"]), _p(o["v"]), _p(o["a"]), _p(o["j"]), _p(o["tau"]), _p(o["dtau"])), ctx)
+    return o
+
+
+def gd_set_state(ctx, n, x, v, a, j, tau, dtau):
+    x, v, a, j = (_f64(q, (n, 3)) for q in (x, v, a, j))
+    tau = np.ascontiguousarray(tau, dtype=np.int64)
+    dtau = np.ascontiguousarray(dtau, dtype=np.int64)
+    _check(load().gd_set_state(ctx, _p(x), _p(v), _p(a), _p(j), _p(tau), _p(dtau)), ctx)
+
+
+def gd_get_stats(ctx):
+    s = gd_stats()
+    _check(load().gd_get_stats(ctx, ctypes.byref(s)), ctx)
+    return dict(tick=s.tick, block_steps=s.block_steps, particle_steps=s.particle_steps,
+                interactions=s.interactions, last_nact=s.last_nact)
+
+
+def gd_kernel_time(ctx):
+    ms = ctypes.c_double()
+    k = ctypes.c_int64()
+    _check(load().gd_kernel_time(ctx, ctypes.byref(ms), ctypes.byref(k)), ctx)
+    return ms.value, k.value
+
+
+def gd_free(ctx):
+    if ctx is not None and ctx.value:
+        load().gd_free(ctx)
+
+
+def gd_force(ctx, tick, idx):
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    k = idx.shape[0]
+    acc = np.empty((k, 3))
+    jrk = np.empty((k, 3))
+    _check(load().gd_force(ctx, int(tick), _p(idx), k, _p(acc), _p(jrk)), ctx)
+    return acc, jrk
+
+
+def gd_predict(ctx, n, tick):
+    xp = np.empty((n, 3))
+    vp = np.empty((n, 3))
+    _check(load().gd_predict(ctx, int(tick), _p(xp), _p(vp)), ctx)
+    return xp, vp
+
+
+def gd_active(ctx, n):
+    idx = np.empty(n, np.int32)
+    k = ctypes.c_int64()
+    t = ctypes.c_int64()
+    _check(load().gd_active(ctx, _p(idx), ctypes.byref(k), ctypes.byref(t)), ctx)
+    return idx[: k.value].copy(), t.value
+
+
+def gd_replay_step(ctx, tick, idx):
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    _check(load().gd_replay_step(ctx, int(tick), _p(idx), idx.shape[0]), ctx)
+
+
+class Integrator:
+    """One gd_ctx: the GPU Hermite-4 block-step integrator."""
+
+    def __init__(self, m, x, v, eps, eta, **opts):
+        self.n = int(np.asarray(m).shape[0])
+        self.dt_min = float(opts.get("dt_min", 2.0 ** -22))
+        self.dt_max = float(opts.get("dt_max", 0.125))
+        self._h = gd_init(m, x, v, eps, eta, **opts)
+
+    def close(self):
+        h, self._h = getattr(self, "_h", None), None
+        if h is not None:
+            gd_free(h)
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def evolve(self, t_end):
+        gd_evolve(self._h, t_end)
+
+    def step_block(self):
+        return gd_step_block(self._h)
+
+    def energy(self):
+        return gd_energy(self._h)
+
+    def state(self, out=None):
+        return gd_get_state(self._h, self.n, out)
+
+    def set_state(self, x, v, a, j, tau, dtau):
+        gd_set_state(self._h, self.n, x, v, a, j, tau, dtau)
+
+    def stats(self):
+        return gd_get_stats(self._h)
+
+    def kernel_time(self):
+        return gd_kernel_time(self._h)
+
+    def force(self, tick, idx):
+        return gd_force(self._h, tick, idx)
+
+    def predict(self, tick):
+        return gd_predict(self._h, self.n, tick)
+
+    def active(self):
+        return gd_active(self._h, self.n)
+
+    def replay_step(self, tick, idx):
+        gd_replay_step(self._h, tick, idx)

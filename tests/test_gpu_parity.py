@@ -1,0 +1,306 @@
+"""GPU path vs the FP64 oracle, through the C ABI (ctypes binding).
+
+Tolerances:
+  FP64 path   per-particle |a_gpu - a_oracle| / |a| <= 1e-12 (force/jerk), plus a
+              round-off bound scaled by the sum of term magnitudes.
+  mixed path  FP32 pair arithmetic on double-single positions, FP32 sums over at
+              most 128 consecutive terms folded into FP64.  One term carries about
+              8 units of 2^-24 (difference, r^2, rsqrt.approx, three products); the
+              per-tile FP32 sum adds up to 128 units in the worst case, so
+              |a_gpu - a_oracle|_component <= 2^-24 * 160 * sum_j |term_j|  (~1e-5),
+              and the per-particle relative error's median is held to <= 1e-6.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1702_00440_gb300 import gravidy, inputs
+
+pytestmark = pytest.mark.gpu
+
+EPS = 1e-4
+ETA = 0.01
+DT_MIN = 2.0 ** -22
+U32 = 2.0 ** -24
+MIXED_TERM_BOUND = 160 * U32
+FP64_TERM_BOUND = 64 * 2.0 ** -53
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    gravidy.load()
+    oracle.build()
+
+
+def _check_force(prec, m, x, v, eps, idx, tick_state=None, label=""):
+    n = m.shape[0]
+    with gravidy.Integrator(m, x, v, eps, ETA, precision=prec) as g:
+        a, j = g.force(0, idx)
+    a_or, j_or = oracle.force(m, x, v, eps, idx)
+    an, jn = oracle.force_absnorm(m, x, v, eps, idx)
+    bound = MIXED_TERM_BOUND if prec == "mixed" else FP64_TERM_BOUND
+    ra = np.abs(a - a_or).max(axis=1) / an
+    rj = np.abs(j - j_or).max(axis=1) / jn
+    rel_a = np.linalg.norm(a - a_or, axis=1) / np.linalg.norm(a_or, axis=1)
+    rel_j = np.linalg.norm(j - j_or, axis=1) / np.linalg.norm(j_or, axis=1)
+    print("%s %s n=%d nact=%d: max|da|/sum|a_j| %.2e max|dj|/sum|j_j| %.2e  rel a med %.2e p99 %.2e max %.2e"
+          "  rel j med %.2e p99 %.2e max %.2e" % (label, prec, n, idx.size, ra.max(), rj.max(), np.median(rel_a),
+                                                np.percentile(rel_a, 99), rel_a.max(), np.median(rel_j),
+                                                np.percentile(rel_j, 99), rel_j.max()))
+    assert ra.max() <= bound
+    assert rj.max() <= bound
+    if prec == "fp64":
+        assert np.median(rel_a) <= 1e-12 and np.median(rel_j) <= 1e-12
+        assert np.percentile(rel_a, 99) <= 1e-12
+    else:
+        assert np.median(rel_a) <= 1e-6 and np.median(rel_j) <= 1e-6
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("n", [1, 2, 3, 127, 512, 1000, 3001])
+def test_force_all_active(prec, n):
+    m, x, v = inputs.plummer(n, seed=n)
+    if n < 3:
+        x = x + np.arange(3 * n).reshape(n, 3) * 0.1  # distinct points
+    idx = np.arange(n, dtype=np.int32)
+    if n == 1:
+        with gravidy.Integrator(m, x, v, EPS, ETA, precision=prec) as g:
+            a, j = g.force(0, idx)
+        assert np.array_equal(a, np.zeros((1, 3))) and np.array_equal(j, np.zeros((1, 3)))
+        return
+    _check_force(prec, m, x, v, EPS, idx, label="all")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("nact", [1, 5, 32, 33, 191, 192, 257, 700])
+def test_force_subsets_split(prec, nact):
+    """Small active sets take the warp mode and a j-split; larger ones the
+    i-parallel mode; ragged N spans several j-tiles and a padded tail."""
+    n = 5000
+    m, x, v = inputs.plummer(n, seed=7, masses=inputs.power_law_masses(n, seed=7))
+    idx = inputs.random_subset(n, nact, seed=nact)
+    _check_force(prec, m, x, v, EPS, idx, label="subset")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_force_unsoftened(prec):
+    m, x, v = inputs.plummer(700, seed=3)
+    idx = np.arange(700, dtype=np.int32)
+    _check_force(prec, m, x, v, 0.0, idx, label="eps0")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_force_duplicates_and_order(prec):
+    m, x, v = inputs.plummer(300, seed=5)
+    idx = np.array([7, 3, 3, 299, 0, 7], dtype=np.int32)
+    with gravidy.Integrator(m, x, v, EPS, ETA, precision=prec) as g:
+        a, j = g.force(0, idx)
+    assert np.array_equal(a[1], a[2]) and np.array_equal(a[0], a[5])
+    a_or, _ = oracle.force(m, x, v, EPS, idx)
+    np.testing.assert_allclose(a, a_or, rtol=1e-5)
+
+
+def _random_state(n, seed):
+    rng = np.random.default_rng(seed)
+    m, x, v = inputs.plummer(n, seed=seed)
+    a = rng.normal(size=(n, 3))
+    j = rng.normal(size=(n, 3)) * 3
+    dtau = 2 ** rng.integers(0, 8, size=n).astype(np.int64) * 64
+    tau = (rng.integers(0, 40, size=n).astype(np.int64) * dtau)
+    return m, x, v, a, j, tau, dtau
+
+
+def test_predictor_matches_oracle():
+    n = 1537
+    m, x, v, a, j, tau, dtau = _random_state(n, 3)
+    tick = int((tau + dtau).max())
+    with gravidy.Integrator(m, x, v, EPS, ETA, precision="fp64") as g:
+        g.set_state(x, v, a, j, tau, dtau)
+        xp, vp = g.predict(tick)
+    for i in range(n):
+        dt = (tick - tau[i]) * DT_MIN
+        xo, vo = oracle.predict_one(x[i], v[i], a[i], j[i], dt)
+        scale = np.abs(x[i]) + np.abs(v[i] * dt) + np.abs(a[i]) * dt * dt + np.abs(j[i]) * dt ** 3
+        assert np.all(np.abs(xp[i] - xo) <= 8 * 2.0 ** -53 * scale)
+        assert np.all(np.abs(vp[i] - vo) <= 8 * 2.0 ** -53 * (np.abs(v[i]) + np.abs(a[i]) * dt + np.abs(j[i]) * dt * dt))
+
+
+@pytest.mark.parametrize("n", [1, 31, 128, 129, 4097, 300001])
+@pytest.mark.parametrize("pattern", ["random", "all", "first", "last", "sparse"])
+def test_active_list_bit_exact(n, pattern):
+    rng = np.random.default_rng(n)
+    m, x, v = inputs.plummer(n, seed=2)
+    a = np.zeros((n, 3))
+    jk = np.zeros((n, 3))
+    if pattern == "all":
+        dtau = np.full(n, 256, np.int64)
+        tau = np.zeros(n, np.int64)
+    else:
+        dtau = 2 ** rng.integers(3, 9, size=n).astype(np.int64)
+        tau = rng.integers(1, 6, size=n).astype(np.int64) * 256
+        if pattern == "first":
+            tau[:] = 2048
+            dtau[:] = 256
+            tau[0] = 1792
+        elif pattern == "last":
+            tau[:] = 2048
+            dtau[:] = 256
+            tau[-1] = 1792
+        elif pattern == "sparse":
+            tau[:] = 2048
+            dtau[:] = 256
+            pick = rng.choice(n, size=max(1, n // 1000), replace=False)
+            tau[pick] = 1792
+    with gravidy.Integrator(m, x, v, EPS, ETA, precision="mixed") as g:
+        g.set_state(x, v, a, jk, tau, dtau)
+        idx, tick = g.active()
+    want, wt = oracle.active(tau + dtau)
+    assert tick == wt
+    assert np.array_equal(idx, want)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_energy_matches_oracle(prec):
+    m, x, v = inputs.plummer(3001, seed=4)
+    with gravidy.Integrator(m, x, v, EPS, ETA, precision=prec) as g:
+        K, U = g.energy()
+    Ko, Uo = oracle.energy(m, x, v, EPS)
+    assert K == pytest.approx(Ko, rel=1e-13)
+    assert U == pytest.approx(Uo, rel=1e-12)
+
+
+def test_initial_state_matches_oracle():
+    m, x, v = inputs.plummer(512, seed=1)
+    sim = oracle.Sim(m, x, v, EPS, ETA)
+    so = sim.state()
+    with gravidy.Integrator(m, x, v, EPS, ETA, precision="fp64") as g:
+        st = g.state()
+    np.testing.assert_allclose(st["a"], so["a"], rtol=0, atol=1e-12 * np.abs(so["a"]).max())
+    np.testing.assert_allclose(st["j"], so["j"], rtol=0, atol=1e-12 * np.abs(so["j"]).max())
+    assert (st["tau"] == 0).all()
+    assert np.mean(st["dtau"] == so["dtau"]) > 0.99
+
+
+def _replay(prec, m, x, v, rec):
+    with gravidy.Integrator(m, x, v, EPS, ETA, precision=prec) as g:
+        E0 = sum(g.energy())
+        for tick, idx in rec:
+            g.replay_step(tick, idx)
+        st = g.state()
+        E1 = sum(g.energy())
+        stats = g.stats()
+    return st, E0, E1, stats
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_replayed_schedule_n512_to_t1(prec):
+    """Plummer N = 512, eps = 1e-4, eta = 0.01, t = 0 -> 1, the GPU following
+    the oracle's block schedule step by step."""
+    m, x, v = inputs.plummer(512, seed=1)
+    sim = oracle.Sim(m, x, v, EPS, ETA)
+    K0, U0 = sim.energy()
+    rec = []
+    while True:
+        tick, idx = sim.step()
+        rec.append((tick, idx))
+        if tick >= int(1.0 / DT_MIN):
+            break
+    so = sim.state()
+    K1, U1 = sim.energy()
+    st, E0, E1, stats = _replay(prec, m, x, v, rec)
+    assert stats["block_steps"] == len(rec)
+    assert stats["particle_steps"] == sum(len(r[1]) for r in rec)
+    de_or = (K1 + U1 - K0 - U0) / (K0 + U0)
+    de_gpu = (E1 - E0) / E0
+    dx = np.abs(st["x"] - so["x"]).max()
+    agree = np.mean(st["dtau"] == so["dtau"])
+    print("%s replay n=512: %d steps |dE/E| oracle %.3e gpu %.3e  max|dx| %.2e  dtau agree %.4f"
+          % (prec, len(rec), abs(de_or), abs(de_gpu), dx, agree))
+    assert (st["tau"] == so["tau"]).all()
+    if prec == "fp64":
+        assert dx < 1e-9
+        assert abs(de_gpu - de_or) < 1e-10
+        assert agree > 0.99
+    else:
+        assert dx < 1e-4
+        assert abs(de_gpu) < 2 * abs(de_or) + 1e-9
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_free_running_energy_within_2x_of_oracle(prec):
+    m, x, v = inputs.plummer(512, seed=1)
+    sim = oracle.Sim(m, x, v, EPS, ETA)
+    K0, U0 = sim.energy()
+    sim.evolve(1.0)
+    K1, U1 = sim.energy()
+    de_or = abs((K1 + U1 - K0 - U0) / (K0 + U0))
+    with gravidy.Integrator(m, x, v, EPS, ETA, precision=prec) as g:
+        E0 = sum(g.energy())
+        g.evolve(1.0)
+        E1 = sum(g.energy())
+        st = g.state()
+        stats = g.stats()
+    de = abs((E1 - E0) / E0)
+    so = sim.stats()
+    print("%s free n=512 t=1: |dE/E| oracle %.3e gpu %.3e  blocks %d/%d  psteps %d/%d"
+          % (prec, de_or, de, stats["block_steps"], so["nblock"], stats["particle_steps"], so["nsteps"]))
+    assert (st["tau"] == int(1.0 / DT_MIN)).all()
+    assert de <= 2 * de_or + 1e-9
+    assert 0.8 < stats["block_steps"] / so["nblock"] < 1.25
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_graph_and_eager_paths_identical(prec):
+    m, x, v = inputs.plummer(1000, seed=8)
+    out = []
+    for use_graph in (True, False):
+        with gravidy.Integrator(m, x, v, EPS, ETA, precision=prec, use_graph=use_graph, graph_steps=7) as g:
+            g.evolve(0.25)
+            out.append(g.state())
+    for k in out[0]:
+        assert np.array_equal(out[0][k], out[1][k]), k
+
+
+def test_step_block_matches_oracle_schedule():
+    m, x, v = inputs.plummer(700, seed=9)
+    sim = oracle.Sim(m, x, v, EPS, ETA)
+    with gravidy.Integrator(m, x, v, EPS, ETA, precision="fp64") as g:
+        for _ in range(50):
+            tick, idx = sim.step()
+            t, nact = g.step_block()
+            assert t == tick * DT_MIN
+            assert nact == idx.size
+
+
+def test_checkpoint_restart_is_exact():
+    m, x, v = inputs.plummer(900, seed=10)
+    with gravidy.Integrator(m, x, v, EPS, ETA, precision="mixed") as g:
+        g.evolve(0.125)
+        ck = {k: a.copy() for k, a in g.state().items()}
+        g.evolve(0.25)
+        ref = g.state()
+    with gravidy.Integrator(m, x, v, EPS, ETA, precision="mixed") as g:
+        g.set_state(ck["x"], ck["v"], ck["a"], ck["j"], ck["tau"], ck["dtau"])
+        g.evolve(0.25)
+        got = g.state()
+    for k in ref:
+        assert np.array_equal(ref[k], got[k]), k
+
+
+def test_replay_rejects_a_particle_not_behind_the_block_time():
+    m, x, v = inputs.plummer(64, seed=1)
+    with gravidy.Integrator(m, x, v, EPS, ETA, precision="fp64") as g:
+        with pytest.raises(gravidy.GravidyError) as e:
+            g.replay_step(0 + 1, [0, 1])          # fine: tau = 0 < 1
+            g.replay_step(1, [0])                 # particle 0 is already at tick 1
+        assert e.value.code == gravidy.GD_EINVAL
+
+
+def test_kernel_timing_hook():
+    m, x, v = inputs.plummer(2000, seed=2)
+    with gravidy.Integrator(m, x, v, EPS, ETA, time_force=True) as g:
+        g.evolve(0.125)
+        ms, launches = g.kernel_time()
+        st = g.stats()
+    assert launches == st["block_steps"]
+    assert ms > 0
