@@ -1,0 +1,480 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 Hermite-4 block-step N-body hot path.
+
+Workload: Plummer sphere, N = 16384 equal masses in N-body units, Plummer
+softening eps = 1e-4, Aarseth eta = 0.01, power-of-two block steps in
+[2^-22, 1/8], mixed precision (FP32 pair arithmetic on double-single positions,
+FP64 prediction/correction/steps/energy).  One benchmark step advances the
+system by dt_max = 1/8 N-body time unit -- every block step in that interval
+(active-list compaction, prediction of all N, force/jerk of the active set with
+j-split reduction, correction + Aarseth step + quantisation) -- and evaluates
+the energy at the synchronised end time, i.e. one output row of GraviDy's run
+log (Appendix A).  Metric: acc+jerk interactions per second (sum of N_act * N
+over all force evaluations of the timed steps / device time).
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "acc+jerk interactions/s (%FP32 peak @60 flop); s per N-body time unit at |dE/E|"
+UNIT = "interactions/s"
+N_DEFAULT = 16384
+EPS = 1e-4
+ETA = 0.01
+DT_STEP = 0.125
+FLOP_PER_INTERACTION = 60
+# FP32 non-tensor peak from unit counts and the maximum SM clock:
+# 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+L2_FLUSH_BYTES = 512 << 20
+# DRAM traffic of one force launch per ncu capture, keyed by the SHA-256 of the
+# kernel source it was measured on (a changed source reports null).
+FORCE_TRAFFIC_PER_LAUNCH = {}
+
+
+def _args():
+    p = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=8)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gravidy", choices=["gravidy", "reference"])
+    p.add_argument("--n", type=int, default=N_DEFAULT)
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--no-extras", action="store_true", help="skip the fp64, force-sweep, e2e and cpu legs")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="bounded oracle sample length")
+    p.add_argument("--sweep-n", type=int, default=1 << 20)
+    p.add_argument("--profile-force", type=int, default=0, metavar="N",
+                   help="profiling hook: initialise an N-particle Plummer sphere (one full force evaluation), "
+                        "evaluate all N once more, print nothing and exit")
+    p.add_argument("--profile-steps", type=int, default=0, metavar="K",
+                   help="profiling hook: initialise the --n workload and take K block steps one by one "
+                        "(no graph), print nothing and exit")
+    return p.parse_args()
+
+
+def _workload(n):
+    return {
+        "workload": "plummer_n%d_equal_mass_eps1e-4_eta0.01_blocksteps_2^-22..1/8" % n,
+        "n": n,
+        "eps": EPS,
+        "eta": ETA,
+        "dt_min": 2.0 ** -22,
+        "dt_max": DT_STEP,
+        "step": "advance 1/8 N-body time unit (all block steps) + energy at the synchronised end",
+        "ics": "Aarseth-Henon-Wielen Plummer sampling, seed 1 (+rank), N-body units",
+        "l2": "flushed between timed steps (512 MiB device write outside the events)",
+    }
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [q.strip() for q in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower().startswith("active")})
+        sm = [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(r[1] for r in rows), "samples": len(rows),
+                "reasons": reasons}
+
+
+def _rejected(clocks):
+    if not clocks:
+        return False
+    bad = {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
+    if bad & set(clocks["reasons"]):
+        return True
+    return clocks["sm_mhz"] < 0.5 * clocks["sm_max_mhz"] and not clocks["reasons"]
+
+
+# ------------------------------------------------------------------ distributed
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class _Comm:
+    def __init__(self, world, rank, use_cuda):
+        self.world, self.rank = world, rank
+        self.dist = None
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.init_process_group("nccl" if use_cuda else "gloo")
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist:
+            self.dist.barrier()
+
+    def reduce(self, value, op):
+        if not self.dist:
+            return value
+        import torch
+
+        t = torch.tensor([float(value)], dtype=torch.float64,
+                         device="cuda" if self.dist.get_backend() == "nccl" else "cpu")
+        self.dist.all_reduce(t, op=getattr(self.dist.ReduceOp, op))
+        return float(t.item())
+
+    def close(self):
+        if self.dist:
+            self.dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ oracle legs
+
+def _oracle_sample(n, seconds, seed=1):
+    """Time the FP64 oracle integrator on the benchmark's initial conditions:
+    its initial O(N^2) force plus as many block steps as fit in ``seconds``."""
+    import oracle
+    from paper_1702_00440_gb300 import inputs
+
+    m, x, v = inputs.plummer(n, seed=seed)
+    t0 = time.perf_counter()
+    sim = oracle.Sim(m, x, v, EPS, ETA)
+    steps = 0
+    while time.perf_counter() - t0 < seconds:
+        sim.step()
+        steps += 1
+    dt = time.perf_counter() - t0
+    st = sim.stats()
+    return st["interactions"] / dt, st, dt, steps
+
+
+def run_reference(a):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1702_00440_gb300 import inputs
+
+    oracle.build()
+    n = a.n
+    m, x, v = inputs.plummer(n, seed=1)
+    sim = oracle.Sim(m, x, v, EPS, ETA)
+    per_step = 40  # oracle block steps per benchmark step
+
+    def one():
+        t0 = time.perf_counter()
+        it0 = sim.stats()["interactions"]
+        for _ in range(per_step):
+            sim.step()
+        return sim.stats()["interactions"] - it0, time.perf_counter() - t0
+
+    for _ in range(a.warmup):
+        one()
+    tot_i = tot_t = 0.0
+    for _ in range(a.steps):
+        i, t = one()
+        tot_i += i
+        tot_t += t
+    value = tot_i / tot_t
+    sample = ("oracle block steps on the N=%d Plummer ICs after its initial force: %d timed steps of %d block "
+              "steps each (%.3g interactions in %.2f s), single-threaded FP64 C" % (n, a.steps, per_step, tot_i, tot_t))
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": 1e3 * tot_t / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _workload(n),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+    return 0
+
+
+# ------------------------------------------------------------------ main arm
+
+def _traffic():
+    src = os.path.join(ROOT, "paper_1702_00440_gb300", "csrc", "gravidy.cu")
+    with open(src, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()
+    return FORCE_TRAFFIC_PER_LAUNCH.get(h)
+
+
+def run_gravidy(a):
+    import torch
+
+    from paper_1702_00440_gb300 import gravidy, inputs
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    comm = _Comm(world, rank, True)
+    gravidy.load()
+    n = a.n
+    stream = torch.cuda.Stream()
+    m, x, v = inputs.plummer(n, seed=1 + rank)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def flush_l2():
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+
+    g = gravidy.Integrator(m, x, v, EPS, ETA, precision=a.precision, stream=stream.cuda_stream)
+    K0, U0 = g.energy()
+    E0 = K0 + U0
+    t = 0.0
+    for _ in range(a.warmup):
+        t += DT_STEP
+        g.evolve(t)
+        g.energy()
+
+    def timed_region():
+        nonlocal t
+        s0 = g.stats()
+        comm.barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local)
+        sampler.start()
+        total_ms = 0.0
+        per = []
+        E = None
+        for _ in range(a.steps):
+            flush_l2()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            t += DT_STEP
+            g.evolve(t)
+            Kx, Ux = g.energy()
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            per.append(ms)
+            total_ms += ms
+            E = Kx + Ux
+        torch.cuda.synchronize()
+        comm.barrier()
+        clocks = sampler.stop()
+        s1 = g.stats()
+        return total_ms, per, E, clocks, s0, s1
+
+    total_ms, per, E, clocks, s0, s1 = timed_region()
+    retried = False
+    if _rejected(clocks):
+        retried = True
+        total_ms, per, E, clocks, s0, s1 = timed_region()
+    inter = s1["interactions"] - s0["interactions"]
+    launches = s1["kernel_launches"] - s0["kernel_launches"]
+    max_ms = comm.reduce(total_ms, "MAX")
+    tot_inter = comm.reduce(inter, "SUM")
+    value = tot_inter / (max_ms / 1e3)
+    nbu = a.steps * DT_STEP
+    de = abs((E - E0) / E0)
+    state_end = {k: q.copy() for k, q in g.state().items()}
+
+    # ---- roofline of the force kernel: the same workload continued for the
+    # same number of steps with CUDA events around every force launch
+    g2 = gravidy.Integrator(m, x, v, EPS, ETA, precision=a.precision, stream=stream.cuda_stream, time_force=True)
+    g2.set_state(state_end["x"], state_end["v"], state_end["a"], state_end["j"], state_end["tau"], state_end["dtau"])
+    g2.kernel_time()
+    t2 = t
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    region_ms = 0.0
+    for _ in range(a.steps):
+        flush_l2()
+        e0.record(stream)
+        t2 += DT_STEP
+        g2.evolve(t2)
+        g2.energy()
+        e1.record(stream)
+        e1.synchronize()
+        region_ms += e0.elapsed_time(e1)
+    f_ms, f_launches, f_inter = g2.kernel_time()
+    g2.close()
+    achieved = FLOP_PER_INTERACTION * f_inter / (f_ms / 1e3) / 1e12
+    traffic = _traffic()
+    roofline = {
+        "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+        "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+        "kernel": "k_force_%s" % ("mixed" if a.precision == "mixed" else "fp64"),
+        "peak_basis": "FP32 non-tensor: 152 SMs x 128 lanes x 2 flop x 2070 MHz (unit counts x max clock)",
+        "flop_per_interaction": FLOP_PER_INTERACTION, "launches": f_launches,
+        "avg_launch_us": 1e3 * f_ms / max(1, f_launches),
+        "interactions_per_launch": f_inter / max(1, f_launches),
+        "share_of_step_time": f_ms / region_ms if region_ms > 0 else None,
+    }
+
+    extras = {}
+    cpu = None
+    e2e = None
+    if not a.no_extras:
+        # ---- end to end through the public API from pinned host buffers
+        pin = {k: torch.empty(q.shape, dtype=torch.float64 if q.dtype == np.float64 else torch.int64,
+                              pin_memory=True).numpy() for k, q in state_end.items()}
+        now = g.state()
+        for k in pin:
+            pin[k][...] = now[k]
+        t_e2e0 = t
+        bi = 4 * n * 3 * 8 + 3 * n * 8   # x, v, a, jerk + tau, dtau, next time
+        bo = 4 * n * 3 * 8 + 2 * n * 8 + 16
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        e_inter = 0.0
+        for _ in range(a.steps):
+            si = g.stats()["interactions"]
+            g.set_state(pin["x"], pin["v"], pin["a"], pin["j"], pin["tau"], pin["dtau"])
+            t += DT_STEP
+            g.evolve(t)
+            g.energy()
+            g.state(out=pin)
+            e_inter += g.stats()["interactions"] - si
+        w1 = time.perf_counter()
+        e_max = comm.reduce(w1 - w0, "MAX")
+        e2e = {"value": comm.reduce(e_inter, "SUM") / e_max, "unit": UNIT, "h2d_bytes_per_step": bi,
+               "d2h_bytes_per_step": bo, "timing": "host wall clock, set_state + evolve(+1/8) + energy + get_state"}
+
+        # ---- plain FP64 GPU form over the first 1/8 from the same ICs
+        if a.precision == "mixed":
+            for prec in ("fp64", "mixed"):
+                g3 = gravidy.Integrator(m, x, v, EPS, ETA, precision=prec, stream=stream.cuda_stream)
+                Ea = sum(g3.energy())
+                e0.record(stream)
+                g3.evolve(DT_STEP)
+                e1.record(stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                Eb = sum(g3.energy())
+                st3 = g3.stats()
+                g3.close()
+                extras["t0_to_1/8_%s" % prec] = {"s_per_nbu": ms / 1e3 / DT_STEP, "dE_E": abs((Eb - Ea) / Ea),
+                                                 "interactions_per_s": (st3["interactions"] - n * n) / (ms / 1e3)}
+
+        # ---- full force evaluation at N = 2^20 (all particles active)
+        if rank == 0 and a.sweep_n > 0:
+            ms_, xs_, vs_ = inputs.plummer(a.sweep_n, seed=1)
+            g4 = gravidy.Integrator(ms_, xs_, vs_, EPS, ETA, precision="mixed", stream=stream.cuda_stream,
+                                    time_force=True)
+            g4.kernel_time()
+            idx = np.arange(a.sweep_n, dtype=np.int32)
+            g4.force(0, idx)
+            g4.kernel_time()
+            g4.force(0, idx)
+            fm, fl, fi = g4.kernel_time()
+            g4.close()
+            extras["force_full_n%d" % a.sweep_n] = {
+                "interactions_per_s": fi / (fm / 1e3), "ms": fm,
+                "tflops_at_60": FLOP_PER_INTERACTION * fi / (fm / 1e3) / 1e12,
+                "frac_fp32_peak": FLOP_PER_INTERACTION * fi / (fm / 1e3) / 1e12 / FP32_PEAK_TFLOPS}
+
+        # ---- the oracle on the host cores (rank 0, single GPU only)
+        if rank == 0 and world == 1:
+            cv, cst, cdt, csteps = _oracle_sample(n, a.cpu_seconds)
+            cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": "FP64 C oracle on the same N=%d ICs: initial O(N^2) force + %d block steps "
+                             "(%.3g interactions in %.1f s)" % (n, csteps, cst["interactions"], cdt)}
+    g.close()
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": max_ms / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 pair / f64 update" if a.precision == "mixed" else "f64",
+            "data": "synthetic", "config": _workload(n),
+            "s_per_nbu": max_ms / 1e3 / nbu, "dE_E": de,
+            "t_timed": [(a.warmup) * DT_STEP, (a.warmup + a.steps) * DT_STEP],
+            "block_steps": s1["block_steps"] - s0["block_steps"],
+            "particle_steps": s1["particle_steps"] - s0["particle_steps"],
+            "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clocks, "clock_retry": retried, "per_step_ms": per, **extras,
+        }
+        print(json.dumps(out))
+    comm.close()
+    return 0
+
+
+def profile_force(a):
+    from paper_1702_00440_gb300 import gravidy, inputs
+
+    m, x, v = inputs.plummer(a.profile_force, seed=1)
+    with gravidy.Integrator(m, x, v, EPS, ETA, precision=a.precision) as g:
+        g.force(0, np.arange(a.profile_force, dtype=np.int32))
+    return 0
+
+
+def profile_steps(a):
+    from paper_1702_00440_gb300 import gravidy, inputs
+
+    m, x, v = inputs.plummer(a.n, seed=1)
+    with gravidy.Integrator(m, x, v, EPS, ETA, precision=a.precision, use_graph=False) as g:
+        for _ in range(a.profile_steps):
+            g.step_block()
+    return 0
+
+
+def main():
+    a = _args()
+    if a.profile_force:
+        return profile_force(a)
+    if a.profile_steps:
+        return profile_steps(a)
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_gravidy(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

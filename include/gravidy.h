@@ -76,6 +76,7 @@ typedef struct gd_stats {
     int64_t particle_steps;/* sum of N_act over block steps ("Nsteps") */
     double interactions;   /* sum of N_act * N over all force evaluations */
     int64_t last_nact;     /* N_act of the last block step */
+    int64_t kernel_launches; /* CUDA kernels this context has launched (host count) */
 } gd_stats;
 
 typedef struct gd_ctx gd_ctx;
@@ -121,9 +122,12 @@ int gd_set_state(gd_ctx *c, const double *x, const double *v, const double *a,
 /* Counters since gd_init. */
 int gd_get_stats(gd_ctx *c, gd_stats *s);
 
-/* Average device time of the force launches recorded since the last call
- * (needs opts.time_force = 1): *ms_total, *launches. */
-int gd_kernel_time(gd_ctx *c, double *ms_total, int64_t *launches);
+/* Device time of the force-kernel launches recorded (CUDA events on the
+ * context's stream) since the last call, for launches with a non-empty active
+ * set (needs opts.time_force = 1): *ms_total summed milliseconds, *launches
+ * their count, *interactions the sum of N_act * N they computed.  Any pointer
+ * may be NULL.  Resets the counters. */
+int gd_kernel_time(gd_ctx *c, double *ms_total, int64_t *launches, double *interactions);
 
 void gd_free(gd_ctx *c);
 

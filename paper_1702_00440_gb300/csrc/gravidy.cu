@@ -902,6 +902,10 @@ struct gd_ctx {
     int grid_force, grid_sel, grid_corr;
     bool mixed, soft;
     Ctrl *h_ctrl;  // pinned mirror
+    Ctrl *h_snap;  // two pinned snapshots for the pipelined gd_evolve
+    cudaEvent_t ev_snap[2];
+    double *h_stage;  // pinned staging: 12 n doubles then 3 n int64
+    long long launches;  // kernels launched by this context
     cudaGraphExec_t graph;
     int graph_steps;
     std::vector<cudaEvent_t> ev;  // force timing pairs, one per graph slot (or eager)
@@ -952,6 +956,7 @@ FArgs fargs(const gd_ctx *c) { return FArgs{c->d, c->grid_force, c->opt.mode_cut
 int launch_force(gd_ctx *c)
 {
     FArgs fa = fargs(c);
+    c->launches += 1;
     if (c->mixed) {
         if (c->soft)
             k_force_mixed<true><<<c->grid_force, FT, 0, c->stream>>>(fa);
@@ -969,6 +974,7 @@ int launch_force(gd_ctx *c)
 void launch_predict_all(gd_ctx *c, long long tick, bool mixed_records)
 {
     const int g = (c->d.n + 255) / 256;
+    c->launches += 1;
     if (mixed_records)
         k_predict_all<true><<<g, 256, 0, c->stream>>>(c->d, tick);
     else
@@ -978,6 +984,7 @@ void launch_predict_all(gd_ctx *c, long long tick, bool mixed_records)
 // One free-running block step: select+predict, force, correct.
 void launch_step(gd_ctx *c, int slot, cudaEvent_t e0, cudaEvent_t e1, bool capturing)
 {
+    c->launches += 2;  // select + correct (launch_force counts itself)
     if (c->mixed)
         k_select_predict<true><<<c->grid_sel, ST, 0, c->stream>>>(c->d, slot);
     else
@@ -1030,6 +1037,10 @@ void free_all(gd_ctx *c)
     for (void *p : ps)
         if (p) cudaFree(p);
     if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
+    if (c->h_snap) cudaFreeHost(c->h_snap);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    for (int k = 0; k < 2; k++)
+        if (c->ev_snap[k]) cudaEventDestroy(c->ev_snap[k]);
     if (c->h_hist) cudaFreeHost(c->h_hist);
     if (c->graph) cudaGraphExecDestroy(c->graph);
     for (cudaEvent_t e : c->ev)
@@ -1037,28 +1048,39 @@ void free_all(gd_ctx *c)
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
-// AoS (n,3) host -> SoA planes on the device
-int upload_aos(gd_ctx *c, double *dst, const double *src)
+// AoS (n,3) host -> SoA planes on the device through pinned staging slot `slot`
+// (0..3); the copy is queued on the stream, the caller synchronises.
+int upload_aos(gd_ctx *c, double *dst, const double *src, int slot)
 {
     const int n = c->d.n;
-    std::vector<double> t((size_t)3 * n);
+    double *t = c->h_stage + (size_t)slot * 3 * n;
     for (int i = 0; i < n; i++)
         for (int k = 0; k < 3; k++) t[(size_t)k * n + i] = src[3 * (size_t)i + k];
-    CK(cudaMemcpyAsync(dst, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpyAsync(dst, t, (size_t)3 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     return GD_OK;
 }
 
-int download_aos(gd_ctx *c, double *dst, const double *src, int plane_stride)
+// Device SoA planes (stride plane_stride) -> pinned staging slot; transpose later
+// with unstage_aos after a synchronise.
+int download_planes(gd_ctx *c, const double *src, int plane_stride, int slot)
 {
     const int n = c->d.n;
-    std::vector<double> t((size_t)3 * plane_stride);
-    CK(cudaMemcpyAsync(t.data(), src, t.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    for (int i = 0; i < n; i++)
-        for (int k = 0; k < 3; k++) dst[3 * (size_t)i + k] = t[(size_t)k * plane_stride + i];
+    double *t = c->h_stage + (size_t)slot * 3 * n;
+    for (int k = 0; k < 3; k++)
+        CK(cudaMemcpyAsync(t + (size_t)k * n, src + (size_t)k * plane_stride, (size_t)n * sizeof(double),
+                           cudaMemcpyDeviceToHost, c->stream));
     return GD_OK;
 }
+
+void unstage_aos(gd_ctx *c, double *dst, int slot)
+{
+    const int n = c->d.n;
+    const double *t = c->h_stage + (size_t)slot * 3 * n;
+    for (int i = 0; i < n; i++)
+        for (int k = 0; k < 3; k++) dst[3 * (size_t)i + k] = t[(size_t)k * n + i];
+}
+
+long long *stage_i64(gd_ctx *c, int k) { return (long long *)(c->h_stage + (size_t)12 * c->d.n) + (size_t)k * c->d.n; }
 
 int first_forces(gd_ctx *c)
 {
@@ -1075,6 +1097,7 @@ int first_forces(gd_ctx *c)
     k_reduce_partials<<<(n + 255) / 256, 256, 0, c->stream>>>(rargs(c), d.a, d.jk, n);
     k_init_steps<<<(n + 255) / 256, 256, 0, c->stream>>>(d);
     k_resync<<<1, 1024, 0, c->stream>>>(d);
+    c->launches += 5;
     CK(cudaGetLastError());
     return sync_ctrl(c);
 }
@@ -1227,6 +1250,10 @@ int gd_init(gd_ctx **out, int64_t n, const double *m, const double *x, const dou
         return bail(rc);
     e = cudaMallocHost((void **)&c->h_ctrl, sizeof(Ctrl));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_hist, sizeof(int) * 64);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_snap, 2 * sizeof(Ctrl));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_stage, (size_t)15 * d.n * sizeof(double));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_snap[0], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_snap[1], cudaEventDisableTiming);
     if (e != cudaSuccess) return bail(fail(c, GD_ENOMEM, "pinned host allocation failed"));
     if (o.time_force) {
         c->ev.resize(2 * 64);
@@ -1247,7 +1274,9 @@ int gd_init(gd_ctx **out, int64_t n, const double *m, const double *x, const dou
     if (e == cudaSuccess) e = cudaMemsetAsync(d.act, 0, sizeof(int) * d.n, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d.m, m, sizeof(double) * d.n, cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "upload"));
-    if ((rc = upload_aos(c, d.x, x)) || (rc = upload_aos(c, d.v, v))) return bail(rc);
+    if ((rc = upload_aos(c, d.x, x, 0)) || (rc = upload_aos(c, d.v, v, 1))) return bail(rc);
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "upload"));
     if (d.npad > d.n) k_init_pads<<<(d.npad - d.n + 127) / 128, 128, 0, c->stream>>>(d);
     if ((rc = first_forces(c))) return bail(rc);
     *out = c;
@@ -1263,14 +1292,16 @@ int gd_evolve(gd_ctx *c, double t_end)
     if (q > 9.0e18) return fail(c, GD_EINVAL, "t_end too large");
     const long long tick_end = (long long)q;
     if (tick_end < c->h_ctrl->T_last) return fail(c, GD_EINVAL, "t_end is before the current time");
-    k_set_tick_end<<<1, 1, 0, c->stream>>>(c->d.ctrl, tick_end);
     const int G = c->graph_steps;
     if (c->opt.use_graph) {
         if ((rc = build_graph(c))) return rc;
     }
-    for (;;) {
+    k_set_tick_end<<<1, 1, 0, c->stream>>>(c->d.ctrl, tick_end);
+    c->launches += 1;
+    auto chunk = [&]() -> int {
         if (c->opt.use_graph) {
             CK(cudaGraphLaunch(c->graph, c->stream));
+            c->launches += 3LL * G;
         } else {
             for (int s = 0; s < G; s++) {
                 cudaEvent_t e0 = c->opt.time_force ? c->ev[2 * s] : nullptr;
@@ -1279,11 +1310,32 @@ int gd_evolve(gd_ctx *c, double t_end)
             }
         }
         CK(cudaGetLastError());
-        if ((rc = sync_ctrl(c))) return rc;
-        if ((rc = harvest_times(c, G))) return rc;
-        if (c->h_ctrl->T_cur > tick_end) break;
+        return GD_OK;
+    };
+    if (c->opt.time_force) {
+        // timed runs read the per-slot events after every chunk: no overlap
+        for (;;) {
+            if ((rc = chunk())) return rc;
+            if ((rc = sync_ctrl(c))) return rc;
+            if ((rc = harvest_times(c, G))) return rc;
+            if (c->h_ctrl->T_cur > tick_end) break;
+        }
+    } else {
+        // keep one chunk in flight while the host looks at the previous one's snapshot
+        if ((rc = chunk())) return rc;
+        CK(cudaMemcpyAsync(&c->h_snap[0], c->d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaEventRecord(c->ev_snap[0], c->stream));
+        for (long long k = 0;; k++) {
+            const int cur = (int)(k & 1), nxt = 1 - cur;
+            if ((rc = chunk())) return rc;
+            CK(cudaMemcpyAsync(&c->h_snap[nxt], c->d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaEventRecord(c->ev_snap[nxt], c->stream));
+            CK(cudaEventSynchronize(c->ev_snap[cur]));
+            if (c->h_snap[cur].err != 0 || c->h_snap[cur].T_cur > tick_end) break;
+        }
     }
     k_set_tick_end<<<1, 1, 0, c->stream>>>(c->d.ctrl, LLONG_MAX);
+    c->launches += 1;
     return sync_ctrl(c);
 }
 
@@ -1307,6 +1359,7 @@ int gd_energy(gd_ctx *c, double *K, double *U)
     launch_predict_all(c, c->h_ctrl->T_last, false);
     k_energy_terms<<<(c->d.n + ET - 1) / ET, ET, 0, c->stream>>>(c->d);
     k_energy_sum<<<1, 1024, 0, c->stream>>>(c->d);
+    c->launches += 2;
     CK(cudaGetLastError());
     if ((rc = sync_ctrl(c))) return rc;
     if (K) *K = c->h_ctrl->K;
@@ -1319,13 +1372,19 @@ int gd_get_state(gd_ctx *c, double *x, double *v, double *a, double *jerk, int64
     int rc = check_usable(c);
     if (rc) return rc;
     const Dev &d = c->d;
-    if (x && (rc = download_aos(c, x, d.x, d.n))) return rc;
-    if (v && (rc = download_aos(c, v, d.v, d.n))) return rc;
-    if (a && (rc = download_aos(c, a, d.a, d.n))) return rc;
-    if (jerk && (rc = download_aos(c, jerk, d.jk, d.n))) return rc;
-    if (tau) CK(cudaMemcpyAsync(tau, d.tau, sizeof(long long) * d.n, cudaMemcpyDeviceToHost, c->stream));
-    if (dtau) CK(cudaMemcpyAsync(dtau, d.dtau, sizeof(long long) * d.n, cudaMemcpyDeviceToHost, c->stream));
+    if (x && (rc = download_planes(c, d.x, d.n, 0))) return rc;
+    if (v && (rc = download_planes(c, d.v, d.n, 1))) return rc;
+    if (a && (rc = download_planes(c, d.a, d.n, 2))) return rc;
+    if (jerk && (rc = download_planes(c, d.jk, d.n, 3))) return rc;
+    if (tau) CK(cudaMemcpyAsync(stage_i64(c, 0), d.tau, sizeof(long long) * d.n, cudaMemcpyDeviceToHost, c->stream));
+    if (dtau) CK(cudaMemcpyAsync(stage_i64(c, 1), d.dtau, sizeof(long long) * d.n, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    if (x) unstage_aos(c, x, 0);
+    if (v) unstage_aos(c, v, 1);
+    if (a) unstage_aos(c, a, 2);
+    if (jerk) unstage_aos(c, jerk, 3);
+    if (tau) std::memcpy(tau, stage_i64(c, 0), sizeof(long long) * d.n);
+    if (dtau) std::memcpy(dtau, stage_i64(c, 1), sizeof(long long) * d.n);
     return GD_OK;
 }
 
@@ -1350,14 +1409,18 @@ int gd_set_state(gd_ctx *c, const double *x, const double *v, const double *a, c
         tn[i] = t + dt;
         tmax = std::max(tmax, t);
     }
-    if ((rc = upload_aos(c, d.x, x)) || (rc = upload_aos(c, d.v, v)) || (rc = upload_aos(c, d.a, a)) ||
-        (rc = upload_aos(c, d.jk, jerk)))
+    CK(cudaStreamSynchronize(c->stream));  // the staging buffer is free
+    if ((rc = upload_aos(c, d.x, x, 0)) || (rc = upload_aos(c, d.v, v, 1)) || (rc = upload_aos(c, d.a, a, 2)) ||
+        (rc = upload_aos(c, d.jk, jerk, 3)))
         return rc;
-    CK(cudaMemcpyAsync(d.tau, tau, sizeof(long long) * d.n, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(d.dtau, dtau, sizeof(long long) * d.n, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(d.tnext, tn.data(), sizeof(long long) * d.n, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    std::memcpy(stage_i64(c, 0), tau, sizeof(long long) * d.n);
+    std::memcpy(stage_i64(c, 1), dtau, sizeof(long long) * d.n);
+    std::memcpy(stage_i64(c, 2), tn.data(), sizeof(long long) * d.n);
+    CK(cudaMemcpyAsync(d.tau, stage_i64(c, 0), sizeof(long long) * d.n, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(d.dtau, stage_i64(c, 1), sizeof(long long) * d.n, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(d.tnext, stage_i64(c, 2), sizeof(long long) * d.n, cudaMemcpyHostToDevice, c->stream));
     k_resync<<<1, 1024, 0, c->stream>>>(c->d);
+    c->launches += 1;
     // the time of the last block step becomes the latest particle time
     Ctrl *h = c->h_ctrl;
     if ((rc = sync_ctrl(c))) return rc;
@@ -1379,15 +1442,17 @@ int gd_get_stats(gd_ctx *c, gd_stats *s)
     s->particle_steps = h->nsteps;
     s->interactions = h->interactions;
     s->last_nact = h->last_nact;
+    s->kernel_launches = c->launches;
     return GD_OK;
 }
 
-int gd_kernel_time(gd_ctx *c, double *ms_total, int64_t *launches)
+int gd_kernel_time(gd_ctx *c, double *ms_total, int64_t *launches, double *interactions)
 {
     if (!c) return fail(nullptr, GD_EINVAL, "null context");
     if (!c->opt.time_force) return fail(c, GD_ESTATE, "time_force was not enabled");
     if (ms_total) *ms_total = c->force_ms;
     if (launches) *launches = c->force_launches;
+    if (interactions) *interactions = c->force_interactions;
     c->force_ms = 0;
     c->force_launches = 0;
     c->force_interactions = 0;
@@ -1423,7 +1488,10 @@ int gd_force(gd_ctx *c, int64_t tick, const int32_t *idx, int64_t nact, double *
     const long long Tsave = c->h_ctrl->T_cur;
     launch_predict_all(c, tick, c->mixed);
     k_set_step<<<1, 1, 0, c->stream>>>(d.ctrl, Tsave, (int)nact);
+    c->launches += 2;
+    if (c->opt.time_force) CK(cudaEventRecord(c->ev[0], c->stream));
     launch_force(c);
+    if (c->opt.time_force) CK(cudaEventRecord(c->ev[1], c->stream));
     double *out = d.fout;
     k_reduce_partials<<<(int)((nact + 255) / 256), 256, 0, c->stream>>>(rargs(c), out, out + 3 * nact, (int)nact);
     std::vector<double> h((size_t)6 * nact);
@@ -1437,6 +1505,13 @@ int gd_force(gd_ctx *c, int64_t tick, const int32_t *idx, int64_t nact, double *
             acc[3 * k + q] = h[(size_t)q * nact + k];
             jerk[3 * k + q] = h[(size_t)(3 + q) * nact + k];
         }
+    if (c->opt.time_force) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+        c->force_ms += ms;
+        c->force_launches += 1;
+        c->force_interactions += (double)nact * (double)d.n;
+    }
     // the free-running step recomputes act and nact
     return sync_ctrl(c);
 }
@@ -1448,8 +1523,11 @@ int gd_predict(gd_ctx *c, int64_t tick, double *xp, double *vp)
     if (tick < 0) return fail(c, GD_EINVAL, "tick must be >= 0");
     launch_predict_all(c, tick, false);
     CK(cudaGetLastError());
-    if (xp && (rc = download_aos(c, xp, c->d.pd, c->d.npad))) return rc;
-    if (vp && (rc = download_aos(c, vp, c->d.pd + 3 * (size_t)c->d.npad, c->d.npad))) return rc;
+    if ((rc = download_planes(c, c->d.pd, c->d.npad, 0))) return rc;
+    if ((rc = download_planes(c, c->d.pd + 3 * (size_t)c->d.npad, c->d.npad, 1))) return rc;
+    CK(cudaStreamSynchronize(c->stream));
+    if (xp) unstage_aos(c, xp, 0);
+    if (vp) unstage_aos(c, vp, 1);
     return GD_OK;
 }
 
@@ -1470,6 +1548,7 @@ int gd_active(gd_ctx *c, int32_t *idx, int64_t *nact, int64_t *tick_next)
     *tick_next = c->h_ctrl->T_cur;
     CK(cudaMemcpyAsync(idx, d.act, sizeof(int) * na, cudaMemcpyDeviceToHost, c->stream));
     k_resync<<<1, 1024, 0, c->stream>>>(d);
+    c->launches += 2;
     return sync_ctrl(c);
 }
 
@@ -1491,6 +1570,7 @@ int gd_replay_step(gd_ctx *c, int64_t tick_next, const int32_t *idx, int64_t nac
     launch_force(c);
     k_correct<<<c->grid_corr, CT, 0, c->stream>>>(rargs(c));
     k_resync<<<1, 1024, 0, c->stream>>>(d);
+    c->launches += 3;
     CK(cudaGetLastError());
     return sync_ctrl(c);
 }

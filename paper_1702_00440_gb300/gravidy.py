@@ -58,6 +58,7 @@ class gd_stats(ctypes.Structure):
         ("particle_steps", ctypes.c_int64),
         ("interactions", ctypes.c_double),
         ("last_nact", ctypes.c_int64),
+        ("kernel_launches", ctypes.c_int64),
     ]
 
 
@@ -91,7 +92,7 @@ def load(build_if_missing: bool = True):
             "gd_get_state": (ctypes.c_int, [P, P, P, P, P, P, P]),
             "gd_set_state": (ctypes.c_int, [P, P, P, P, P, P, P]),
             "gd_get_stats": (ctypes.c_int, [P, P]),
-            "gd_kernel_time": (ctypes.c_int, [P, P, P]),
+            "gd_kernel_time": (ctypes.c_int, [P, P, P, P]),
             "gd_free": (None, [P]),
             "gd_last_error": (ctypes.c_char_p, [P]),
             "gd_force": (ctypes.c_int, [P, I64, P, I64, P, P]),
@@ -195,14 +196,16 @@ def gd_get_stats(ctx):
     s = gd_stats()
     _check(load().gd_get_stats(ctx, ctypes.byref(s)), ctx)
     return dict(tick=s.tick, block_steps=s.block_steps, particle_steps=s.particle_steps,
-                interactions=s.interactions, last_nact=s.last_nact)
+                interactions=s.interactions, last_nact=s.last_nact, kernel_launches=s.kernel_launches)
 
 
 def gd_kernel_time(ctx):
+    """(milliseconds, launches, interactions) of the timed force launches."""
     ms = ctypes.c_double()
     k = ctypes.c_int64()
-    _check(load().gd_kernel_time(ctx, ctypes.byref(ms), ctypes.byref(k)), ctx)
-    return ms.value, k.value
+    it = ctypes.c_double()
+    _check(load().gd_kernel_time(ctx, ctypes.byref(ms), ctypes.byref(k), ctypes.byref(it)), ctx)
+    return ms.value, k.value, it.value
 
 
 def gd_free(ctx):

@@ -300,7 +300,8 @@ def test_kernel_timing_hook():
     m, x, v = inputs.plummer(2000, seed=2)
     with gravidy.Integrator(m, x, v, EPS, ETA, time_force=True) as g:
         g.evolve(0.125)
-        ms, launches = g.kernel_time()
+        ms, launches, inter = g.kernel_time()
         st = g.stats()
     assert launches == st["block_steps"]
+    assert inter == st["interactions"] - 2000.0 ** 2   # all but the initial evaluation
     assert ms > 0
