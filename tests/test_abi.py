@@ -1,0 +1,74 @@
+"""The C ABI without a GPU: the library builds, loads, and exports every
+function include/gravidy.h declares; host-side argument checks of gd_init
+reject bad input before any device work."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1702_00440_gb300 import gravidy
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "gravidy.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w \*]*?\b(gd_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("gd_init", "gd_evolve", "gd_step_block", "gd_energy", "gd_get_state", "gd_free", "gd_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_function():
+    lib = gravidy.load()
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert sorted(gravidy.EXPORTS) == _declared()
+
+
+def _init(n, m, x, v, eps=1e-4, eta=0.01, **kw):
+    lib = gravidy.load()
+    o = gravidy.make_opts(**kw)
+    h = ctypes.c_void_p()
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    rc = lib.gd_init(ctypes.byref(h), n, p(m), p(x), p(v), eps, eta, ctypes.byref(o))
+    return rc, lib.gd_last_error(None).decode()
+
+
+@pytest.mark.parametrize("case", ["n0", "eps", "eta", "dtmin", "dtorder", "mass", "nan"])
+def test_gd_init_rejects_bad_arguments_on_the_host(case):
+    n = 4
+    m = np.full(n, 0.25)
+    x = np.arange(12, dtype=float).reshape(4, 3)
+    v = np.zeros((4, 3))
+    kw = {}
+    eps, eta = 1e-4, 0.01
+    if case == "n0":
+        n = 0
+    elif case == "eps":
+        eps = -1.0
+    elif case == "eta":
+        eta = 0.0
+    elif case == "dtmin":
+        kw["dt_min"] = 3e-7
+    elif case == "dtorder":
+        kw["dt_min"], kw["dt_max"] = 0.25, 0.125
+    elif case == "mass":
+        m[1] = -1.0
+    elif case == "nan":
+        x[2, 1] = np.nan
+    rc, msg = _init(n, m, x, v, eps, eta, **kw)
+    assert rc == gravidy.GD_EINVAL
+    assert msg
+
+
+def test_opts_defaults():
+    o = gravidy.make_opts()
+    assert o.dt_min == 2.0 ** -22 and o.dt_max == 0.125 and o.precision == gravidy.GD_MIXED
