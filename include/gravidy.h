@@ -131,7 +131,8 @@ int gd_kernel_time(gd_ctx *c, double *ms_total, int64_t *launches, double *inter
 
 void gd_free(gd_ctx *c);
 
-/* Message of the last error on c (or of the last failed gd_init if c is NULL). */
+/* Message of the last error on c (or, for c NULL, of the calling thread's last
+ * failed gd_init or gd_force_noalloc). */
 const char *gd_last_error(const gd_ctx *c);
 
 /* ---- hooks for tests and measurement (no integration state changes) ---- */
@@ -157,6 +158,43 @@ int gd_active(gd_ctx *c, int32_t *idx, int64_t *nact, int64_t *tick_next);
  * tick_next): used to replay another integrator's schedule.  The new steps
  * are computed and stored as usual but the block times come from the caller. */
 int gd_replay_step(gd_ctx *c, int64_t tick_next, const int32_t *idx, int64_t nact);
+
+/* ---- allocation-free variant ---------------------------------------------
+ *
+ * The paper has no counterpart of this entry point; it exists for callers that
+ * cannot call cudaMalloc -- code running where another component owns the
+ * device memory budget (a framework's caching allocator, a hard memory cap),
+ * or on a latency-critical path where an allocation and the device-wide
+ * synchronisation it may imply are not acceptable.
+ *
+ * gd_force_noalloc computes what gd_force computes with GD_MIXED precision --
+ * the softened acceleration and jerk of the particles idx[0..nact) against all
+ * n particles (Sec. 2.4, softened Eq. 1 and its time derivative) -- but from
+ * caller-owned DEVICE arrays and without allocating anything.  Its scratch
+ * (about 4.4 MiB: j-records, j-split partial sums, a control block) is a fixed
+ * array compiled into the library, which every GPU that loads the library
+ * holds until the process exits.
+ *
+ *   n      number of particles, 1 <= n <= 32768 (larger n returns GD_EINVAL)
+ *   m      device, n doubles;  x, v  device, n*3 doubles (AoS xyz)
+ *   eps    Plummer softening >= 0
+ *   idx    device, nact int32 particle indices (duplicates allowed); an entry
+ *          outside [0, n) yields NaN in its output rows
+ *   nact   1 <= nact <= n
+ *   acc, jerk  device, nact*3 doubles (AoS), written in the order of idx
+ *   stream cudaStream_t to run on (NULL = the legacy default stream)
+ *
+ * All pointers refer to memory on the current device.  The call only queues
+ * kernels: results are ready once the stream has reached them.  The first call
+ * on a device does a one-time set-up for that device (it looks up the scratch
+ * array's device address and the kernel's occupancy), so make that first call
+ * before any stream capture.  All calls on a device share the one scratch
+ * array, and each call re-initialises everything it reads from it; calls whose
+ * work overlaps on the GPU (different streams, or different host threads)
+ * race on that array and give wrong results, so serialise them.  Errors are
+ * reported by the return value, with a message from gd_last_error(NULL). */
+int gd_force_noalloc(int64_t n, const double *m, const double *x, const double *v, double eps,
+                     const int32_t *idx, int64_t nact, double *acc, double *jerk, void *stream);
 
 #ifdef __cplusplus
 }

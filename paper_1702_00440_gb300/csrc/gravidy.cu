@@ -24,6 +24,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -1576,3 +1577,165 @@ int gd_replay_step(gd_ctx *c, int64_t tick_next, const int32_t *idx, int64_t nac
 }
 
 }  // extern "C"
+
+// ================================================================ allocation-free force evaluation
+//
+// gd_force_noalloc: the mixed-precision force/jerk evaluation (k_force_mixed with
+// its j-split partial sums) for callers that cannot allocate device memory.  Its
+// scratch -- control block, a sanitised copy of the index list, the predicted
+// j-records and the j-split partials -- lives in one file-scope __device__ array
+// of fixed size, so the call allocates nothing.  Host code must not use the
+// array's name as an address: the per-device set-up below asks the runtime for
+// the array's device address once, with that device current, and passes it to
+// the kernels.
+
+namespace {
+
+constexpr int NOALLOC_NMAX = 32768;                        // largest n accepted
+constexpr long long NOALLOC_CAP = 2LL * NOALLOC_NMAX;      // partial entries per component
+constexpr size_t NA_OFF_ACT = 256;
+constexpr size_t NA_OFF_JA = NA_OFF_ACT + sizeof(int) * (size_t)NOALLOC_NMAX;
+constexpr size_t NA_OFF_JB = NA_OFF_JA + sizeof(float4) * (size_t)NOALLOC_NMAX;
+constexpr size_t NA_OFF_JC = NA_OFF_JB + sizeof(float4) * (size_t)NOALLOC_NMAX;
+constexpr size_t NA_OFF_PART = NA_OFF_JC + sizeof(float2) * (size_t)NOALLOC_NMAX;
+constexpr size_t NOALLOC_BYTES = NA_OFF_PART + sizeof(double) * 6 * (size_t)NOALLOC_CAP;  // about 4.4 MiB
+static_assert(sizeof(Ctrl) <= NA_OFF_ACT, "control block must fit its slot");
+static_assert(NOALLOC_NMAX % BJ == 0, "the j-records are padded to whole tiles");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+struct NoAllocDevice {
+    bool ready;
+    unsigned char *scratch;  // device address of g_noalloc_scratch on this device
+    int grid;                // force-kernel grid (SMs x resident CTAs)
+};
+constexpr int NOALLOC_MAX_DEVICES = 64;
+NoAllocDevice g_noalloc_dev[NOALLOC_MAX_DEVICES];
+std::mutex g_noalloc_mu;
+
+// Packs the caller's FP64 particles (AoS, device) into the scratch j-records with
+// massless far-away padding, copies the index list with out-of-range entries
+// replaced by 0 (and remembered), and resets the control block.
+__global__ void k_noalloc_pack(Dev d, const double *m, const double *x, const double *v, const int *idx, int nact,
+                               int *bad_flags)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < d.npad) {
+        if (i < d.n) {
+            double xp[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+            double vp[3] = {v[3 * i], v[3 * i + 1], v[3 * i + 2]};
+            store_jrec<true>(d, i, xp, vp, m[i]);
+        } else {
+            d.jA[i] = make_float4(PAD_FAR_F, PAD_FAR_F, PAD_FAR_F, 0.f);
+            d.jB[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            d.jC[i] = make_float2(0.f, 0.f);
+        }
+    }
+    if (i < nact) {
+        const int k = idx[i];
+        const bool ok = k >= 0 && k < d.n;
+        d.act[i] = ok ? k : 0;
+        bad_flags[i] = ok ? 0 : 1;
+    }
+    if (i == 0) {
+        Ctrl c;
+        memset(&c, 0, sizeof(c));
+        c.nact = nact;
+        *d.ctrl = c;
+    }
+}
+
+// Sums the j-split partials of every slot into the caller's AoS outputs; slots
+// whose index was out of range get NaN.
+__global__ void k_noalloc_out(RArgs ra, const int *bad_flags, double *acc, double *jerk)
+{
+    const Dev &d = ra.d;
+    const int nact = d.ctrl->nact;
+    const Plan pl = make_plan(nact, d.npad, ra.grid, ra.mode_cut, ra.jsplit, true, d.cap);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nact; k += gridDim.x * blockDim.x) {
+        double f[6];
+        sum_partials(d, nact, pl.S, k, f);
+        if (bad_flags[k]) {
+            for (int c = 0; c < 6; c++) f[c] = __longlong_as_double(0x7ff8000000000000LL);
+        }
+        for (int c = 0; c < 3; c++) {
+            acc[3 * (long long)k + c] = f[c];
+            jerk[3 * (long long)k + c] = f[3 + c];
+        }
+    }
+}
+
+// Once per device, with that device current: the device address of the scratch
+// array and the force-kernel grid.
+int noalloc_setup(int dev, NoAllocDevice **out)
+{
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(nullptr, GD_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoAllocDevice &s = g_noalloc_dev[dev];
+    if (!s.ready) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        int sms = 0, occ_s = 0, occ_u = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, k_force_mixed<true>, FT, 0);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_u, k_force_mixed<false>, FT, 0);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "device query");
+        s.scratch = (unsigned char *)p;
+        s.grid = sms * std::max(1, std::min(occ_s, occ_u));
+        s.ready = true;
+    }
+    *out = &s;
+    return GD_OK;
+}
+
+}  // namespace
+
+extern "C" int gd_force_noalloc(int64_t n, const double *m, const double *x, const double *v, double eps,
+                                const int32_t *idx, int64_t nact, double *acc, double *jerk, void *stream)
+{
+    if (n < 1 || n > NOALLOC_NMAX)
+        return fail(nullptr, GD_EINVAL,
+                    "gd_force_noalloc: n must be in [1, " + std::to_string(NOALLOC_NMAX) + "], got " +
+                        std::to_string((long long)n));
+    if (nact < 1 || nact > n)
+        return fail(nullptr, GD_EINVAL, "gd_force_noalloc: nact must be in [1, n], got " + std::to_string((long long)nact));
+    if (!m || !x || !v || !idx || !acc || !jerk) return fail(nullptr, GD_EINVAL, "gd_force_noalloc: null pointer");
+    if (!(eps >= 0) || !std::isfinite(eps)) return fail(nullptr, GD_EINVAL, "gd_force_noalloc: eps must be finite and >= 0");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
+    NoAllocDevice *s = nullptr;
+    int rc = noalloc_setup(dev, &s);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    Dev d;
+    std::memset(&d, 0, sizeof(d));
+    d.n = (int)n;
+    d.npad = (int)((n + BJ - 1) / BJ * BJ);
+    d.eps2f = (float)(eps * eps);
+    d.eps2 = eps * eps;
+    d.ctrl = (Ctrl *)s->scratch;
+    d.act = (int *)(s->scratch + NA_OFF_ACT);
+    d.jA = (float4 *)(s->scratch + NA_OFF_JA);
+    d.jB = (float4 *)(s->scratch + NA_OFF_JB);
+    d.jC = (float2 *)(s->scratch + NA_OFF_JC);
+    d.part = (double *)(s->scratch + NA_OFF_PART);
+    // the partial area's tail holds the per-slot out-of-range flags: the plan keeps
+    // S * nact <= cap - nact, so they never overlap a partial in use
+    d.cap = NOALLOC_CAP - (long long)n;
+    int *bad = (int *)(d.part + 6 * (size_t)d.cap);
+    const int mode_cut = 192;
+    const int g = (d.npad + 255) / 256;
+    k_noalloc_pack<<<g, 256, 0, st>>>(d, m, x, v, idx, (int)nact, bad);
+    FArgs fa{d, s->grid, mode_cut, 0};
+    if (eps > 0)
+        k_force_mixed<true><<<s->grid, FT, 0, st>>>(fa);
+    else
+        k_force_mixed<false><<<s->grid, FT, 0, st>>>(fa);
+    RArgs ra{d, s->grid, mode_cut, 0, true};
+    k_noalloc_out<<<(int)((nact + 255) / 256), 256, 0, st>>>(ra, bad, acc, jerk);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "gd_force_noalloc launch");
+    return GD_OK;
+}

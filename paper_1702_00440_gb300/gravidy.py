@@ -26,7 +26,7 @@ _PRECISION = {"fp64": GD_FP64, "mixed": GD_MIXED, GD_FP64: GD_FP64, GD_MIXED: GD
 EXPORTS = (
     "gd_opts_default", "gd_init", "gd_evolve", "gd_step_block", "gd_energy", "gd_get_state",
     "gd_set_state", "gd_get_stats", "gd_kernel_time", "gd_free", "gd_last_error", "gd_force",
-    "gd_predict", "gd_active", "gd_replay_step",
+    "gd_predict", "gd_active", "gd_replay_step", "gd_force_noalloc",
 )
 
 
@@ -99,6 +99,7 @@ def load(build_if_missing: bool = True):
             "gd_predict": (ctypes.c_int, [P, I64, P, P]),
             "gd_active": (ctypes.c_int, [P, P, P, P]),
             "gd_replay_step": (ctypes.c_int, [P, I64, P, I64]),
+            "gd_force_noalloc": (ctypes.c_int, [I64, P, P, P, D, P, I64, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -240,6 +241,14 @@ def gd_active(ctx, n):
 def gd_replay_step(ctx, tick, idx):
     idx = np.ascontiguousarray(idx, dtype=np.int32)
     _check(load().gd_replay_step(ctx, int(tick), _p(idx), idx.shape[0]), ctx)
+
+
+def gd_force_noalloc(n, m_ptr, x_ptr, v_ptr, eps, idx_ptr, nact, acc_ptr, jerk_ptr, stream=None):
+    """Allocation-free force/jerk evaluation on caller-owned device buffers
+    (raw device addresses as ints); queues the work on ``stream`` and returns."""
+    rc = load().gd_force_noalloc(int(n), m_ptr, x_ptr, v_ptr, float(eps), idx_ptr, int(nact), acc_ptr, jerk_ptr,
+                                 stream)
+    _check(rc)
 
 
 class Integrator:
