@@ -58,6 +58,7 @@ def _args():
     p.add_argument("--n", type=int, default=N_DEFAULT)
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--no-extras", action="store_true", help="skip the fp64, force-sweep, e2e and cpu legs")
+    p.add_argument("--no-autotune", action="store_true", help="use the default force-kernel tuning table")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="bounded oracle sample length")
     p.add_argument("--sweep-n", type=int, default=1 << 20)
     p.add_argument("--profile-force", type=int, default=0, metavar="N",
@@ -272,7 +273,8 @@ def run_gravidy(a):
         with torch.cuda.stream(stream):
             flush.fill_(1.0)
 
-    g = gravidy.Integrator(m, x, v, EPS, ETA, precision=a.precision, stream=stream.cuda_stream)
+    g = gravidy.Integrator(m, x, v, EPS, ETA, precision=a.precision, stream=stream.cuda_stream,
+                           autotune=not a.no_autotune)
     K0, U0 = g.energy()
     E0 = K0 + U0
     t = 0.0
@@ -327,7 +329,8 @@ def run_gravidy(a):
 
     # ---- roofline of the force kernel: the same workload continued for the
     # same number of steps with CUDA events around every force launch
-    g2 = gravidy.Integrator(m, x, v, EPS, ETA, precision=a.precision, stream=stream.cuda_stream, time_force=True)
+    g2 = gravidy.Integrator(m, x, v, EPS, ETA, precision=a.precision, stream=stream.cuda_stream, time_force=True,
+                            autotune=not a.no_autotune)
     g2.set_state(state_end["x"], state_end["v"], state_end["a"], state_end["j"], state_end["tau"], state_end["dtau"])
     g2.kernel_time()
     t2 = t

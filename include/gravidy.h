@@ -65,9 +65,11 @@ typedef struct gd_opts {
     int32_t use_graph;  /* 1 = run gd_evolve through a captured CUDA graph (default 1) */
     int32_t graph_steps;/* block steps per graph launch, a multiple of 1..64 (default 16) */
     int32_t jsplit;     /* > 0 forces the j-split factor of the force kernel; 0 = tuned */
-    int32_t mode_cut;   /* active count at/above which the i-parallel force mode is used;
-                           0 = tuned default */
+    int32_t mode_cut;   /* active count at/above which the i-parallel force mode is used
+                           (0 = default: 1024 mixed, 256 FP64); per-bucket autotuned choices
+                           override it */
     int32_t time_force; /* 1 = record CUDA events around every force launch (gd_kernel_time) */
+    int32_t autotune;   /* 1 = run gd_autotune(c, 3) at the end of gd_init */
 } gd_opts;
 
 typedef struct gd_stats {
@@ -118,6 +120,21 @@ int gd_get_state(gd_ctx *c, double *x, double *v, double *a, double *jerk, int64
  * [1, dt_max/dt_min] and every tau a non-negative multiple of its dtau. */
 int gd_set_state(gd_ctx *c, const double *x, const double *v, const double *a,
                  const double *jerk, const int64_t *tau, const int64_t *dtau);
+
+/* Force-kernel autotuner: for every active-count bucket floor(log2 N_act) up to
+ * 2^34 interactions, times the force kernel (CUDA events, median of reps
+ * launches, 1 <= reps <= 100) on the current particles for both work
+ * decompositions (i-parallel tiles, warp j-parallel tiles) and a ladder of
+ * j-split factors (the j-range split of Sec. 2.5), and keeps the fastest choice
+ * for later steps.  The integration state is not changed. */
+int gd_autotune(gd_ctx *c, int32_t reps);
+
+/* The tuning table: *mode_cut, and for buckets b < nbuckets (<= 32) the j-split
+ * factor split[b] (0 = rule), the mode mode[b] (0 i-parallel, 1 warp, -1 rule)
+ * and the autotuner's best force-kernel time ms[b] for N_act = 2^b (0 = not
+ * measured).  Any pointer may be NULL. */
+int gd_get_tuning(gd_ctx *c, int32_t *mode_cut, int16_t *split, int8_t *mode, float *ms,
+                  int32_t nbuckets);
 
 /* Counters since gd_init. */
 int gd_get_stats(gd_ctx *c, gd_stats *s);

@@ -29,7 +29,7 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = SRC + [os.path.join(INCLUDE, "gravidy.h")]
+    deps = SRC + [os.path.join(INCLUDE, "gravidy.h"), os.path.join(HERE, "csrc", "kernels.cuh")]
     return any(os.path.getmtime(p) > t for p in deps)
 
 

@@ -1,0 +1,1083 @@
+// kernels.cuh -- device code of the GB300 Hermite-4 block-time-step integrator
+// (GraviDy, arXiv 1702.00440).  Included once, by gravidy.cu.
+//
+// One block step (Sec. 2.4 steps 5-7) is three kernels and no host round trip:
+//   k_select_predict  predict every particle to the block time (step 7a) and list
+//                     the active ones in ascending index order (step 5) with a
+//                     single-pass decoupled look-back scan; start the minimum of
+//                     the next block time over the inactive ones.
+//   k_force_*         force and jerk of the active set against all N predicted
+//                     particles (step 7c, Sec. 2.5): a persistent kernel over
+//                     (i-tile x j-chunk) work items; the j-range is split when the
+//                     active set is small, and the last CTA to finish an i-tile
+//                     sums its partials (step 7c-iii).
+//   k_correct         correct (7d), take Aarseth's step (Sec. 3.2), quantise it to
+//                     the block scheme, keep the new force (step 6), and finish the
+//                     minimum that gives the next block time.
+//
+// Cost model that shapes the code: on this GPU an FP64 warp instruction holds an
+// SMSP for about 78 cycles whether 1 or 32 lanes are active, while an FP32 one
+// issues every cycle.  So FP64 appears only where the method needs it (prediction,
+// correction, step selection, energy sums, the FP64 path), every FP64 instruction
+// works on as many particles or components as possible, and the mixed force path
+// keeps its sums in FP32 with compensated (two-sum) accumulation.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdint>
+
+namespace gdk {
+
+// ---------------------------------------------------------------- constants
+
+constexpr int FT = 128;                      // force kernel threads per CTA
+constexpr int BJ = 128;                      // j-tile, and padding granule of the j-arrays
+constexpr int BJ64 = 64;                     // FP64 i-parallel mode j-tile
+constexpr int ITILE_A_MIX = 2 * FT;          // mixed i-parallel: 2 active particles per thread
+constexpr int ITILE_A_64 = FT;               // FP64 i-parallel: 1 per thread
+constexpr int ITILE_B_MIX = 2 * (FT / 32);   // mixed warp mode: 2 per warp, lanes split j
+constexpr int ITILE_B_64 = FT / 32;          // FP64 warp mode: 1 per warp
+constexpr int FOLD_B = 16;                   // warp mode: j-iterations per lane between folds
+constexpr int ST = 128;                      // select/predict threads per CTA (= particles per chunk)
+constexpr int CT = 128;                      // corrector threads per CTA
+constexpr int ET = 128;                      // energy threads per CTA
+constexpr int SPIN_LIMIT = 1 << 22;          // bounded device waits
+constexpr float PAD_FAR_F = 1.0e18f;
+constexpr double PAD_FAR_D = 1.0e30;
+
+// status codes written to the device flag (same values as gd_status)
+constexpr int ST_EINVAL = -1, ST_ENONFINITE = -4, ST_ETIMEOUT = -5, ST_ESTATE = -6;
+
+// ---------------------------------------------------------------- control block
+
+struct Ctrl {
+    long long T_cur;       // block time of the next step (ticks)
+    long long T_acc;       // running minimum of next times, for the step after it
+    long long T_last;      // block time of the last finished step
+    long long tick_end;    // steps whose block time is above this are skipped
+    long long nblock;      // block steps
+    long long nsteps;      // particle steps
+    double interactions;   // sum of nact * n
+    double K, U;           // energy results
+    int nact;              // active count of the current step
+    int last_nact;
+    unsigned int epoch;    // look-back tag, advanced once per step
+    unsigned int done;     // finished-CTA counter of k_correct
+    int err;               // first device-side fault (gd_status), 0 = none
+    int pad_;
+};
+
+__device__ __forceinline__ void set_err(Ctrl *c, int code) { atomicCAS(&c->err, 0, code); }
+
+// ---------------------------------------------------------------- tuning table
+
+// Force work decomposition, chosen by the autotuner (or defaults).
+struct Tune {
+    int mode_cut;             // N_act >= mode_cut: i-parallel mode, else warp mode
+    int jchunk_min;           // smallest j-chunk of a split (multiple of BJ)
+    int items_x4;             // target work items = grid * items_x4 / 4
+    short s_fixed[32];        // per floor(log2 N_act): > 0 forces the j-split factor
+    signed char mode_b[32];   // per floor(log2 N_act): 0 / 1 forces the mode, -1 = mode_cut
+};
+
+// ---------------------------------------------------------------- device state
+
+struct Dev {
+    int n, npad;
+    double dt_min, inv_dt_min, dt_min2;
+    long long dtau_max;
+    double eta;
+    double eps2;
+    float eps2f;
+    // FP64 state at each particle's own time, structure of arrays (plane c at +c*n)
+    double *x, *v, *a, *jk, *m;
+    long long *tau, *dtau, *tnext;
+    // predicted j-records, mixed: A = (x_hi, y_hi, z_hi, m), B = (x_lo, y_lo, z_lo, vx),
+    // C = (vy, vz); padded to npad with massless far-away particles
+    float4 *jA, *jB;
+    float2 *jC;
+    // predicted j-records, FP64: 7 planes of npad (x, y, z, vx, vy, vz, m)
+    double *pd;
+    int *act;                 // active list
+    void *part;               // j-split partials (float mixed, double FP64), (s*6 + c)*nact + k
+    long long cap;            // partial capacity (entries per component)
+    double *fsum;             // summed force of active slot k: fsum[c*n + k], c < 3 a, c >= 3 jerk
+    unsigned int *tilecnt;    // per i-tile arrival counters (zero between launches)
+    unsigned long long *status;  // look-back words, one per chunk of ST particles
+    double *eu, *ek;          // per-particle energy terms
+    int *nact_hist;           // nact of each step slot of a captured graph
+    Ctrl *ctrl;
+};
+
+// ---------------------------------------------------------------- force plan
+
+struct Plan {
+    int mode;     // 0 = i-parallel, 1 = warp j-parallel
+    int itile;    // active particles per work item
+    int itiles;
+    int S;        // j-split factor
+    int chunk;    // j per split (multiple of BJ)
+    long long items;
+};
+
+__host__ __device__ inline int ilog2_floor(int x)
+{
+    int l = 0;
+    while (x > 1) {
+        x >>= 1;
+        l++;
+    }
+    return l;
+}
+
+__host__ __device__ inline Plan make_plan(int nact, int npad, int grid, const Tune &tn, bool mixed, long long cap)
+{
+    Plan p;
+    const int b = nact > 0 ? ilog2_floor(nact) : 0;
+    const int mb = tn.mode_b[b < 32 ? b : 31];
+    p.mode = mb >= 0 ? mb : (nact >= tn.mode_cut ? 0 : 1);
+    p.itile = p.mode == 0 ? (mixed ? ITILE_A_MIX : ITILE_A_64) : (mixed ? ITILE_B_MIX : ITILE_B_64);
+    p.itiles = (nact + p.itile - 1) / p.itile;
+    if (p.itiles < 1) p.itiles = 1;
+    long long S = tn.s_fixed[b < 32 ? b : 31];
+    if (S <= 0) {
+        const long long target = (long long)grid * tn.items_x4 / 4;
+        S = (target + p.itiles - 1) / p.itiles;
+    }
+    long long smax = npad / (tn.jchunk_min > BJ ? tn.jchunk_min : BJ);
+    if (smax < 1) smax = 1;
+    if (S > smax) S = smax;
+    if (S < 1) S = 1;
+    if (nact > 0 && S * (long long)nact > cap) S = cap / nact;
+    if (S < 1) S = 1;
+    const int tiles = npad / BJ;
+    const int tpc = (int)((tiles + S - 1) / S);
+    p.chunk = tpc * BJ;
+    p.S = (tiles + tpc - 1) / tpc;
+    p.items = (long long)p.itiles * p.S;
+    return p;
+}
+
+// ---------------------------------------------------------------- small helpers
+
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ unsigned long long lb_pack(unsigned epoch, unsigned flag, unsigned val)
+{
+    return ((unsigned long long)(epoch & 0x3FFFFFFFu) << 34) | ((unsigned long long)flag << 32) | val;
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long *p)
+{
+    return *(const volatile unsigned long long *)p;
+}
+
+__device__ __forceinline__ long long warp_min_ll(long long v)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w < v ? w : v;
+    }
+    return v;
+}
+
+// Compensated FP32 accumulator: h + l carries the running sum to about twice the
+// float precision; each add is Knuth's two-sum of h and the addend, with the
+// rounding error collected in l.
+struct DS {
+    float h, l;
+    __device__ __forceinline__ void zero()
+    {
+        h = 0.f;
+        l = 0.f;
+    }
+    __device__ __forceinline__ void add(float f)
+    {
+        const float s = h + f;
+        const float bb = s - h;
+        const float e = (h - (s - bb)) + (f - bb);
+        l += e;
+        h = s;
+    }
+    __device__ __forceinline__ float as_float() const { return h + l; }
+    __device__ __forceinline__ double as_double() const { return (double)h + (double)l; }
+};
+
+// Taylor prediction of particle i over dt (Sec. 2.4 step 7a), FP64.
+__device__ __forceinline__ void predict64(const Dev &d, int i, double dt, double xp[3], double vp[3])
+{
+    const int n = d.n;
+    const double h2 = 0.5 * dt * dt, h3 = dt * dt * dt * (1.0 / 6.0);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const double x0 = d.x[c * n + i], v0 = d.v[c * n + i], a0 = d.a[c * n + i], j0 = d.jk[c * n + i];
+        xp[c] = fma(j0, h3, fma(a0, h2, fma(v0, dt, x0)));
+        vp[c] = fma(j0, h2, fma(a0, dt, v0));
+    }
+}
+
+// Store the predicted particle as the record the force kernel reads.
+template <bool MIXED>
+__device__ __forceinline__ void store_jrec(const Dev &d, int i, const double xp[3], const double vp[3], double mi)
+{
+    if (MIXED) {
+        const float h0 = __double2float_rn(xp[0]), h1 = __double2float_rn(xp[1]), h2 = __double2float_rn(xp[2]);
+        const float l0 = __double2float_rn(xp[0] - (double)h0);
+        const float l1 = __double2float_rn(xp[1] - (double)h1);
+        const float l2 = __double2float_rn(xp[2] - (double)h2);
+        d.jA[i] = make_float4(h0, h1, h2, __double2float_rn(mi));
+        d.jB[i] = make_float4(l0, l1, l2, __double2float_rn(vp[0]));
+        d.jC[i] = make_float2(__double2float_rn(vp[1]), __double2float_rn(vp[2]));
+    } else {
+        const int np = d.npad;
+        d.pd[0 * np + i] = xp[0];
+        d.pd[1 * np + i] = xp[1];
+        d.pd[2 * np + i] = xp[2];
+        d.pd[3 * np + i] = vp[0];
+        d.pd[4 * np + i] = vp[1];
+        d.pd[5 * np + i] = vp[2];
+        d.pd[6 * np + i] = mi;
+    }
+}
+
+// ---------------------------------------------------------------- kernel: select + predict
+
+// Predicts every particle to T = ctrl->T_cur and writes the ascending list of the
+// particles whose next time equals T.  The grid never exceeds the number of CTAs
+// that can be resident at once, and each CTA walks its chunks in increasing order,
+// so a chunk's look-back only waits on chunks that are being or have been
+// processed; every wait is bounded.  `slot` >= 0 records nact in nact_hist[slot].
+template <bool MIXED>
+__global__ void __launch_bounds__(ST) k_select_predict(Dev d, int slot, int nchunks)
+{
+    Ctrl *ctrl = d.ctrl;
+    const long long T = ctrl->T_cur;
+    if (T > ctrl->tick_end) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            ctrl->nact = 0;
+            if (slot >= 0) d.nact_hist[slot] = 0;
+        }
+        return;
+    }
+    __shared__ unsigned s_excl;
+    __shared__ unsigned s_wcnt[ST / 32];
+    __shared__ long long s_wmin[ST / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned ep = ctrl->epoch & 0x3FFFFFFFu;
+    long long mn_all = LLONG_MAX;
+    for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+        const int i = chunk * ST + threadIdx.x;
+        bool act = false;
+        if (i < d.n) {
+            const long long tn = d.tnext[i];
+            act = (tn == T);
+            if (!act) mn_all = tn < mn_all ? tn : mn_all;
+            const double dt = (double)(T - d.tau[i]) * d.dt_min;
+            double xp[3], vp[3];
+            predict64(d, i, dt, xp, vp);
+            store_jrec<MIXED>(d, i, xp, vp, d.m[i]);
+        }
+        const unsigned ballot = __ballot_sync(0xffffffffu, act);
+        if (lane == 0) s_wcnt[warp] = __popc(ballot);
+        __syncthreads();
+        if (warp == 0) {
+            const unsigned cnt = lane < ST / 32 ? s_wcnt[lane] : 0u;
+            unsigned incl = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+            if (lane < ST / 32) s_wcnt[lane] = incl - cnt;  // exclusive offsets
+            unsigned excl = 0;
+            if (chunk == 0) {
+                if (lane == 0) atomicExch(&d.status[0], lb_pack(ep, 2u, total));
+            } else {
+                if (lane == 0) atomicExch(&d.status[chunk], lb_pack(ep, 1u, total));
+                int base = chunk - 1;
+                int spins = 0;
+                for (;;) {
+                    const int p = base - lane;
+                    unsigned f = 2u, val = 0u;
+                    if (p >= 0) {
+                        const unsigned long long w = ld_volatile_u64(&d.status[p]);
+                        f = ((unsigned)(w >> 34) == ep) ? (unsigned)((w >> 32) & 3u) : 0u;
+                        val = (unsigned)w;
+                    }
+                    const unsigned notready = __ballot_sync(0xffffffffu, f == 0u);
+                    const unsigned prefix = __ballot_sync(0xffffffffu, f == 2u);
+                    const int first = prefix ? __ffs(prefix) - 1 : 31;
+                    const unsigned need = first == 31 ? 0xffffffffu : ((2u << first) - 1u);
+                    if (notready & need) {
+                        if (++spins > SPIN_LIMIT) {
+                            if (lane == 0) set_err(ctrl, ST_ETIMEOUT);
+                            break;
+                        }
+                        __nanosleep(32);
+                        continue;
+                    }
+                    unsigned contrib = lane <= first ? val : 0u;
+                    for (int o = 16; o > 0; o >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
+                    excl += contrib;
+                    if (prefix) break;
+                    base -= 32;
+                }
+                if (lane == 0) atomicExch(&d.status[chunk], lb_pack(ep, 2u, excl + total));
+            }
+            if (lane == 0) {
+                s_excl = excl;
+                if (chunk == nchunks - 1) {
+                    int na = (int)(excl + total);
+                    if (excl + total > (unsigned)d.n) {
+                        set_err(ctrl, ST_ETIMEOUT);
+                        na = 0;
+                    }
+                    ctrl->nact = na;
+                    if (slot >= 0) d.nact_hist[slot] = na;
+                }
+            }
+        }
+        __syncthreads();
+        if (act) {
+            const unsigned pos = s_excl + s_wcnt[warp] + __popc(ballot & ((1u << lane) - 1u));
+            if (pos < (unsigned)d.n) d.act[pos] = i;
+        }
+        __syncthreads();
+    }
+    // minimum next time of the inactive particles -> next block time candidate
+    long long mn = warp_min_ll(mn_all);
+    if (lane == 0) s_wmin[warp] = mn;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < ST / 32; w++) mn = s_wmin[w] < mn ? s_wmin[w] : mn;
+        if (mn != LLONG_MAX) atomicMin((unsigned long long *)&ctrl->T_acc, (unsigned long long)mn);
+    }
+}
+
+// Predict all particles to `tick` (no selection): the hooks and gd_energy.
+template <bool MIXED>
+__global__ void k_predict_all(Dev d, long long tick)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.n) return;
+    const double dt = (double)(tick - d.tau[i]) * d.dt_min;
+    double xp[3], vp[3];
+    predict64(d, i, dt, xp, vp);
+    store_jrec<MIXED>(d, i, xp, vp, d.m[i]);
+}
+
+// Padding records: massless particles far away, so the inner loops need no tail test.
+__global__ void k_init_pads(Dev d)
+{
+    const int i = d.n + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.npad) return;
+    d.jA[i] = make_float4(PAD_FAR_F, PAD_FAR_F, PAD_FAR_F, 0.f);
+    d.jB[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    d.jC[i] = make_float2(0.f, 0.f);
+    const int np = d.npad;
+    d.pd[0 * np + i] = PAD_FAR_D;
+    d.pd[1 * np + i] = PAD_FAR_D;
+    d.pd[2 * np + i] = PAD_FAR_D;
+    d.pd[3 * np + i] = 0.0;
+    d.pd[4 * np + i] = 0.0;
+    d.pd[5 * np + i] = 0.0;
+    d.pd[6 * np + i] = 0.0;
+}
+
+// ---------------------------------------------------------------- pair interactions
+
+// One softened pair term (Sec. 2.4, softened Eq. 1, and its time derivative) in FP32
+// on double-single positions: r = x_j - x_i from the hi and lo parts separately, so
+// the difference keeps the bits of the FP64 positions.
+//   a += m r / s^3,   jerk += m (v - 3 (r.v) r / s^2) / s^3,   s^2 = r^2 + eps^2
+template <bool SOFT>
+__device__ __forceinline__ void pair_mixed(const float4 A, const float4 B, const float2 C, const float xh,
+                                           const float yh, const float zh, const float xl, const float yl,
+                                           const float zl, const float vx, const float vy, const float vz,
+                                           const float eps2, float f[6])
+{
+    const float dx = (A.x - xh) + (B.x - xl);
+    const float dy = (A.y - yh) + (B.y - yl);
+    const float dz = (A.z - zh) + (B.z - zl);
+    const float dvx = B.w - vx, dvy = C.x - vy, dvz = C.y - vz;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+    const float rv = fmaf(dx, dvx, fmaf(dy, dvy, dz * dvz));
+    float rinv = rsqrt_approx(r2);
+    if (!SOFT) rinv = r2 > 0.f ? rinv : 0.f;
+    const float rinv2 = rinv * rinv;
+    const float mr3 = A.w * rinv * rinv2;
+    const float b = -3.f * rv * rinv2;
+    f[0] = fmaf(mr3, dx, f[0]);
+    f[1] = fmaf(mr3, dy, f[1]);
+    f[2] = fmaf(mr3, dz, f[2]);
+    f[3] = fmaf(mr3, fmaf(b, dx, dvx), f[3]);
+    f[4] = fmaf(mr3, fmaf(b, dy, dvy), f[4]);
+    f[5] = fmaf(mr3, fmaf(b, dz, dvz), f[5]);
+}
+
+template <bool SOFT>
+__device__ __forceinline__ void pair_fp64(const double xj, const double yj, const double zj, const double vxj,
+                                          const double vyj, const double vzj, const double mj, const double xi,
+                                          const double yi, const double zi, const double vxi, const double vyi,
+                                          const double vzi, const double eps2, double f[6])
+{
+    const double dx = xj - xi, dy = yj - yi, dz = zj - zi;
+    const double dvx = vxj - vxi, dvy = vyj - vyi, dvz = vzj - vzi;
+    const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+    const double rv = fma(dx, dvx, fma(dy, dvy, dz * dvz));
+    double rinv = rsqrt(r2);
+    if (!SOFT) rinv = r2 > 0.0 ? rinv : 0.0;
+    const double rinv2 = rinv * rinv;
+    const double mr3 = mj * rinv * rinv2;
+    const double b = -3.0 * rv * rinv2;
+    f[0] = fma(mr3, dx, f[0]);
+    f[1] = fma(mr3, dy, f[1]);
+    f[2] = fma(mr3, dz, f[2]);
+    f[3] = fma(mr3, fma(b, dx, dvx), f[3]);
+    f[4] = fma(mr3, fma(b, dy, dvy), f[4]);
+    f[5] = fma(mr3, fma(b, dz, dvz), f[5]);
+}
+
+struct FArgs {
+    Dev d;
+    int grid;
+    Tune tn;
+};
+
+// ---------------------------------------------------------------- j-split reduction
+
+template <class P>
+__device__ __forceinline__ void store_partial(const Dev &d, int nact, int s, int k, const P f[6])
+{
+    P *p = (P *)d.part + (long long)s * 6 * nact + k;
+#pragma unroll
+    for (int c = 0; c < 6; c++) p[(long long)c * nact] = f[c];
+}
+
+template <class P>
+struct Acc;
+template <>
+struct Acc<float> {
+    DS v;
+    __device__ void zero() { v.zero(); }
+    __device__ void add(float f) { v.add(f); }
+    __device__ void add(const Acc &o)
+    {
+        v.add(o.v.h);
+        v.add(o.v.l);
+    }
+    __device__ double value() const { return v.as_double(); }
+};
+template <>
+struct Acc<double> {
+    double v;
+    __device__ void zero() { v = 0.0; }
+    __device__ void add(double f) { v += f; }
+    __device__ void add(const Acc &o) { v += o.v; }
+    __device__ double value() const { return v; }
+};
+
+// a += p[s * stride] for s = s0, s0 + ds, ... < S, in that order, with eight loads
+// in flight (the partials come from L2).
+template <class P>
+__device__ __forceinline__ void sum_strided(Acc<P> &a, const P *p, long long stride, int s0, int S, int ds)
+{
+    int s = s0;
+    for (; s + 7 * ds < S; s += 8 * ds) {
+        P v[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) v[u] = __ldcg(p + (long long)(s + u * ds) * stride);
+#pragma unroll
+        for (int u = 0; u < 8; u++) a.add(v[u]);
+    }
+    for (; s < S; s += ds) a.add(__ldcg(p + (long long)s * stride));
+}
+
+// Sums the S partials of slots [k0, k0 + nvalid) into fsum, in a fixed order
+// (deterministic whichever CTA arrives last).  Partials written by other CTAs are
+// read through L2 (__ldcg).
+template <class P>
+__device__ void tile_reduce(const Dev &d, int nact, int S, int k0, int nvalid)
+{
+    __shared__ Acc<P> s_acc[FT];
+    const P *part = (const P *)d.part;
+    const int npairs = nvalid * 6;
+    const int t = threadIdx.x;
+    const int G = npairs >= FT ? 1 : FT / npairs;  // threads per (slot, component) pair
+    if (G == 1) {
+        for (int pidx = t; pidx < npairs; pidx += FT) {
+            const int c = pidx / nvalid, k = k0 + pidx % nvalid;
+            Acc<P> a;
+            a.zero();
+            sum_strided<P>(a, part + (long long)c * nact + k, 6LL * nact, 0, S, 1);
+            d.fsum[(long long)c * d.n + k] = a.value();
+        }
+    } else {
+        const int pidx = t / G, sub = t % G;
+        Acc<P> a;
+        a.zero();
+        if (pidx < npairs) {
+            const int c = pidx / nvalid, k = k0 + pidx % nvalid;
+            sum_strided<P>(a, part + (long long)c * nact + k, 6LL * nact, sub, S, G);
+        }
+        s_acc[t] = a;
+        __syncthreads();
+        if (pidx < npairs && sub == 0) {
+            for (int q = 1; q < G; q++) a.add(s_acc[t + q]);
+            const int c = pidx / nvalid, k = k0 + pidx % nvalid;
+            d.fsum[(long long)c * d.n + k] = a.value();
+        }
+    }
+}
+
+// After a CTA has stored its partials for i-tile `it`: the last of the S CTAs of
+// that tile reduces them.  The counter returns to zero for the next launch.
+template <class P>
+__device__ __forceinline__ void finish_item(const Dev &d, int nact, const Plan &pl, int it)
+{
+    __shared__ int s_last;
+    // the barrier gathers this CTA's partial stores; thread 0's fence releases them
+    // before the arrival is counted
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&d.tilecnt[it], 1u);
+        s_last = prev == (unsigned)(pl.S - 1);
+        if (s_last) d.tilecnt[it] = 0u;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        const int k0 = it * pl.itile;
+        const int nvalid = min(pl.itile, nact - k0);
+        tile_reduce<P>(d, nact, pl.S, k0, nvalid);
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- kernel: force (mixed)
+
+template <bool SOFT>
+__global__ void __launch_bounds__(FT, 4) k_force_mixed(FArgs fa)
+{
+    const Dev &d = fa.d;
+    const int nact = min(d.ctrl->nact, d.n);
+    if (nact <= 0) return;
+    const Plan pl = make_plan(nact, d.npad, fa.grid, fa.tn, true, d.cap);
+    const float eps2 = d.eps2f;
+    __shared__ float4 sA[BJ], sB[BJ];
+    __shared__ float2 sC[BJ];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (long long item = blockIdx.x; item < pl.items; item += gridDim.x) {
+        const int it = (int)(item / pl.S), s = (int)(item % pl.S);
+        const int jbeg = s * pl.chunk;
+        const int jend = min(jbeg + pl.chunk, d.npad);
+        if (pl.mode == 0) {
+            // i-parallel: thread t owns active slots k0 and k1; j-tiles staged in shared memory
+            const int k0 = it * ITILE_A_MIX + t, k1 = k0 + FT;
+            const int i0 = d.act[min(k0, nact - 1)], i1 = d.act[min(k1, nact - 1)];
+            const float4 A0 = d.jA[i0], B0 = d.jB[i0];
+            const float2 C0 = d.jC[i0];
+            const float4 A1 = d.jA[i1], B1 = d.jB[i1];
+            const float2 C1 = d.jC[i1];
+            const bool busy = it * ITILE_A_MIX + warp * 32 < nact;  // the warp has a real slot
+            DS g0[6], g1[6];
+#pragma unroll
+            for (int c = 0; c < 6; c++) {
+                g0[c].zero();
+                g1[c].zero();
+            }
+            for (int jt = jbeg; jt < jend; jt += BJ) {
+                __syncthreads();
+                sA[t] = d.jA[jt + t];
+                sB[t] = d.jB[jt + t];
+                sC[t] = d.jC[jt + t];
+                __syncthreads();
+                if (busy) {
+                    float f0[6] = {0, 0, 0, 0, 0, 0}, f1[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll 4
+                    for (int jj = 0; jj < BJ; jj++) {
+                        const float4 A = sA[jj], B = sB[jj];
+                        const float2 C = sC[jj];
+                        pair_mixed<SOFT>(A, B, C, A0.x, A0.y, A0.z, B0.x, B0.y, B0.z, B0.w, C0.x, C0.y, eps2, f0);
+                        pair_mixed<SOFT>(A, B, C, A1.x, A1.y, A1.z, B1.x, B1.y, B1.z, B1.w, C1.x, C1.y, eps2, f1);
+                    }
+#pragma unroll
+                    for (int c = 0; c < 6; c++) {
+                        g0[c].add(f0[c]);
+                        g1[c].add(f1[c]);
+                    }
+                }
+            }
+            float r0[6], r1[6];
+#pragma unroll
+            for (int c = 0; c < 6; c++) {
+                r0[c] = g0[c].as_float();
+                r1[c] = g1[c].as_float();
+            }
+            if (k0 < nact) store_partial<float>(d, nact, s, k0, r0);
+            if (k1 < nact) store_partial<float>(d, nact, s, k1, r1);
+        } else {
+            // warp j-parallel: warp w owns slots k0, k0+1; its lanes split the j-chunk
+            const int k0 = it * ITILE_B_MIX + 2 * warp;
+            if (k0 < nact) {
+                const bool has1 = k0 + 1 < nact;
+                const int i0 = d.act[k0], i1 = d.act[has1 ? k0 + 1 : k0];
+                const float4 A0 = d.jA[i0], B0 = d.jB[i0];
+                const float2 C0 = d.jC[i0];
+                const float4 A1 = d.jA[i1], B1 = d.jB[i1];
+                const float2 C1 = d.jC[i1];
+                DS g0[6], g1[6];
+#pragma unroll
+                for (int c = 0; c < 6; c++) {
+                    g0[c].zero();
+                    g1[c].zero();
+                }
+                for (int jb = jbeg; jb < jend; jb += 32 * FOLD_B) {
+                    const int je = min(jb + 32 * FOLD_B, jend);
+                    float f0[6] = {0, 0, 0, 0, 0, 0}, f1[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll 4
+                    for (int j = jb + lane; j < je; j += 32) {
+                        const float4 A = __ldg(&d.jA[j]), B = __ldg(&d.jB[j]);
+                        const float2 C = __ldg(&d.jC[j]);
+                        pair_mixed<SOFT>(A, B, C, A0.x, A0.y, A0.z, B0.x, B0.y, B0.z, B0.w, C0.x, C0.y, eps2, f0);
+                        pair_mixed<SOFT>(A, B, C, A1.x, A1.y, A1.z, B1.x, B1.y, B1.z, B1.w, C1.x, C1.y, eps2, f1);
+                    }
+#pragma unroll
+                    for (int c = 0; c < 6; c++) {
+                        g0[c].add(f0[c]);
+                        g1[c].add(f1[c]);
+                    }
+                }
+                float r0[6], r1[6];
+#pragma unroll
+                for (int c = 0; c < 6; c++) {
+                    r0[c] = g0[c].as_float();
+                    r1[c] = g1[c].as_float();
+                    for (int o = 16; o > 0; o >>= 1) {
+                        r0[c] += __shfl_xor_sync(0xffffffffu, r0[c], o);
+                        r1[c] += __shfl_xor_sync(0xffffffffu, r1[c], o);
+                    }
+                }
+                if (lane == 0) {
+                    store_partial<float>(d, nact, s, k0, r0);
+                    if (has1) store_partial<float>(d, nact, s, k0 + 1, r1);
+                }
+            }
+        }
+        finish_item<float>(d, nact, pl, it);
+    }
+}
+
+// ---------------------------------------------------------------- kernel: force (FP64)
+
+template <bool SOFT>
+__global__ void __launch_bounds__(FT, 4) k_force_fp64(FArgs fa)
+{
+    const Dev &d = fa.d;
+    const int nact = min(d.ctrl->nact, d.n);
+    if (nact <= 0) return;
+    const Plan pl = make_plan(nact, d.npad, fa.grid, fa.tn, false, d.cap);
+    const double eps2 = d.eps2;
+    const int np = d.npad;
+    const double *P = d.pd;
+    __shared__ double sP[7][BJ64];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (long long item = blockIdx.x; item < pl.items; item += gridDim.x) {
+        const int it = (int)(item / pl.S), s = (int)(item % pl.S);
+        const int jbeg = s * pl.chunk;
+        const int jend = min(jbeg + pl.chunk, np);
+        if (pl.mode == 0) {
+            const int k = it * ITILE_A_64 + t;
+            const int i = d.act[min(k, nact - 1)];
+            const double xi = P[i], yi = P[np + i], zi = P[2 * np + i];
+            const double vxi = P[3 * np + i], vyi = P[4 * np + i], vzi = P[5 * np + i];
+            const bool busy = it * ITILE_A_64 + warp * 32 < nact;
+            double g[6] = {0, 0, 0, 0, 0, 0};
+            for (int jt = jbeg; jt < jend; jt += BJ64) {
+                __syncthreads();
+                for (int q = t; q < 7 * BJ64; q += FT) {
+                    const int c = q / BJ64, jj = q % BJ64;
+                    sP[c][jj] = P[(long long)c * np + jt + jj];
+                }
+                __syncthreads();
+                if (busy) {
+#pragma unroll 2
+                    for (int jj = 0; jj < BJ64; jj++)
+                        pair_fp64<SOFT>(sP[0][jj], sP[1][jj], sP[2][jj], sP[3][jj], sP[4][jj], sP[5][jj], sP[6][jj],
+                                        xi, yi, zi, vxi, vyi, vzi, eps2, g);
+                }
+            }
+            if (k < nact) store_partial<double>(d, nact, s, k, g);
+        } else {
+            const int k = it * ITILE_B_64 + warp;
+            if (k < nact) {
+                const int i = d.act[k];
+                const double xi = P[i], yi = P[np + i], zi = P[2 * np + i];
+                const double vxi = P[3 * np + i], vyi = P[4 * np + i], vzi = P[5 * np + i];
+                double g[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll 2
+                for (int j = jbeg + lane; j < jend; j += 32)
+                    pair_fp64<SOFT>(__ldg(&P[j]), __ldg(&P[np + j]), __ldg(&P[2 * np + j]), __ldg(&P[3 * np + j]),
+                                    __ldg(&P[4 * np + j]), __ldg(&P[5 * np + j]), __ldg(&P[6 * np + j]), xi, yi, zi,
+                                    vxi, vyi, vzi, eps2, g);
+#pragma unroll
+                for (int c = 0; c < 6; c++)
+                    for (int o = 16; o > 0; o >>= 1) g[c] += __shfl_xor_sync(0xffffffffu, g[c], o);
+                if (lane == 0) store_partial<double>(d, nact, s, k, g);
+            }
+        }
+        finish_item<double>(d, nact, pl, it);
+    }
+}
+
+// ---------------------------------------------------------------- corrector + time step
+
+// The power-of-two block step after a correction at tick T, from the Aarseth
+// estimate dt_new^2 = num / den (Sec. 3.2) with num = eta (|a1||a2e| + |j1|^2) and
+// den = |j1||a3| + |a2e|^2.  Rules (same as the initial quantisation): steps are
+// powers of two of dt_min in [1, dtau_max] ticks; shrink to the largest power of two
+// not above dt_new; grow by 2 only if dt_new >= 2 dt_old at a time that is a
+// multiple of twice the old step.  dt_new = Inf or NaN (an isolated particle)
+// counts as unconstrained.  The decisions compare num with den times exact powers
+// of two, so no FP64 divide or square root is needed; floor(log2(num / D)) is read
+// off the binary exponents and a mantissa comparison.
+__device__ __forceinline__ long long next_block_step(const Dev &d, double num, double den, long long dtau_old,
+                                                     long long T)
+{
+    const bool unconstrained = !(den > 0.0) || !(num == num) || isinf(num);
+    if (!unconstrained) {
+        if (!(num > 0.0)) return 1;  // dt_new = 0
+        const double dto = (double)dtau_old * d.dt_min;
+        const double lim = dto * dto * den;
+        if (num < lim) {
+            const double D = den * d.dt_min2;  // exact: dt_min^2 is a power of two
+            int fl;
+            if (D >= 2.2250738585072014e-308 && num >= 2.2250738585072014e-308) {
+                const long long bn = __double_as_longlong(num), bd = __double_as_longlong(D);
+                const int en = (int)((bn >> 52) & 0x7FF), ed = (int)((bd >> 52) & 0x7FF);
+                const long long mn = bn & 0xFFFFFFFFFFFFFLL, md = bd & 0xFFFFFFFFFFFFFLL;
+                fl = en - ed - (mn < md ? 1 : 0);
+            } else {
+                const double q = num / D;
+                fl = (int)((__double_as_longlong(q) >> 52) & 0x7FF) - 1023;
+            }
+            const int lvl = fl >> 1;  // floor(fl / 2)
+            if (lvl < 0) return 1;
+            return 1LL << lvl;
+        }
+        if (!(num >= 4.0 * lim)) return dtau_old;
+    }
+    if (2 * dtau_old <= d.dtau_max && (T & (2 * dtau_old - 1)) == 0) return 2 * dtau_old;
+    return dtau_old;
+}
+
+struct CArgs {
+    Dev d;
+};
+
+// Corrects every active particle and (last CTA) turns the running minimum into the
+// next block time.  Four lanes per particle: lanes 0-2 take the x, y, z components
+// (prediction, Hermite derivatives, correction), the squared norms of the Aarseth
+// criterion are summed across the four lanes, and lanes 0 and 1 take its two
+// square roots side by side.
+__global__ void __launch_bounds__(CT) k_correct(CArgs ca)
+{
+    const Dev &d = ca.d;
+    Ctrl *ctrl = d.ctrl;
+    const int nact = min(ctrl->nact, d.n);
+    if (nact <= 0) return;
+    const long long T = ctrl->T_cur;
+    const int n = d.n;
+    const int lane = threadIdx.x & 31;
+    const int q = lane & 3;
+    const int c = q < 3 ? q : 2;
+    const bool real = q < 3;
+    const int gwarp = (blockIdx.x * CT + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * CT) >> 5;
+    long long mymin = LLONG_MAX;
+    int bad = 0;
+    for (int kw = gwarp * 8; kw < nact; kw += nwarps * 8) {
+        const int k = kw + (lane >> 2);
+        const bool valid = k < nact;
+        const int i = d.act[valid ? k : nact - 1];
+        const long long tau0 = d.tau[i];
+        const long long dtau_old = d.dtau[i];
+        const long long dtick = T - tau0;
+        const bool behind = dtick > 0;
+        const double dt = (double)dtick * d.dt_min;
+        double idt;
+        if (behind && (dtick & (dtick - 1)) == 0) {
+            const int e = 63 - __clzll(dtick);
+            idt = d.inv_dt_min * __longlong_as_double((long long)(1023 - e) << 52);
+        } else {
+            idt = 1.0 / dt;
+        }
+        const double dt2 = dt * dt, dt3 = dt2 * dt, dt4 = dt3 * dt, dt5 = dt4 * dt;
+        const double idt2 = idt * idt, idt3 = idt2 * idt;
+        const double h2 = 0.5 * dt2, h3 = dt3 * (1.0 / 6.0), h4 = dt4 * (1.0 / 24.0), h5 = dt5 * (1.0 / 120.0);
+        const double x0 = d.x[c * n + i], v0 = d.v[c * n + i], a0 = d.a[c * n + i], j0 = d.jk[c * n + i];
+        const int kk = valid ? k : nact - 1;
+        const double a1 = d.fsum[(long long)c * n + kk], j1 = d.fsum[(long long)(3 + c) * n + kk];
+        // prediction of this component (Sec. 2.4 step 7a)
+        const double xp = fma(j0, h3, fma(a0, h2, fma(v0, dt, x0)));
+        const double vp = fma(j0, h2, fma(a0, dt, v0));
+        // 2nd and 3rd derivative at the start of the step from the end-point values
+        const double da = a0 - a1;
+        const double a2 = (-6.0 * da - dt * (4.0 * j0 + 2.0 * j1)) * idt2;
+        const double a3 = (12.0 * da + 6.0 * dt * (j0 + j1)) * idt3;
+        const double x1 = xp + a2 * h4 + a3 * h5;
+        const double v1 = vp + a2 * h3 + a3 * h4;
+        const double a2e = fma(dt, a3, a2);  // 2nd derivative at the end of the step
+        // squared norms, summed over the group's lanes
+        double sA = real ? a1 * a1 : 0.0, sJ = real ? j1 * j1 : 0.0;
+        double sB = real ? a2e * a2e : 0.0, sC = real ? a3 * a3 : 0.0;
+#pragma unroll
+        for (int o = 1; o <= 2; o <<= 1) {
+            sA += __shfl_xor_sync(0xffffffffu, sA, o);
+            sJ += __shfl_xor_sync(0xffffffffu, sJ, o);
+            sB += __shfl_xor_sync(0xffffffffu, sB, o);
+            sC += __shfl_xor_sync(0xffffffffu, sC, o);
+        }
+        // |a1||a2e| = sqrt(A B) on even lanes, |j1||a3| = sqrt(J C) on odd lanes
+        const double r = sqrt((q & 1) ? sJ * sC : sA * sB);
+        const double ro = __shfl_xor_sync(0xffffffffu, r, 1);
+        const double sAB = (q & 1) ? ro : r, sJC = (q & 1) ? r : ro;
+        const double num = d.eta * (sAB + sJ);
+        const double den = sJC + sB;
+        const long long dtau = next_block_step(d, num, den, dtau_old, T);
+        const bool fin = isfinite(x1) && isfinite(v1) && isfinite(a1) && isfinite(j1);
+        if (valid) {
+            if (!behind) {
+                bad |= 2;
+            } else {
+                if (real) {
+                    if (!fin) bad |= 1;
+                    d.x[c * n + i] = x1;
+                    d.v[c * n + i] = v1;
+                    d.a[c * n + i] = a1;
+                    d.jk[c * n + i] = j1;
+                }
+                if (q == 0) {
+                    d.tau[i] = T;
+                    d.dtau[i] = dtau;
+                    const long long tn = T + dtau;
+                    d.tnext[i] = tn;
+                    mymin = tn < mymin ? tn : mymin;
+                }
+            }
+        }
+    }
+    if (bad & 2) set_err(ctrl, ST_EINVAL);
+    if (bad & 1) set_err(ctrl, ST_ENONFINITE);
+    mymin = warp_min_ll(mymin);
+    if (lane == 0 && mymin != LLONG_MAX) atomicMin((unsigned long long *)&ctrl->T_acc, (unsigned long long)mymin);
+    // the barrier orders this CTA's minimum updates before thread 0's release fence
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&ctrl->done, 1u);
+        if (prev == gridDim.x - 1) {
+            __threadfence();
+            const long long next = (long long)atomicAdd((unsigned long long *)&ctrl->T_acc, 0ull);
+            ctrl->T_last = T;
+            ctrl->last_nact = nact;
+            ctrl->T_cur = next;
+            ctrl->T_acc = LLONG_MAX;
+            ctrl->nblock += 1;
+            ctrl->nsteps += nact;
+            ctrl->interactions += (double)nact * (double)n;
+            ctrl->epoch += 1;
+            ctrl->done = 0;
+        }
+    }
+}
+
+// Initial steps after the first full force evaluation (Sec. 2.4 steps 3-4 and the
+// initial step dt = eta |a| / |jerk|), and a = fsum, jerk = fsum.
+__global__ void k_init_steps(Dev d)
+{
+    const int n = d.n;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double a[3], j[3];
+    for (int c = 0; c < 3; c++) {
+        a[c] = d.fsum[(long long)c * n + i];
+        j[c] = d.fsum[(long long)(3 + c) * n + i];
+        d.a[c * n + i] = a[c];
+        d.jk[c * n + i] = j[c];
+    }
+    const double na = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    const double nj = sqrt(j[0] * j[0] + j[1] * j[1] + j[2] * j[2]);
+    const double dt0 = d.eta * na / nj;
+    long long dtau;
+    if (!(dt0 < INFINITY)) {
+        dtau = d.dtau_max;
+    } else {
+        const double q = dt0 / d.dt_min;
+        if (q < 1.0) {
+            dtau = 1;
+        } else if (q >= (double)d.dtau_max) {
+            dtau = d.dtau_max;
+        } else {
+            dtau = 1LL << ((int)((__double_as_longlong(q) >> 52) & 0x7FF) - 1023);
+        }
+    }
+    d.tau[i] = 0;
+    d.dtau[i] = dtau;
+    d.tnext[i] = dtau;
+    bool ok = true;
+    for (int c = 0; c < 3; c++) ok = ok && isfinite(a[c]) && isfinite(j[c]);
+    if (!ok) set_err(d.ctrl, ST_ENONFINITE);
+}
+
+// Minimum next time from scratch (after init, set_state and replayed steps).
+__global__ void k_resync(Dev d)
+{
+    __shared__ long long s_m[32];
+    long long mn = LLONG_MAX;
+    for (int i = threadIdx.x; i < d.n; i += blockDim.x) mn = d.tnext[i] < mn ? d.tnext[i] : mn;
+    mn = warp_min_ll(mn);
+    if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = mn;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        mn = threadIdx.x < (blockDim.x >> 5) ? s_m[threadIdx.x] : LLONG_MAX;
+        mn = warp_min_ll(mn);
+        if (threadIdx.x == 0) {
+            Ctrl *c = d.ctrl;
+            c->T_cur = mn;
+            c->T_acc = LLONG_MAX;
+            c->epoch += 1;
+            c->done = 0;
+        }
+    }
+}
+
+__global__ void k_iota(int *p, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = i;
+}
+
+// ---------------------------------------------------------------- energy
+
+// FP64 path: eu[i] = m_i sum_{j != i} m_j / sqrt(r_ij^2 + eps^2) in FP64 pairs, and
+// ek[i] = m_i |v_i|^2 / 2, from the FP64 predicted planes.
+__global__ void __launch_bounds__(ET) k_energy_fp64(Dev d)
+{
+    const int np = d.npad, n = d.n;
+    const double *P = d.pd;
+    __shared__ double sx[ET], sy[ET], sz[ET], sm[ET];
+    const int i = blockIdx.x * ET + threadIdx.x;
+    const int ii = i < n ? i : n - 1;
+    const double xi = P[ii], yi = P[np + ii], zi = P[2 * np + ii];
+    double phi = 0.0;
+    for (int jt = 0; jt < n; jt += ET) {
+        __syncthreads();
+        const int j = jt + threadIdx.x;
+        if (j < n) {
+            sx[threadIdx.x] = P[j];
+            sy[threadIdx.x] = P[np + j];
+            sz[threadIdx.x] = P[2 * np + j];
+            sm[threadIdx.x] = P[6 * np + j];
+        }
+        __syncthreads();
+        const int jn = min(ET, n - jt);
+        for (int jj = 0; jj < jn; jj++) {
+            const double dx = sx[jj] - xi, dy = sy[jj] - yi, dz = sz[jj] - zi;
+            const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, d.eps2)));
+            const double term = (jt + jj == ii) ? 0.0 : sm[jj] * rsqrt(r2);
+            phi += term;
+        }
+    }
+    if (i < n) {
+        const double mi = P[6 * np + i];
+        const double vx = P[3 * np + i], vy = P[4 * np + i], vz = P[5 * np + i];
+        d.eu[i] = mi * phi;
+        d.ek[i] = 0.5 * mi * (vx * vx + vy * vy + vz * vz);
+    }
+}
+
+// Mixed path: the same sums with FP32 pair arithmetic on the double-single
+// j-records (one Newton step refines rsqrt.approx to about one float ulp) and a
+// compensated accumulator per term, so the sum adds no error beyond the terms'
+// own rounding; FP64 result; kinetic terms from the FP64 state predicted by
+// k_predict_all<false>.
+__global__ void __launch_bounds__(ET) k_energy_mixed(Dev d)
+{
+    const int n = d.n, np = d.npad;
+    __shared__ float4 sA[ET], sB[ET];
+    const int i = blockIdx.x * ET + threadIdx.x;
+    const int ii = i < n ? i : n - 1;
+    const float4 Ai = d.jA[ii], Bi = d.jB[ii];
+    const float eps2 = d.eps2f;
+    DS phi;
+    phi.zero();
+    for (int jt = 0; jt < np; jt += ET) {
+        __syncthreads();
+        sA[threadIdx.x] = d.jA[jt + threadIdx.x];
+        sB[threadIdx.x] = d.jB[jt + threadIdx.x];
+        __syncthreads();
+#pragma unroll 4
+        for (int jj = 0; jj < ET; jj++) {
+            const float4 A = sA[jj], B = sB[jj];
+            const float dx = (A.x - Ai.x) + (B.x - Bi.x);
+            const float dy = (A.y - Ai.y) + (B.y - Bi.y);
+            const float dz = (A.z - Ai.z) + (B.z - Bi.z);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+            float y = rsqrt_approx(r2);
+            y = y * fmaf(-0.5f * r2 * y, y, 1.5f);
+            const float term = (jt + jj == ii) ? 0.f : A.w * y;
+            phi.add(term);
+        }
+    }
+    if (i < n) {
+        const double mi = d.m[i];
+        const double vx = d.pd[3 * np + i], vy = d.pd[4 * np + i], vz = d.pd[5 * np + i];
+        d.eu[i] = mi * phi.as_double();
+        d.ek[i] = 0.5 * mi * (vx * vx + vy * vy + vz * vz);
+    }
+}
+
+// Deterministic sums of eu and ek (one CTA, fixed order).
+__global__ void k_energy_sum(Dev d)
+{
+    __shared__ double su[1024], sk[1024];
+    double u = 0.0, k = 0.0;
+    for (int i = threadIdx.x; i < d.n; i += blockDim.x) {
+        u += d.eu[i];
+        k += d.ek[i];
+    }
+    su[threadIdx.x] = u;
+    sk[threadIdx.x] = k;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            su[threadIdx.x] += su[threadIdx.x + o];
+            sk[threadIdx.x] += sk[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        d.ctrl->K = sk[0];
+        d.ctrl->U = -0.5 * su[0];
+    }
+}
+
+// Sets the block time and active count of a caller-given step.
+__global__ void k_set_step(Ctrl *c, long long T, int nact)
+{
+    c->T_cur = T;
+    c->nact = nact;
+}
+
+__global__ void k_set_tick_end(Ctrl *c, long long tick_end) { c->tick_end = tick_end; }
+
+}  // namespace gdk

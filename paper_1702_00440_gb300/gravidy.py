@@ -26,7 +26,7 @@ _PRECISION = {"fp64": GD_FP64, "mixed": GD_MIXED, GD_FP64: GD_FP64, GD_MIXED: GD
 EXPORTS = (
     "gd_opts_default", "gd_init", "gd_evolve", "gd_step_block", "gd_energy", "gd_get_state",
     "gd_set_state", "gd_get_stats", "gd_kernel_time", "gd_free", "gd_last_error", "gd_force",
-    "gd_predict", "gd_active", "gd_replay_step", "gd_force_noalloc",
+    "gd_predict", "gd_active", "gd_replay_step", "gd_force_noalloc", "gd_autotune", "gd_get_tuning",
 )
 
 
@@ -48,6 +48,7 @@ class gd_opts(ctypes.Structure):
         ("jsplit", ctypes.c_int32),
         ("mode_cut", ctypes.c_int32),
         ("time_force", ctypes.c_int32),
+        ("autotune", ctypes.c_int32),
     ]
 
 
@@ -100,6 +101,8 @@ def load(build_if_missing: bool = True):
             "gd_active": (ctypes.c_int, [P, P, P, P]),
             "gd_replay_step": (ctypes.c_int, [P, I64, P, I64]),
             "gd_force_noalloc": (ctypes.c_int, [I64, P, P, P, D, P, I64, P, P, P]),
+            "gd_autotune": (ctypes.c_int, [P, I32]),
+            "gd_get_tuning": (ctypes.c_int, [P, P, P, P, P, I32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -124,7 +127,7 @@ def _check(rc, ctx=None):
 
 
 def make_opts(dt_min=2.0 ** -22, dt_max=0.125, precision="mixed", device=0, stream=None, use_graph=True,
-              graph_steps=16, jsplit=0, mode_cut=0, time_force=False):
+              graph_steps=16, jsplit=0, mode_cut=0, time_force=False, autotune=False):
     o = gd_opts()
     load().gd_opts_default(ctypes.byref(o))
     o.dt_min = float(dt_min)
@@ -137,6 +140,7 @@ def make_opts(dt_min=2.0 ** -22, dt_max=0.125, precision="mixed", device=0, stre
     o.jsplit = int(jsplit)
     o.mode_cut = int(mode_cut)
     o.time_force = 1 if time_force else 0
+    o.autotune = 1 if autotune else 0
     return o
 
 
@@ -207,6 +211,20 @@ def gd_kernel_time(ctx):
     it = ctypes.c_double()
     _check(load().gd_kernel_time(ctx, ctypes.byref(ms), ctypes.byref(k), ctypes.byref(it)), ctx)
     return ms.value, k.value, it.value
+
+
+def gd_autotune(ctx, reps=3):
+    _check(load().gd_autotune(ctx, int(reps)), ctx)
+
+
+def gd_get_tuning(ctx):
+    """(mode_cut, split[32], mode[32], ms[32]) of the force-kernel tuning table."""
+    mc = ctypes.c_int32()
+    split = np.zeros(32, np.int16)
+    mode = np.zeros(32, np.int8)
+    ms = np.zeros(32, np.float32)
+    _check(load().gd_get_tuning(ctx, ctypes.byref(mc), _p(split), _p(mode), _p(ms), 32), ctx)
+    return mc.value, split, mode, ms
 
 
 def gd_free(ctx):
@@ -298,6 +316,12 @@ class Integrator:
 
     def kernel_time(self):
         return gd_kernel_time(self._h)
+
+    def autotune(self, reps=3):
+        gd_autotune(self._h, reps)
+
+    def tuning(self):
+        return gd_get_tuning(self._h)
 
     def force(self, tick, idx):
         return gd_force(self._h, tick, idx)
