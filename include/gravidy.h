@@ -70,6 +70,10 @@ typedef struct gd_opts {
                            override it */
     int32_t time_force; /* 1 = record CUDA events around every force launch (gd_kernel_time) */
     int32_t autotune;   /* 1 = run gd_autotune(c, 3) at the end of gd_init */
+    int32_t fused;      /* GD_MIXED: 1 = gd_evolve runs many block steps per cooperative launch of
+                           one fused kernel with grid barriers; 0 = three kernels per block step
+                           (graph or eager, see use_graph; the default, faster on GB300 at the
+                           sizes measured).  Both compute the same results bit for bit. */
 } gd_opts;
 
 typedef struct gd_stats {
@@ -79,6 +83,9 @@ typedef struct gd_stats {
     double interactions;   /* sum of N_act * N over all force evaluations */
     int64_t last_nact;     /* N_act of the last block step */
     int64_t kernel_launches; /* CUDA kernels this context has launched (host count) */
+    double phase_ms[3];    /* fused gd_evolve path: time spent in its select/predict, force
+                              (+ small-set correction) and correction phases, each up to and
+                              including its grid barrier (one CTA's device clock) */
 } gd_stats;
 
 typedef struct gd_ctx gd_ctx;
@@ -142,8 +149,10 @@ int gd_get_stats(gd_ctx *c, gd_stats *s);
 /* Device time of the force-kernel launches recorded (CUDA events on the
  * context's stream) since the last call, for launches with a non-empty active
  * set (needs opts.time_force = 1): *ms_total summed milliseconds, *launches
- * their count, *interactions the sum of N_act * N they computed.  Any pointer
- * may be NULL.  Resets the counters. */
+ * their count, *interactions the sum of N_act * N they computed.  With the fused
+ * gd_evolve path the timed kernel is the fused block-step kernel (prediction,
+ * force and correction together).  Any pointer may be NULL.  Resets the
+ * counters. */
 int gd_kernel_time(gd_ctx *c, double *ms_total, int64_t *launches, double *interactions);
 
 void gd_free(gd_ctx *c);

@@ -27,7 +27,7 @@ struct gd_ctx {
     Dev d;
     Tune tn;
     float tune_ms[32];  // autotuner: best force time per bucket (ms), 0 = not measured
-    int grid_force, grid_sel, nchunks, grid_corr;
+    int grid_force, grid_sel, nchunks, grid_corr, grid_steps;
     bool mixed, soft;
     Ctrl *h_ctrl;       // pinned mirror
     Ctrl *h_snap;       // two pinned snapshots for the pipelined gd_evolve
@@ -150,6 +150,19 @@ void launch_step(gd_ctx *c, int slot, cudaEvent_t e0, cudaEvent_t e1, bool captu
     launch_correct(c);
 }
 
+bool use_fused(const gd_ctx *c) { return c->mixed && c->opt.fused && c->grid_steps > 0; }
+
+// One cooperative launch of up to max_steps fused block steps.
+int launch_fused(gd_ctx *c, int max_steps)
+{
+    SArgs a{c->d, c->grid_force, effective_tune(c), c->nchunks, max_steps};
+    void *args[] = {&a};
+    const void *fn = c->soft ? (const void *)k_steps<true> : (const void *)k_steps<false>;
+    c->launches += 1;
+    CK(cudaLaunchCooperativeKernel(fn, dim3(c->grid_steps), dim3(FT), args, 0, c->stream));
+    return GD_OK;
+}
+
 int sync_ctrl(gd_ctx *c)
 {
     CK(cudaMemcpyAsync(c->h_ctrl, c->d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
@@ -188,8 +201,8 @@ int dalloc(gd_ctx *c, T **p, size_t count)
 void free_all(gd_ctx *c)
 {
     Dev &d = c->d;
-    void *ps[] = {d.x,  d.v,  d.a,   d.jk,   d.m,    d.tau,     d.dtau,   d.tnext, d.jA,  d.jB,        d.jC,
-                  d.pd, d.act, d.part, d.fsum, d.tilecnt, d.status, d.eu,    d.ek,  d.nact_hist, d.ctrl};
+    void *ps[] = {d.x,  d.v,   d.a,    d.jk,   d.m,       d.tau,    d.dtau, d.tnext, d.jA,        d.jB,   d.jC,
+                  d.pd, d.act, d.part, d.fsum, d.tilecnt, d.status, d.eu,   d.ek,    d.nact_hist, d.bar, d.ctrl};
     for (void *p : ps)
         if (p) cudaFree(p);
     if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
@@ -373,6 +386,52 @@ int autotune(gd_ctx *c, int reps)
     return sync_ctrl(c);
 }
 
+// gd_evolve through the fused kernel: cooperative launches of up to FUSED_STEPS block
+// steps each, one launch kept in flight while the host reads the previous one's
+// control-block snapshot.  With time_force each launch is bracketed by CUDA events
+// and the launches are not overlapped.
+constexpr int FUSED_STEPS = 1024;
+
+int evolve_fused(gd_ctx *c, long long tick_end)
+{
+    int rc;
+    k_set_tick_end<<<1, 1, 0, c->stream>>>(c->d.ctrl, tick_end);
+    c->launches += 1;
+    if (c->opt.time_force) {
+        for (;;) {
+            const double before = c->h_ctrl->interactions;
+            CK(cudaEventRecord(c->ev[0], c->stream));
+            if ((rc = launch_fused(c, FUSED_STEPS))) return rc;
+            CK(cudaEventRecord(c->ev[1], c->stream));
+            if ((rc = sync_ctrl(c))) return rc;
+            const double done = c->h_ctrl->interactions - before;
+            if (done > 0) {
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+                c->force_ms += ms;
+                c->force_launches += 1;
+                c->force_interactions += done;
+            }
+            if (c->h_ctrl->T_cur > tick_end) break;
+        }
+    } else {
+        if ((rc = launch_fused(c, FUSED_STEPS))) return rc;
+        CK(cudaMemcpyAsync(&c->h_snap[0], c->d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaEventRecord(c->ev_snap[0], c->stream));
+        for (long long k = 0;; k++) {
+            const int cur = (int)(k & 1), nxt = 1 - cur;
+            if ((rc = launch_fused(c, FUSED_STEPS))) return rc;
+            CK(cudaMemcpyAsync(&c->h_snap[nxt], c->d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaEventRecord(c->ev_snap[nxt], c->stream));
+            CK(cudaEventSynchronize(c->ev_snap[cur]));
+            if (c->h_snap[cur].err != 0 || c->h_snap[cur].T_cur > tick_end) break;
+        }
+    }
+    k_set_tick_end<<<1, 1, 0, c->stream>>>(c->d.ctrl, LLONG_MAX);
+    c->launches += 1;
+    return sync_ctrl(c);
+}
+
 }  // namespace
 
 extern "C" {
@@ -392,6 +451,7 @@ void gd_opts_default(gd_opts *o)
     o->mode_cut = 0;
     o->time_force = 0;
     o->autotune = 0;
+    o->fused = 0;
 }
 
 int gd_init(gd_ctx **out, int64_t n, const double *m, const double *x, const double *v, double eps, double eta,
@@ -444,8 +504,9 @@ int gd_init(gd_ctx **out, int64_t n, const double *m, const double *x, const dou
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaStreamCreate"));
         c->own_stream = true;
     }
-    int sms = 0, occ = 0, occ_sel = 0;
+    int sms = 0, occ = 0, occ_sel = 0, occ_steps = 0, coop = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, o.device);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, o.device);
     if (c->mixed)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->soft ? k_force_mixed<true> : k_force_mixed<false>,
                                                           FT, 0);
@@ -455,8 +516,12 @@ int gd_init(gd_ctx **out, int64_t n, const double *m, const double *x, const dou
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             &occ_sel, c->mixed ? k_select_predict<true> : k_select_predict<false>, ST, 0);
+    if (e == cudaSuccess && c->mixed)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_steps, c->soft ? k_steps<true> : k_steps<false>, FT, 0);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "occupancy query"));
     c->grid_force = sms * std::max(1, occ);
+    // the fused kernel needs every CTA resident (cooperative launch)
+    c->grid_steps = (coop && occ_steps > 0) ? sms * occ_steps : 0;
 
     Dev &d = c->d;
     d.n = (int)n;
@@ -486,7 +551,7 @@ int gd_init(gd_ctx **out, int64_t n, const double *m, const double *x, const dou
         (rc = dalloc(c, &d.fsum, (size_t)6 * d.n)) || (rc = dalloc(c, &d.tilecnt, ntiles)) ||
         (rc = dalloc(c, &d.status, (size_t)c->nchunks)) || (rc = dalloc(c, &d.eu, (size_t)d.n)) ||
         (rc = dalloc(c, &d.ek, (size_t)d.n)) || (rc = dalloc(c, &d.nact_hist, (size_t)64)) ||
-        (rc = dalloc(c, &d.ctrl, (size_t)1)))
+        (rc = dalloc(c, &d.bar, (size_t)BAR_WORDS)) || (rc = dalloc(c, &d.ctrl, (size_t)1)))
         return bail(rc);
     e = cudaMallocHost((void **)&c->h_ctrl, sizeof(Ctrl));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_hist, sizeof(int) * 64);
@@ -505,6 +570,8 @@ int gd_init(gd_ctx **out, int64_t n, const double *m, const double *x, const dou
     Ctrl h;
     std::memset(&h, 0, sizeof(h));
     h.T_acc = LLONG_MAX;
+    h.T_acc2[0] = LLONG_MAX;
+    h.T_acc2[1] = LLONG_MAX;
     h.tick_end = LLONG_MAX;
     h.epoch = 1;
     h.interactions = (double)n * (double)n;  // the initial full force evaluation
@@ -513,6 +580,8 @@ int gd_init(gd_ctx **out, int64_t n, const double *m, const double *x, const dou
     if (e == cudaSuccess) e = cudaMemsetAsync(d.nact_hist, 0, sizeof(int) * 64, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.act, 0, sizeof(int) * d.n, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.tilecnt, 0, sizeof(unsigned int) * ntiles, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(d.bar, 0, sizeof(unsigned int) * BAR_WORDS, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d.m, m, sizeof(double) * d.n, cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "upload"));
     if ((rc = upload_aos(c, d.x, x, 0)) || (rc = upload_aos(c, d.v, v, 1))) return bail(rc);
@@ -559,6 +628,7 @@ int gd_evolve(gd_ctx *c, double t_end)
     const long long tick_end = (long long)q;
     if (tick_end < c->h_ctrl->T_last) return fail(c, GD_EINVAL, "t_end is before the current time");
     const int G = c->graph_steps;
+    if (use_fused(c)) return evolve_fused(c, tick_end);
     if (c->opt.use_graph) {
         if ((rc = build_graph(c))) return rc;
     }
@@ -714,6 +784,7 @@ int gd_get_stats(gd_ctx *c, gd_stats *s)
     s->interactions = h->interactions;
     s->last_nact = h->last_nact;
     s->kernel_launches = c->launches;
+    for (int k = 0; k < 3; k++) s->phase_ms[k] = 1e-6 * (double)h->ph_ns[k];
     return GD_OK;
 }
 

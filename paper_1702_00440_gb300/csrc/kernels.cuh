@@ -55,6 +55,7 @@ constexpr int ST_EINVAL = -1, ST_ENONFINITE = -4, ST_ETIMEOUT = -5, ST_ESTATE = 
 struct Ctrl {
     long long T_cur;       // block time of the next step (ticks)
     long long T_acc;       // running minimum of next times, for the step after it
+    long long T_acc2[2];   // the same for the fused kernel, by step parity
     long long T_last;      // block time of the last finished step
     long long tick_end;    // steps whose block time is above this are skipped
     long long nblock;      // block steps
@@ -67,9 +68,17 @@ struct Ctrl {
     unsigned int done;     // finished-CTA counter of k_correct
     int err;               // first device-side fault (gd_status), 0 = none
     int pad_;
+    unsigned long long ph_ns[3];  // fused kernel, CTA 0's clock: select, force, correct phases
 };
 
 __device__ __forceinline__ void set_err(Ctrl *c, int code) { atomicCAS(&c->err, 0, code); }
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // ---------------------------------------------------------------- tuning table
 
@@ -108,6 +117,7 @@ struct Dev {
     unsigned long long *status;  // look-back words, one per chunk of ST particles
     double *eu, *ek;          // per-particle energy terms
     int *nact_hist;           // nact of each step slot of a captured graph
+    unsigned int *bar;        // grid-barrier counters of the fused kernel (see grid_sync)
     Ctrl *ctrl;
 };
 
@@ -179,6 +189,14 @@ __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned lon
     return *(const volatile unsigned long long *)p;
 }
 
+// Loads of data that another CTA may have written earlier in the same launch go
+// through L2 (the per-SM L1 is not coherent across SMs).
+template <class T>
+__device__ __forceinline__ T ldc(const T *p)
+{
+    return __ldcg(p);
+}
+
 __device__ __forceinline__ long long warp_min_ll(long long v)
 {
     for (int o = 16; o > 0; o >>= 1) {
@@ -217,7 +235,8 @@ __device__ __forceinline__ void predict64(const Dev &d, int i, double dt, double
     const double h2 = 0.5 * dt * dt, h3 = dt * dt * dt * (1.0 / 6.0);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        const double x0 = d.x[c * n + i], v0 = d.v[c * n + i], a0 = d.a[c * n + i], j0 = d.jk[c * n + i];
+        const double x0 = ldc(&d.x[c * n + i]), v0 = ldc(&d.v[c * n + i]), a0 = ldc(&d.a[c * n + i]),
+                     j0 = ldc(&d.jk[c * n + i]);
         xp[c] = fma(j0, h3, fma(a0, h2, fma(v0, dt, x0)));
         vp[c] = fma(j0, h2, fma(a0, dt, v0));
     }
@@ -255,31 +274,24 @@ __device__ __forceinline__ void store_jrec(const Dev &d, int i, const double xp[
 // so a chunk's look-back only waits on chunks that are being or have been
 // processed; every wait is bounded.  `slot` >= 0 records nact in nact_hist[slot].
 template <bool MIXED>
-__global__ void __launch_bounds__(ST) k_select_predict(Dev d, int slot, int nchunks)
+__device__ void phase_select(const Dev &d, long long T, unsigned epoch, int slot, int nchunks,
+                             unsigned long long *Tacc)
 {
     Ctrl *ctrl = d.ctrl;
-    const long long T = ctrl->T_cur;
-    if (T > ctrl->tick_end) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            ctrl->nact = 0;
-            if (slot >= 0) d.nact_hist[slot] = 0;
-        }
-        return;
-    }
     __shared__ unsigned s_excl;
     __shared__ unsigned s_wcnt[ST / 32];
     __shared__ long long s_wmin[ST / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned ep = ctrl->epoch & 0x3FFFFFFFu;
+    const unsigned ep = epoch & 0x3FFFFFFFu;
     long long mn_all = LLONG_MAX;
     for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
         const int i = chunk * ST + threadIdx.x;
         bool act = false;
         if (i < d.n) {
-            const long long tn = d.tnext[i];
+            const long long tn = ldc(&d.tnext[i]);
             act = (tn == T);
             if (!act) mn_all = tn < mn_all ? tn : mn_all;
-            const double dt = (double)(T - d.tau[i]) * d.dt_min;
+            const double dt = (double)(T - ldc(&d.tau[i])) * d.dt_min;
             double xp[3], vp[3];
             predict64(d, i, dt, xp, vp);
             store_jrec<MIXED>(d, i, xp, vp, d.m[i]);
@@ -357,8 +369,24 @@ __global__ void __launch_bounds__(ST) k_select_predict(Dev d, int slot, int nchu
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int w = 1; w < ST / 32; w++) mn = s_wmin[w] < mn ? s_wmin[w] : mn;
-        if (mn != LLONG_MAX) atomicMin((unsigned long long *)&ctrl->T_acc, (unsigned long long)mn);
+        if (mn != LLONG_MAX) atomicMin(Tacc, (unsigned long long)mn);
     }
+    __syncthreads();
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(ST) k_select_predict(Dev d, int slot, int nchunks)
+{
+    Ctrl *ctrl = d.ctrl;
+    const long long T = ctrl->T_cur;
+    if (T > ctrl->tick_end) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            ctrl->nact = 0;
+            if (slot >= 0) d.nact_hist[slot] = 0;
+        }
+        return;
+    }
+    phase_select<MIXED>(d, T, ctrl->epoch, slot, nchunks, (unsigned long long *)&ctrl->T_acc);
 }
 
 // Predict all particles to `tick` (no selection): the hooks and gd_energy.
@@ -451,6 +479,136 @@ struct FArgs {
     Tune tn;
 };
 
+// ---------------------------------------------------------------- corrector + time step
+
+// The power-of-two block step after a correction at tick T, from the Aarseth
+// estimate dt_new^2 = num / den (Sec. 3.2) with num = eta (|a1||a2e| + |j1|^2) and
+// den = |j1||a3| + |a2e|^2.  Rules (same as the initial quantisation): steps are
+// powers of two of dt_min in [1, dtau_max] ticks; shrink to the largest power of two
+// not above dt_new; grow by 2 only if dt_new >= 2 dt_old at a time that is a
+// multiple of twice the old step.  dt_new = Inf or NaN (an isolated particle)
+// counts as unconstrained.  The decisions compare num with den times exact powers
+// of two, so no FP64 divide or square root is needed; floor(log2(num / D)) is read
+// off the binary exponents and a mantissa comparison.
+__device__ __forceinline__ long long next_block_step(const Dev &d, double num, double den, long long dtau_old,
+                                                     long long T)
+{
+    const bool unconstrained = !(den > 0.0) || !(num == num) || isinf(num);
+    if (!unconstrained) {
+        if (!(num > 0.0)) return 1;  // dt_new = 0
+        const double dto = (double)dtau_old * d.dt_min;
+        const double lim = dto * dto * den;
+        if (num < lim) {
+            const double D = den * d.dt_min2;  // exact: dt_min^2 is a power of two
+            int fl;
+            if (D >= 2.2250738585072014e-308 && num >= 2.2250738585072014e-308) {
+                const long long bn = __double_as_longlong(num), bd = __double_as_longlong(D);
+                const int en = (int)((bn >> 52) & 0x7FF), ed = (int)((bd >> 52) & 0x7FF);
+                const long long mn = bn & 0xFFFFFFFFFFFFFLL, md = bd & 0xFFFFFFFFFFFFFLL;
+                fl = en - ed - (mn < md ? 1 : 0);
+            } else {
+                const double q = num / D;
+                fl = (int)((__double_as_longlong(q) >> 52) & 0x7FF) - 1023;
+            }
+            const int lvl = fl >> 1;  // floor(fl / 2)
+            if (lvl < 0) return 1;
+            return 1LL << lvl;
+        }
+        if (!(num >= 4.0 * lim)) return dtau_old;
+    }
+    if (2 * dtau_old <= d.dtau_max && (T & (2 * dtau_old - 1)) == 0) return 2 * dtau_old;
+    return dtau_old;
+}
+
+// Correction (Sec. 2.4 step 7d, Hermite scheme) of active slots [k_lo, k_hi) with
+// the new force in fsum, at block time T: the calling warps w0, w0 + ws, ... take
+// eight particles at a time, four lanes per particle -- lanes 0-2 the x, y, z
+// components (prediction, Hermite derivatives, correction), the squared norms of
+// the Aarseth criterion summed across the four lanes, lanes 0 and 1 its two square
+// roots side by side.  mymin collects the new next times, bad the fault bits
+// (1 non-finite, 2 a particle not behind T, which is left untouched).
+__device__ __forceinline__ void correct_slots(const Dev &d, long long T, int k_lo, int k_hi, int w0, int ws,
+                                              long long &mymin, int &bad)
+{
+    const int n = d.n;
+    const int lane = threadIdx.x & 31;
+    const int q = lane & 3;
+    const int c = q < 3 ? q : 2;
+    const bool real = q < 3;
+    for (int kw = k_lo + w0 * 8; kw < k_hi; kw += ws * 8) {
+        const int k = kw + (lane >> 2);
+        const bool valid = k < k_hi;
+        const int kk = valid ? k : k_hi - 1;
+        const int i = ldc(&d.act[kk]);
+        const long long tau0 = ldc(&d.tau[i]);
+        const long long dtau_old = ldc(&d.dtau[i]);
+        const long long dtick = T - tau0;
+        const bool behind = dtick > 0;
+        const double dt = (double)dtick * d.dt_min;
+        double idt;
+        if (behind && (dtick & (dtick - 1)) == 0) {
+            const int e = 63 - __clzll(dtick);
+            idt = d.inv_dt_min * __longlong_as_double((long long)(1023 - e) << 52);
+        } else {
+            idt = 1.0 / dt;
+        }
+        const double dt2 = dt * dt, dt3 = dt2 * dt, dt4 = dt3 * dt, dt5 = dt4 * dt;
+        const double idt2 = idt * idt, idt3 = idt2 * idt;
+        const double h2 = 0.5 * dt2, h3 = dt3 * (1.0 / 6.0), h4 = dt4 * (1.0 / 24.0), h5 = dt5 * (1.0 / 120.0);
+        const double x0 = ldc(&d.x[c * n + i]), v0 = ldc(&d.v[c * n + i]), a0 = ldc(&d.a[c * n + i]),
+                     j0 = ldc(&d.jk[c * n + i]);
+        const double a1 = ldc(&d.fsum[(long long)c * n + kk]), j1 = ldc(&d.fsum[(long long)(3 + c) * n + kk]);
+        // prediction of this component (Sec. 2.4 step 7a)
+        const double xp = fma(j0, h3, fma(a0, h2, fma(v0, dt, x0)));
+        const double vp = fma(j0, h2, fma(a0, dt, v0));
+        // 2nd and 3rd derivative at the start of the step from the end-point values
+        const double da = a0 - a1;
+        const double a2 = (-6.0 * da - dt * (4.0 * j0 + 2.0 * j1)) * idt2;
+        const double a3 = (12.0 * da + 6.0 * dt * (j0 + j1)) * idt3;
+        const double x1 = xp + a2 * h4 + a3 * h5;
+        const double v1 = vp + a2 * h3 + a3 * h4;
+        const double a2e = fma(dt, a3, a2);  // 2nd derivative at the end of the step
+        // squared norms, summed over the group's lanes
+        double sA = real ? a1 * a1 : 0.0, sJ = real ? j1 * j1 : 0.0;
+        double sB = real ? a2e * a2e : 0.0, sC = real ? a3 * a3 : 0.0;
+#pragma unroll
+        for (int o = 1; o <= 2; o <<= 1) {
+            sA += __shfl_xor_sync(0xffffffffu, sA, o);
+            sJ += __shfl_xor_sync(0xffffffffu, sJ, o);
+            sB += __shfl_xor_sync(0xffffffffu, sB, o);
+            sC += __shfl_xor_sync(0xffffffffu, sC, o);
+        }
+        // |a1||a2e| = sqrt(A B) on even lanes, |j1||a3| = sqrt(J C) on odd lanes
+        const double r = sqrt((q & 1) ? sJ * sC : sA * sB);
+        const double ro = __shfl_xor_sync(0xffffffffu, r, 1);
+        const double sAB = (q & 1) ? ro : r, sJC = (q & 1) ? r : ro;
+        const double num = d.eta * (sAB + sJ);
+        const double den = sJC + sB;
+        const long long dtau = next_block_step(d, num, den, dtau_old, T);
+        const bool fin = isfinite(x1) && isfinite(v1) && isfinite(a1) && isfinite(j1);
+        if (valid) {
+            if (!behind) {
+                bad |= 2;
+            } else {
+                if (real) {
+                    if (!fin) bad |= 1;
+                    d.x[c * n + i] = x1;
+                    d.v[c * n + i] = v1;
+                    d.a[c * n + i] = a1;
+                    d.jk[c * n + i] = j1;
+                }
+                if (q == 0) {
+                    d.tau[i] = T;
+                    d.dtau[i] = dtau;
+                    const long long tn = T + dtau;
+                    d.tnext[i] = tn;
+                    mymin = tn < mymin ? tn : mymin;
+                }
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- j-split reduction
 
 template <class P>
@@ -538,9 +696,12 @@ __device__ void tile_reduce(const Dev &d, int nact, int S, int k0, int nvalid)
 }
 
 // After a CTA has stored its partials for i-tile `it`: the last of the S CTAs of
-// that tile reduces them.  The counter returns to zero for the next launch.
+// that tile sums them (the counter returns to zero for the next launch) and, with
+// `tail`, corrects the tile's particles right away, adding their new next times
+// to *Tacc.
 template <class P>
-__device__ __forceinline__ void finish_item(const Dev &d, int nact, const Plan &pl, int it)
+__device__ __forceinline__ void finish_item(const Dev &d, int nact, const Plan &pl, int it, bool tail, long long T,
+                                            unsigned long long *Tacc)
 {
     __shared__ int s_last;
     // the barrier gathers this CTA's partial stores; thread 0's fence releases them
@@ -558,22 +719,31 @@ __device__ __forceinline__ void finish_item(const Dev &d, int nact, const Plan &
         const int k0 = it * pl.itile;
         const int nvalid = min(pl.itile, nact - k0);
         tile_reduce<P>(d, nact, pl.S, k0, nvalid);
+        if (tail) {
+            __syncthreads();
+            long long mymin = LLONG_MAX;
+            int bad = 0;
+            correct_slots(d, T, k0, k0 + nvalid, threadIdx.x >> 5, FT / 32, mymin, bad);
+            if (bad & 2) set_err(d.ctrl, ST_EINVAL);
+            if (bad & 1) set_err(d.ctrl, ST_ENONFINITE);
+            mymin = warp_min_ll(mymin);
+            if ((threadIdx.x & 31) == 0 && mymin != LLONG_MAX) atomicMin(Tacc, (unsigned long long)mymin);
+        }
     }
     __syncthreads();
 }
 
-// ---------------------------------------------------------------- kernel: force (mixed)
+// ---------------------------------------------------------------- force (mixed)
+
+constexpr int BJB = 256;  // warp mode j-tile (2 records per thread)
 
 template <bool SOFT>
-__global__ void __launch_bounds__(FT, 4) k_force_mixed(FArgs fa)
+__device__ void phase_force_mixed(const Dev &d, int nact, const Plan &pl, bool tail, long long T,
+                                  unsigned long long *Tacc)
 {
-    const Dev &d = fa.d;
-    const int nact = min(d.ctrl->nact, d.n);
-    if (nact <= 0) return;
-    const Plan pl = make_plan(nact, d.npad, fa.grid, fa.tn, true, d.cap);
     const float eps2 = d.eps2f;
-    __shared__ float4 sA[BJ], sB[BJ];
-    __shared__ float2 sC[BJ];
+    __shared__ float4 sA[BJB], sB[BJB];
+    __shared__ float2 sC[BJB];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     for (long long item = blockIdx.x; item < pl.items; item += gridDim.x) {
         const int it = (int)(item / pl.S), s = (int)(item % pl.S);
@@ -582,11 +752,11 @@ __global__ void __launch_bounds__(FT, 4) k_force_mixed(FArgs fa)
         if (pl.mode == 0) {
             // i-parallel: thread t owns active slots k0 and k1; j-tiles staged in shared memory
             const int k0 = it * ITILE_A_MIX + t, k1 = k0 + FT;
-            const int i0 = d.act[min(k0, nact - 1)], i1 = d.act[min(k1, nact - 1)];
-            const float4 A0 = d.jA[i0], B0 = d.jB[i0];
-            const float2 C0 = d.jC[i0];
-            const float4 A1 = d.jA[i1], B1 = d.jB[i1];
-            const float2 C1 = d.jC[i1];
+            const int i0 = ldc(&d.act[min(k0, nact - 1)]), i1 = ldc(&d.act[min(k1, nact - 1)]);
+            const float4 A0 = ldc(&d.jA[i0]), B0 = ldc(&d.jB[i0]);
+            const float2 C0 = ldc(&d.jC[i0]);
+            const float4 A1 = ldc(&d.jA[i1]), B1 = ldc(&d.jB[i1]);
+            const float2 C1 = ldc(&d.jC[i1]);
             const bool busy = it * ITILE_A_MIX + warp * 32 < nact;  // the warp has a real slot
             DS g0[6], g1[6];
 #pragma unroll
@@ -596,9 +766,9 @@ __global__ void __launch_bounds__(FT, 4) k_force_mixed(FArgs fa)
             }
             for (int jt = jbeg; jt < jend; jt += BJ) {
                 __syncthreads();
-                sA[t] = d.jA[jt + t];
-                sB[t] = d.jB[jt + t];
-                sC[t] = d.jC[jt + t];
+                sA[t] = ldc(&d.jA[jt + t]);
+                sB[t] = ldc(&d.jB[jt + t]);
+                sC[t] = ldc(&d.jC[jt + t]);
                 __syncthreads();
                 if (busy) {
                     float f0[6] = {0, 0, 0, 0, 0, 0}, f1[6] = {0, 0, 0, 0, 0, 0};
@@ -625,28 +795,37 @@ __global__ void __launch_bounds__(FT, 4) k_force_mixed(FArgs fa)
             if (k0 < nact) store_partial<float>(d, nact, s, k0, r0);
             if (k1 < nact) store_partial<float>(d, nact, s, k1, r1);
         } else {
-            // warp j-parallel: warp w owns slots k0, k0+1; its lanes split the j-chunk
+            // warp j-parallel: warp w owns slots k0, k0+1; j-tiles of BJB staged in shared
+            // memory, the warp's lanes split each tile
             const int k0 = it * ITILE_B_MIX + 2 * warp;
-            if (k0 < nact) {
-                const bool has1 = k0 + 1 < nact;
-                const int i0 = d.act[k0], i1 = d.act[has1 ? k0 + 1 : k0];
-                const float4 A0 = d.jA[i0], B0 = d.jB[i0];
-                const float2 C0 = d.jC[i0];
-                const float4 A1 = d.jA[i1], B1 = d.jB[i1];
-                const float2 C1 = d.jC[i1];
-                DS g0[6], g1[6];
+            const bool busy = k0 < nact;
+            const bool has1 = k0 + 1 < nact;
+            const int i0 = ldc(&d.act[min(k0, nact - 1)]), i1 = ldc(&d.act[min(has1 ? k0 + 1 : k0, nact - 1)]);
+            const float4 A0 = ldc(&d.jA[i0]), B0 = ldc(&d.jB[i0]);
+            const float2 C0 = ldc(&d.jC[i0]);
+            const float4 A1 = ldc(&d.jA[i1]), B1 = ldc(&d.jB[i1]);
+            const float2 C1 = ldc(&d.jC[i1]);
+            DS g0[6], g1[6];
 #pragma unroll
-                for (int c = 0; c < 6; c++) {
-                    g0[c].zero();
-                    g1[c].zero();
+            for (int c = 0; c < 6; c++) {
+                g0[c].zero();
+                g1[c].zero();
+            }
+            for (int jt = jbeg; jt < jend; jt += BJB) {
+                const int nt = min(BJB, jend - jt);  // a multiple of BJ
+                __syncthreads();
+                for (int q = t; q < nt; q += FT) {
+                    sA[q] = ldc(&d.jA[jt + q]);
+                    sB[q] = ldc(&d.jB[jt + q]);
+                    sC[q] = ldc(&d.jC[jt + q]);
                 }
-                for (int jb = jbeg; jb < jend; jb += 32 * FOLD_B) {
-                    const int je = min(jb + 32 * FOLD_B, jend);
+                __syncthreads();
+                if (busy) {
                     float f0[6] = {0, 0, 0, 0, 0, 0}, f1[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll 4
-                    for (int j = jb + lane; j < je; j += 32) {
-                        const float4 A = __ldg(&d.jA[j]), B = __ldg(&d.jB[j]);
-                        const float2 C = __ldg(&d.jC[j]);
+                    for (int jj = lane; jj < nt; jj += 32) {
+                        const float4 A = sA[jj], B = sB[jj];
+                        const float2 C = sC[jj];
                         pair_mixed<SOFT>(A, B, C, A0.x, A0.y, A0.z, B0.x, B0.y, B0.z, B0.w, C0.x, C0.y, eps2, f0);
                         pair_mixed<SOFT>(A, B, C, A1.x, A1.y, A1.z, B1.x, B1.y, B1.z, B1.w, C1.x, C1.y, eps2, f1);
                     }
@@ -656,6 +835,8 @@ __global__ void __launch_bounds__(FT, 4) k_force_mixed(FArgs fa)
                         g1[c].add(f1[c]);
                     }
                 }
+            }
+            if (busy) {
                 float r0[6], r1[6];
 #pragma unroll
                 for (int c = 0; c < 6; c++) {
@@ -672,8 +853,18 @@ __global__ void __launch_bounds__(FT, 4) k_force_mixed(FArgs fa)
                 }
             }
         }
-        finish_item<float>(d, nact, pl, it);
+        finish_item<float>(d, nact, pl, it, tail, T, Tacc);
     }
+}
+
+template <bool SOFT>
+__global__ void __launch_bounds__(FT, 4) k_force_mixed(FArgs fa)
+{
+    const Dev &d = fa.d;
+    const int nact = min(d.ctrl->nact, d.n);
+    if (nact <= 0) return;
+    const Plan pl = make_plan(nact, d.npad, fa.grid, fa.tn, true, d.cap);
+    phase_force_mixed<SOFT>(d, nact, pl, false, 0, nullptr);
 }
 
 // ---------------------------------------------------------------- kernel: force (FP64)
@@ -734,49 +925,8 @@ __global__ void __launch_bounds__(FT, 4) k_force_fp64(FArgs fa)
                 if (lane == 0) store_partial<double>(d, nact, s, k, g);
             }
         }
-        finish_item<double>(d, nact, pl, it);
+        finish_item<double>(d, nact, pl, it, false, 0, nullptr);
     }
-}
-
-// ---------------------------------------------------------------- corrector + time step
-
-// The power-of-two block step after a correction at tick T, from the Aarseth
-// estimate dt_new^2 = num / den (Sec. 3.2) with num = eta (|a1||a2e| + |j1|^2) and
-// den = |j1||a3| + |a2e|^2.  Rules (same as the initial quantisation): steps are
-// powers of two of dt_min in [1, dtau_max] ticks; shrink to the largest power of two
-// not above dt_new; grow by 2 only if dt_new >= 2 dt_old at a time that is a
-// multiple of twice the old step.  dt_new = Inf or NaN (an isolated particle)
-// counts as unconstrained.  The decisions compare num with den times exact powers
-// of two, so no FP64 divide or square root is needed; floor(log2(num / D)) is read
-// off the binary exponents and a mantissa comparison.
-__device__ __forceinline__ long long next_block_step(const Dev &d, double num, double den, long long dtau_old,
-                                                     long long T)
-{
-    const bool unconstrained = !(den > 0.0) || !(num == num) || isinf(num);
-    if (!unconstrained) {
-        if (!(num > 0.0)) return 1;  // dt_new = 0
-        const double dto = (double)dtau_old * d.dt_min;
-        const double lim = dto * dto * den;
-        if (num < lim) {
-            const double D = den * d.dt_min2;  // exact: dt_min^2 is a power of two
-            int fl;
-            if (D >= 2.2250738585072014e-308 && num >= 2.2250738585072014e-308) {
-                const long long bn = __double_as_longlong(num), bd = __double_as_longlong(D);
-                const int en = (int)((bn >> 52) & 0x7FF), ed = (int)((bd >> 52) & 0x7FF);
-                const long long mn = bn & 0xFFFFFFFFFFFFFLL, md = bd & 0xFFFFFFFFFFFFFLL;
-                fl = en - ed - (mn < md ? 1 : 0);
-            } else {
-                const double q = num / D;
-                fl = (int)((__double_as_longlong(q) >> 52) & 0x7FF) - 1023;
-            }
-            const int lvl = fl >> 1;  // floor(fl / 2)
-            if (lvl < 0) return 1;
-            return 1LL << lvl;
-        }
-        if (!(num >= 4.0 * lim)) return dtau_old;
-    }
-    if (2 * dtau_old <= d.dtau_max && (T & (2 * dtau_old - 1)) == 0) return 2 * dtau_old;
-    return dtau_old;
 }
 
 struct CArgs {
@@ -784,10 +934,7 @@ struct CArgs {
 };
 
 // Corrects every active particle and (last CTA) turns the running minimum into the
-// next block time.  Four lanes per particle: lanes 0-2 take the x, y, z components
-// (prediction, Hermite derivatives, correction), the squared norms of the Aarseth
-// criterion are summed across the four lanes, and lanes 0 and 1 take its two
-// square roots side by side.
+// next block time.
 __global__ void __launch_bounds__(CT) k_correct(CArgs ca)
 {
     const Dev &d = ca.d;
@@ -797,84 +944,11 @@ __global__ void __launch_bounds__(CT) k_correct(CArgs ca)
     const long long T = ctrl->T_cur;
     const int n = d.n;
     const int lane = threadIdx.x & 31;
-    const int q = lane & 3;
-    const int c = q < 3 ? q : 2;
-    const bool real = q < 3;
     const int gwarp = (blockIdx.x * CT + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * CT) >> 5;
     long long mymin = LLONG_MAX;
     int bad = 0;
-    for (int kw = gwarp * 8; kw < nact; kw += nwarps * 8) {
-        const int k = kw + (lane >> 2);
-        const bool valid = k < nact;
-        const int i = d.act[valid ? k : nact - 1];
-        const long long tau0 = d.tau[i];
-        const long long dtau_old = d.dtau[i];
-        const long long dtick = T - tau0;
-        const bool behind = dtick > 0;
-        const double dt = (double)dtick * d.dt_min;
-        double idt;
-        if (behind && (dtick & (dtick - 1)) == 0) {
-            const int e = 63 - __clzll(dtick);
-            idt = d.inv_dt_min * __longlong_as_double((long long)(1023 - e) << 52);
-        } else {
-            idt = 1.0 / dt;
-        }
-        const double dt2 = dt * dt, dt3 = dt2 * dt, dt4 = dt3 * dt, dt5 = dt4 * dt;
-        const double idt2 = idt * idt, idt3 = idt2 * idt;
-        const double h2 = 0.5 * dt2, h3 = dt3 * (1.0 / 6.0), h4 = dt4 * (1.0 / 24.0), h5 = dt5 * (1.0 / 120.0);
-        const double x0 = d.x[c * n + i], v0 = d.v[c * n + i], a0 = d.a[c * n + i], j0 = d.jk[c * n + i];
-        const int kk = valid ? k : nact - 1;
-        const double a1 = d.fsum[(long long)c * n + kk], j1 = d.fsum[(long long)(3 + c) * n + kk];
-        // prediction of this component (Sec. 2.4 step 7a)
-        const double xp = fma(j0, h3, fma(a0, h2, fma(v0, dt, x0)));
-        const double vp = fma(j0, h2, fma(a0, dt, v0));
-        // 2nd and 3rd derivative at the start of the step from the end-point values
-        const double da = a0 - a1;
-        const double a2 = (-6.0 * da - dt * (4.0 * j0 + 2.0 * j1)) * idt2;
-        const double a3 = (12.0 * da + 6.0 * dt * (j0 + j1)) * idt3;
-        const double x1 = xp + a2 * h4 + a3 * h5;
-        const double v1 = vp + a2 * h3 + a3 * h4;
-        const double a2e = fma(dt, a3, a2);  // 2nd derivative at the end of the step
-        // squared norms, summed over the group's lanes
-        double sA = real ? a1 * a1 : 0.0, sJ = real ? j1 * j1 : 0.0;
-        double sB = real ? a2e * a2e : 0.0, sC = real ? a3 * a3 : 0.0;
-#pragma unroll
-        for (int o = 1; o <= 2; o <<= 1) {
-            sA += __shfl_xor_sync(0xffffffffu, sA, o);
-            sJ += __shfl_xor_sync(0xffffffffu, sJ, o);
-            sB += __shfl_xor_sync(0xffffffffu, sB, o);
-            sC += __shfl_xor_sync(0xffffffffu, sC, o);
-        }
-        // |a1||a2e| = sqrt(A B) on even lanes, |j1||a3| = sqrt(J C) on odd lanes
-        const double r = sqrt((q & 1) ? sJ * sC : sA * sB);
-        const double ro = __shfl_xor_sync(0xffffffffu, r, 1);
-        const double sAB = (q & 1) ? ro : r, sJC = (q & 1) ? r : ro;
-        const double num = d.eta * (sAB + sJ);
-        const double den = sJC + sB;
-        const long long dtau = next_block_step(d, num, den, dtau_old, T);
-        const bool fin = isfinite(x1) && isfinite(v1) && isfinite(a1) && isfinite(j1);
-        if (valid) {
-            if (!behind) {
-                bad |= 2;
-            } else {
-                if (real) {
-                    if (!fin) bad |= 1;
-                    d.x[c * n + i] = x1;
-                    d.v[c * n + i] = v1;
-                    d.a[c * n + i] = a1;
-                    d.jk[c * n + i] = j1;
-                }
-                if (q == 0) {
-                    d.tau[i] = T;
-                    d.dtau[i] = dtau;
-                    const long long tn = T + dtau;
-                    d.tnext[i] = tn;
-                    mymin = tn < mymin ? tn : mymin;
-                }
-            }
-        }
-    }
+    correct_slots(d, T, 0, nact, gwarp, nwarps, mymin, bad);
     if (bad & 2) set_err(ctrl, ST_EINVAL);
     if (bad & 1) set_err(ctrl, ST_ENONFINITE);
     mymin = warp_min_ll(mymin);
@@ -954,6 +1028,8 @@ __global__ void k_resync(Dev d)
             Ctrl *c = d.ctrl;
             c->T_cur = mn;
             c->T_acc = LLONG_MAX;
+            c->T_acc2[0] = LLONG_MAX;
+            c->T_acc2[1] = LLONG_MAX;
             c->epoch += 1;
             c->done = 0;
         }
@@ -1079,5 +1155,118 @@ __global__ void k_set_step(Ctrl *c, long long T, int nact)
 }
 
 __global__ void k_set_tick_end(Ctrl *c, long long tick_end) { c->tick_end = tick_end; }
+
+
+// ---------------------------------------------------------------- fused block steps
+
+constexpr int BAR_WORDS = 32;            // the barrier counter sits alone in a 128-byte line
+constexpr int BAR_SPIN_LIMIT = 1 << 24;  // bounded wait
+
+// Grid-wide barrier for a co-resident (cooperative) grid of nb CTAs: one 64-bit
+// counter that only grows; the k-th barrier is passed when the counter reaches
+// nb * k, so each CTA waits for the multiple of nb above the value its own arrival
+// returned.  Thread 0's fences release the CTA's writes before arriving and
+// acquire the others' after passing.  The wait is bounded: on time-out the device
+// flag records GD_ETIMEOUT and the CTA goes on (the results are then void, but the
+// kernel ends).
+__device__ __forceinline__ void grid_sync(unsigned int *bar, Ctrl *ctrl)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long *ctr = (unsigned long long *)bar;
+        const unsigned long long nb = gridDim.x;
+        __threadfence();
+        const unsigned long long old = atomicAdd(ctr, 1ull);
+        const unsigned long long target = (old / nb + 1) * nb;
+        int spins = 0;
+        while (*(volatile unsigned long long *)ctr < target) {
+            if (++spins > BAR_SPIN_LIMIT) {
+                set_err(ctrl, ST_ETIMEOUT);
+                break;
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+struct SArgs {
+    Dev d;
+    int plan_grid;  // grid size the force plan assumes (the same as the three-kernel path)
+    Tune tn;
+    int nchunks;
+    int max_steps;
+};
+
+// Up to max_steps block steps in one cooperative launch (all CTAs resident).  Per
+// step: select + predict, grid barrier, force -- with the correction done by the
+// last CTA of each i-tile when the tiles are small (warp mode) -- grid barrier, and
+// in i-parallel mode a separate correction pass and a third barrier.  The block
+// time of the next step is the atomic minimum gathered during the step (slot by
+// step parity), read after the last barrier.  Stops early once the block time
+// passes tick_end.  Computes exactly what the three-kernel step computes.
+template <bool SOFT>
+__global__ void __launch_bounds__(FT, 4) k_steps(SArgs a)
+{
+    const Dev &d = a.d;
+    Ctrl *ctrl = d.ctrl;
+    const unsigned base = ctrl->epoch;
+    const long long tick_end = ctrl->tick_end;
+    long long T = ctrl->T_cur;
+    int s = 0;
+    bool capped = true;
+    for (; s < a.max_steps; s++) {
+        const unsigned g = base + (unsigned)s;
+        unsigned long long *acc = (unsigned long long *)&ctrl->T_acc2[g & 1];
+        if (s > 0) T = (long long)ldc((const unsigned long long *)&ctrl->T_acc2[(g - 1) & 1]);
+        if (T > tick_end) {
+            capped = false;
+            break;
+        }
+        const unsigned long long t0 = global_ns();
+        phase_select<true>(d, T, g, -1, a.nchunks, acc);
+        grid_sync(d.bar, ctrl);
+        const unsigned long long t1 = global_ns();
+        const int nact = min(ldc(&ctrl->nact), d.n);
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->T_acc2[(g - 1) & 1] = LLONG_MAX;
+        const Plan pl = make_plan(nact, d.npad, a.plan_grid, a.tn, true, d.cap);
+        const bool tail = pl.mode == 1;
+        if (nact > 0) phase_force_mixed<SOFT>(d, nact, pl, tail, T, acc);
+        grid_sync(d.bar, ctrl);
+        const unsigned long long t2 = global_ns();
+        if (!tail && nact > 0) {
+            long long mymin = LLONG_MAX;
+            int bad = 0;
+            const int gwarp = (blockIdx.x * FT + threadIdx.x) >> 5;
+            const int nwarps = (gridDim.x * FT) >> 5;
+            correct_slots(d, T, 0, nact, gwarp, nwarps, mymin, bad);
+            if (bad & 2) set_err(ctrl, ST_EINVAL);
+            if (bad & 1) set_err(ctrl, ST_ENONFINITE);
+            mymin = warp_min_ll(mymin);
+            if ((threadIdx.x & 31) == 0 && mymin != LLONG_MAX) atomicMin(acc, (unsigned long long)mymin);
+            grid_sync(d.bar, ctrl);
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            const unsigned long long t3 = global_ns();
+            ctrl->ph_ns[0] += t1 - t0;
+            ctrl->ph_ns[1] += t2 - t1;
+            ctrl->ph_ns[2] += t3 - t2;
+            ctrl->T_last = T;
+            ctrl->last_nact = nact;
+            ctrl->nblock += 1;
+            ctrl->nsteps += nact;
+            ctrl->interactions += (double)nact * (double)d.n;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (s > 0) {
+            const unsigned gl = base + (unsigned)s - 1;
+            if (capped) T = (long long)ldc((const unsigned long long *)&ctrl->T_acc2[gl & 1]);
+            ctrl->T_acc2[gl & 1] = LLONG_MAX;
+        }
+        ctrl->T_cur = T;
+        ctrl->epoch = base + (unsigned)s + 1;
+    }
+}
 
 }  // namespace gdk

@@ -49,6 +49,7 @@ class gd_opts(ctypes.Structure):
         ("mode_cut", ctypes.c_int32),
         ("time_force", ctypes.c_int32),
         ("autotune", ctypes.c_int32),
+        ("fused", ctypes.c_int32),
     ]
 
 
@@ -60,6 +61,7 @@ class gd_stats(ctypes.Structure):
         ("interactions", ctypes.c_double),
         ("last_nact", ctypes.c_int64),
         ("kernel_launches", ctypes.c_int64),
+        ("phase_ms", ctypes.c_double * 3),
     ]
 
 
@@ -127,7 +129,7 @@ def _check(rc, ctx=None):
 
 
 def make_opts(dt_min=2.0 ** -22, dt_max=0.125, precision="mixed", device=0, stream=None, use_graph=True,
-              graph_steps=16, jsplit=0, mode_cut=0, time_force=False, autotune=False):
+              graph_steps=16, jsplit=0, mode_cut=0, time_force=False, autotune=False, fused=False):
     o = gd_opts()
     load().gd_opts_default(ctypes.byref(o))
     o.dt_min = float(dt_min)
@@ -141,6 +143,7 @@ def make_opts(dt_min=2.0 ** -22, dt_max=0.125, precision="mixed", device=0, stre
     o.mode_cut = int(mode_cut)
     o.time_force = 1 if time_force else 0
     o.autotune = 1 if autotune else 0
+    o.fused = 1 if fused else 0
     return o
 
 
@@ -201,7 +204,8 @@ def gd_get_stats(ctx):
     s = gd_stats()
     _check(load().gd_get_stats(ctx, ctypes.byref(s)), ctx)
     return dict(tick=s.tick, block_steps=s.block_steps, particle_steps=s.particle_steps,
-                interactions=s.interactions, last_nact=s.last_nact, kernel_launches=s.kernel_launches)
+                interactions=s.interactions, last_nact=s.last_nact, kernel_launches=s.kernel_launches,
+                phase_ms=list(s.phase_ms))
 
 
 def gd_kernel_time(ctx):

@@ -288,15 +288,23 @@ def test_free_running_energy_within_2x_of_oracle(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_graph_and_eager_paths_identical(prec):
-    m, x, v = inputs.plummer(1000, seed=8)
+@pytest.mark.parametrize("n", [1000, 20000])
+def test_graph_eager_and_fused_paths_identical(prec, n):
+    """The fused cooperative kernel, the captured graph and eager launches take
+    the same block steps with the same arithmetic: bit-identical states."""
+    m, x, v = inputs.plummer(n, seed=8)
+    t_end = 0.25 if n <= 1000 else 0.125
     out = []
-    for use_graph in (True, False):
-        with gravidy.Integrator(m, x, v, EPS, ETA, precision=prec, use_graph=use_graph, graph_steps=7) as g:
-            g.evolve(0.25)
-            out.append(g.state())
-    for k in out[0]:
-        assert np.array_equal(out[0][k], out[1][k]), k
+    for opts in (dict(fused=True), dict(fused=False, use_graph=True, graph_steps=7),
+                 dict(fused=False, use_graph=False)):
+        with gravidy.Integrator(m, x, v, EPS, ETA, precision=prec, **opts) as g:
+            g.evolve(t_end)
+            st = g.state()
+            st["stats"] = np.array([g.stats()[k] for k in ("tick", "block_steps", "particle_steps")])
+            out.append(st)
+    for other in out[1:]:
+        for k in out[0]:
+            assert np.array_equal(out[0][k], other[k]), k
 
 
 def test_step_block_matches_oracle_schedule():
@@ -334,12 +342,16 @@ def test_replay_rejects_a_particle_not_behind_the_block_time():
         assert e.value.code == gravidy.GD_EINVAL
 
 
-def test_kernel_timing_hook():
+@pytest.mark.parametrize("fused", [False, True])
+def test_kernel_timing_hook(fused):
     m, x, v = inputs.plummer(2000, seed=2)
-    with gravidy.Integrator(m, x, v, EPS, ETA, time_force=True) as g:
+    with gravidy.Integrator(m, x, v, EPS, ETA, time_force=True, fused=fused) as g:
         g.evolve(0.125)
         ms, launches, inter = g.kernel_time()
         st = g.stats()
-    assert launches == st["block_steps"]
+    if fused:
+        assert 1 <= launches <= st["block_steps"]
+    else:
+        assert launches == st["block_steps"]
     assert inter == st["interactions"] - 2000.0 ** 2   # all but the initial evaluation
     assert ms > 0
