@@ -64,6 +64,11 @@ def _args():
     p.add_argument("--profile-force", type=int, default=0, metavar="N",
                    help="profiling hook: initialise an N-particle Plummer sphere (one full force evaluation), "
                         "evaluate all N once more, print nothing and exit")
+    p.add_argument("--sweep", choices=["force", "powerlaw", "accuracy"],
+                   help="extra measurements, one JSON line each (not the benchmark line): force = "
+                        "full evaluations N=2^10..2^20 and N=2^20 with active sets 1..2^20; powerlaw = "
+                        "N=262144 power-law masses to t=1/8 (active-set histogram, interactions/s per "
+                        "set size); accuracy = N=16384 FP64 vs mixed to t=1")
     p.add_argument("--profile-steps", type=int, default=0, metavar="K",
                    help="profiling hook: initialise the --n workload and take K block steps one by one "
                         "(no graph), print nothing and exit")
@@ -449,6 +454,134 @@ def run_gravidy(a):
     return 0
 
 
+def _timed_force(g, idx, reps=3):
+    """Median force-kernel time (ms) of gd_force over idx, CUDA events."""
+    ts = []
+    g.kernel_time()
+    for _ in range(reps):
+        g.force(0, idx)
+        ms, _, _ = g.kernel_time()
+        ts.append(ms)
+    return sorted(ts)[len(ts) // 2]
+
+
+def sweep_force(a):
+    """Full evaluations N = 2^10..2^20 (mixed), and N = 2^20 with random active
+    sets of 1, 32, 1024, 32768, 2^20 (mixed and FP64, FP64 up to 32768), with the
+    oracle timed on a bounded i-subsample against all N."""
+    import oracle
+    from paper_1702_00440_gb300 import gravidy, inputs
+
+    gravidy.load()
+    rows = []
+    for k in range(10, 21):
+        n = 1 << k
+        m, x, v = inputs.plummer(n, seed=1)
+        with gravidy.Integrator(m, x, v, EPS, ETA, precision="mixed", time_force=True) as g:
+            ms = _timed_force(g, np.arange(n, dtype=np.int32))
+        ips = float(n) * n / (ms / 1e3)
+        rows.append({"n": n, "nact": n, "precision": "mixed", "ms": ms, "interactions_per_s": ips,
+                     "frac_fp32_peak": FLOP_PER_INTERACTION * ips / 1e12 / FP32_PEAK_TFLOPS})
+    n = 1 << 20
+    m, x, v = inputs.plummer(n, seed=1)
+    for prec in ("mixed", "fp64"):
+        with gravidy.Integrator(m, x, v, EPS, ETA, precision=prec, time_force=True, autotune=prec == "mixed") as g:
+            for nact in (1, 32, 1024, 32768, n):
+                if prec == "fp64" and nact > 32768:
+                    continue
+                idx = np.arange(n, dtype=np.int32) if nact == n else inputs.random_subset(n, nact, seed=nact)
+                ms = _timed_force(g, idx)
+                ips = float(nact) * n / (ms / 1e3)
+                rows.append({"n": n, "nact": nact, "precision": prec, "ms": ms, "interactions_per_s": ips,
+                             "frac_fp32_peak": FLOP_PER_INTERACTION * ips / 1e12 / FP32_PEAK_TFLOPS,
+                             "j_bytes_per_s": 40.0 * n / (ms / 1e3)})
+    oracle.build()
+    sub = inputs.random_subset(n, 64, seed=4096)
+    t0 = time.perf_counter()
+    oracle.force(m, x, v, EPS, sub)
+    dt = time.perf_counter() - t0
+    out = {"sweep": "force", "metric": "acc+jerk interactions/s", "rows": rows,
+           "oracle": {"interactions_per_s": 64.0 * n / dt, "sample": "64 i x 2^20 j", "cores": 1},
+           "peak_tflops": FP32_PEAK_TFLOPS}
+    print(json.dumps(out))
+    return 0
+
+
+def sweep_powerlaw(a):
+    """N = 262144 Plummer with power-law masses, mixed, t = 0 -> 1/8: active-set
+    size histogram per block step, the autotuner's force time per set-size bucket
+    (interactions/s per block size), wall time per N-body unit and |dE/E|."""
+    import torch
+
+    from paper_1702_00440_gb300 import gravidy, inputs
+
+    n = 262144
+    m, x, v = inputs.plummer(n, seed=3, masses=inputs.power_law_masses(n, seed=3))
+    g = gravidy.Integrator(m, x, v, EPS, ETA, precision="mixed", autotune=True)
+    _, split, mode, tms = g.tuning()
+    K0, U0 = g.energy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.evolve(DT_STEP)
+    wall = time.perf_counter() - t0
+    K1, U1 = g.energy()
+    st = g.stats()
+    g.close()
+    # the same run again one block step at a time, for the active-set histogram
+    g = gravidy.Integrator(m, x, v, EPS, ETA, precision="mixed")
+    hist = {}
+    steps = 0
+    while True:
+        t, nact = g.step_block()
+        steps += 1
+        b = int(np.log2(nact))
+        hist[b] = hist.get(b, 0) + 1
+        if t >= DT_STEP:
+            break
+    g.close()
+    per_bucket = []
+    for b in sorted(hist):
+        row = {"log2_nact": b, "block_steps": hist[b]}
+        if tms[b] > 0:
+            row["force_ms"] = float(tms[b])
+            row["interactions_per_s"] = float(2 ** b) * n / (float(tms[b]) / 1e3)
+            row["mode"] = "i-parallel" if mode[b] == 0 else "warp"
+            row["jsplit"] = int(split[b])
+        per_bucket.append(row)
+    out = {"sweep": "powerlaw", "n": n, "t_end": DT_STEP, "wall_s": wall, "s_per_nbu": wall / DT_STEP,
+           "block_steps": st["block_steps"], "particle_steps": st["particle_steps"],
+           "interactions_per_s": (st["interactions"] - float(n) * n) / wall,
+           "dE_E": abs((K1 + U1 - K0 - U0) / (K0 + U0)), "histogram": per_bucket}
+    print(json.dumps(out))
+    return 0
+
+
+def sweep_accuracy(a):
+    """N = 16384 Plummer to t = 1 in the FP64 and mixed GPU forms: wall time per
+    N-body unit and |dE/E| at t = 1."""
+    import torch
+
+    from paper_1702_00440_gb300 import gravidy, inputs
+
+    n = 16384
+    m, x, v = inputs.plummer(n, seed=1)
+    res = {}
+    for prec in ("mixed", "fp64"):
+        g = gravidy.Integrator(m, x, v, EPS, ETA, precision=prec)
+        K0, U0 = g.energy()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.evolve(1.0)
+        wall = time.perf_counter() - t0
+        K1, U1 = g.energy()
+        st = g.stats()
+        g.close()
+        res[prec] = {"s_per_nbu": wall, "dE_E": abs((K1 + U1 - K0 - U0) / (K0 + U0)),
+                     "block_steps": st["block_steps"], "particle_steps": st["particle_steps"]}
+    print(json.dumps({"sweep": "accuracy", "n": n, "t_end": 1.0, **res}))
+    return 0
+
+
 def profile_force(a):
     from paper_1702_00440_gb300 import gravidy, inputs
 
@@ -474,6 +607,8 @@ def main():
         return profile_force(a)
     if a.profile_steps:
         return profile_steps(a)
+    if a.sweep:
+        return {"force": sweep_force, "powerlaw": sweep_powerlaw, "accuracy": sweep_accuracy}[a.sweep](a)
     if a.impl == "reference":
         return run_reference(a)
     return run_gravidy(a)

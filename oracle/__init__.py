@@ -58,6 +58,7 @@ def _load():
             "or_energy": (None, [_I64, _P, _P, _P, _D, _P, _P]),
             "or_active": (_I64, [_I64, _P, _P, _P]),
             "or_predict_one": (None, [_P, _P, _P, _P, _D, _P, _P]),
+            "or_predict_all": (None, [_I64, _P, _P, _P, _P, _P, _P, _P]),
             "or_hermite_derivs": (None, [_P, _P, _P, _P, _D, _P, _P]),
             "or_correct_one": (None, [_P, _P, _P, _P, _D, _P, _P]),
             "or_aarseth_dt": (_D, [_P, _P, _P, _P, _D]),
@@ -149,6 +150,18 @@ def predict_one(x, v, a, j, dt):
     xp = np.zeros(3)
     vp = np.zeros(3)
     lib.or_predict_one(_ptr(_f64(x)), _ptr(_f64(v)), _ptr(_f64(a)), _ptr(_f64(j)), float(dt), _ptr(xp), _ptr(vp))
+    return xp, vp
+
+
+def predict_all(x, v, a, j, dt):
+    """Taylor prediction of every particle i over dt[i]."""
+    lib = _load()
+    dt = _f64(dt)
+    n = dt.shape[0]
+    x, v, a, j = (_f64(q, (n, 3)) for q in (x, v, a, j))
+    xp = np.zeros((n, 3))
+    vp = np.zeros((n, 3))
+    lib.or_predict_all(n, _ptr(x), _ptr(v), _ptr(a), _ptr(j), _ptr(dt), _ptr(xp), _ptr(vp))
     return xp, vp
 
 

@@ -189,6 +189,14 @@ void or_predict_one(const double x[3], const double v[3], const double a[3],
     }
 }
 
+/* Prediction of n particles, particle i over dt[i] (AoS [n][3] arrays). */
+void or_predict_all(int64_t n, const double *x, const double *v, const double *a, const double *j,
+                    const double *dt, double *xp, double *vp)
+{
+    for (int64_t i = 0; i < n; i++)
+        or_predict_one(x + 3 * i, v + 3 * i, a + 3 * i, j + 3 * i, dt[i], xp + 3 * i, vp + 3 * i);
+}
+
 /* Second and third derivative of the acceleration at the START of an
  * interval of length dt from the end-point values (a0, j0) and (a1, j1): the
  * cubic a(t) = a0 + j0 t + a2 t^2/2 + a3 t^3/6 that matches a1 and j1 at
