@@ -64,11 +64,13 @@ def _args():
     p.add_argument("--profile-force", type=int, default=0, metavar="N",
                    help="profiling hook: initialise an N-particle Plummer sphere (one full force evaluation), "
                         "evaluate all N once more, print nothing and exit")
-    p.add_argument("--sweep", choices=["force", "powerlaw", "accuracy"],
+    p.add_argument("--sweep", choices=["force", "powerlaw", "accuracy", "ensemble"],
                    help="extra measurements, one JSON line each (not the benchmark line): force = "
                         "full evaluations N=2^10..2^20 and N=2^20 with active sets 1..2^20; powerlaw = "
                         "N=262144 power-law masses to t=1/8 (active-set histogram, interactions/s per "
-                        "set size); accuracy = N=16384 FP64 vs mixed to t=1")
+                        "set size); accuracy = N=16384 FP64 vs mixed to t=1; ensemble = 256 clusters of "
+                        "log-uniform N in [256, 8192] to t=--ens-t, one ensemble vs the clusters one by one")
+    p.add_argument("--ens-t", type=float, default=0.125)
     p.add_argument("--profile-steps", type=int, default=0, metavar="K",
                    help="profiling hook: initialise the --n workload and take K block steps one by one "
                         "(no graph), print nothing and exit")
@@ -582,6 +584,59 @@ def sweep_accuracy(a):
     return 0
 
 
+def sweep_ensemble(a):
+    """256 independent Plummer spheres, N_c log-uniform in [256, 8192] (seeded),
+    eps = 1e-4, eta = 0.01, mixed: advanced together as one ensemble vs the same
+    clusters one after another (one context each, captured-graph steps)."""
+    import torch
+
+    from paper_1702_00440_gb300 import gravidy, inputs
+
+    sizes = inputs.ensemble_sizes(256, seed=1)
+    ms, xs, vs = [], [], []
+    for q, n in enumerate(sizes):
+        m, x, v = inputs.plummer(int(n), seed=1000 + q)
+        ms.append(m)
+        xs.append(x)
+        vs.append(v)
+    t_end = a.ens_t
+    e = gravidy.Ensemble(sizes, np.concatenate(ms), np.concatenate(xs), np.concatenate(vs), EPS, ETA)
+    K0, U0 = e.energy()
+    s0 = e.stats()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e.evolve(t_end)
+    wall_ens = time.perf_counter() - t0
+    K1, U1 = e.energy()
+    s1 = e.stats()
+    e.close()
+    de = np.abs((K1 + U1 - K0 - U0) / (K0 + U0))
+    wall_seq = 0.0
+    inter_seq = 0.0
+    steps_seq = 0
+    for q in range(len(sizes)):
+        g = gravidy.Integrator(ms[q], xs[q], vs[q], EPS, ETA, precision="mixed")
+        st0 = g.stats()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.evolve(t_end)
+        wall_seq += time.perf_counter() - t0
+        st1 = g.stats()
+        inter_seq += st1["interactions"] - st0["interactions"]
+        steps_seq += st1["block_steps"] - st0["block_steps"]
+        g.close()
+    inter_ens = s1["interactions"] - s0["interactions"]
+    out = {"sweep": "ensemble", "clusters": int(sizes.size), "particles": int(sizes.sum()),
+           "n_min": int(sizes.min()), "n_max": int(sizes.max()), "t_end": t_end,
+           "ensemble": {"wall_s": wall_ens, "global_block_steps": s1["block_steps"] - s0["block_steps"],
+                        "interactions_per_s": inter_ens / wall_ens},
+           "one_by_one": {"wall_s": wall_seq, "block_steps": steps_seq, "interactions_per_s": inter_seq / wall_seq},
+           "speedup": wall_seq / wall_ens,
+           "dE_E": {"median": float(np.median(de)), "max": float(de.max())}}
+    print(json.dumps(out))
+    return 0
+
+
 def profile_force(a):
     from paper_1702_00440_gb300 import gravidy, inputs
 
@@ -608,7 +663,8 @@ def main():
     if a.profile_steps:
         return profile_steps(a)
     if a.sweep:
-        return {"force": sweep_force, "powerlaw": sweep_powerlaw, "accuracy": sweep_accuracy}[a.sweep](a)
+        return {"force": sweep_force, "powerlaw": sweep_powerlaw, "accuracy": sweep_accuracy,
+                "ensemble": sweep_ensemble}[a.sweep](a)
     if a.impl == "reference":
         return run_reference(a)
     return run_gravidy(a)

@@ -185,6 +185,43 @@ int gd_active(gd_ctx *c, int32_t *idx, int64_t *nact, int64_t *tick_next);
  * are computed and stored as usual but the block times come from the caller. */
 int gd_replay_step(gd_ctx *c, int64_t tick_next, const int32_t *idx, int64_t nact);
 
+/* ---- ensembles of independent clusters -------------------------------------
+ *
+ * nclusters independent N-body systems advanced together: every cluster follows
+ * the same scheme as gd_init/gd_evolve (Sec. 2.4, Hermite-4 with block steps and
+ * Aarseth's criterion, Plummer softening eps, parameter eta) and feels only its
+ * own particles.  A global block step is the smallest next time over all clusters;
+ * the active particles of every cluster whose next time equals it are advanced in
+ * the same kernels (one captured graph replays many such steps).  GD_MIXED only.
+ * Cluster q has n_per[q] particles, 1 <= n_per[q] <= 2^24, 1 <= nclusters <= 2048;
+ * m, x, v are the clusters' arrays concatenated in cluster order (m: sum n_per
+ * doubles, x and v: sum n_per * 3 doubles AoS).  Same ownership and error rules
+ * as the single-system calls; gd_ens_last_error(NULL) reports a failed init. */
+typedef struct gd_ens gd_ens;
+
+int gd_ens_init(gd_ens **out, int32_t nclusters, const int64_t *n_per, const double *m, const double *x,
+                const double *v, double eps, double eta, const gd_opts *opt);
+
+/* Advance every cluster until no particle's next time is <= t_end. */
+int gd_ens_evolve(gd_ens *s, double t_end);
+
+/* One global block step; *t_out its time, *nact_out its active particles (all clusters). */
+int gd_ens_step_block(gd_ens *s, double *t_out, int64_t *nact_out);
+
+/* Per-cluster kinetic and potential energy (nclusters doubles each) at the time of
+ * the last global block step (Eq. 2 with the softened potential, FP32 pair terms
+ * on double-single positions summed with compensation, FP64 totals). */
+int gd_ens_energy(gd_ens *s, double *K, double *U);
+
+/* Concatenated state (cluster order, as given to gd_ens_init); any pointer may be NULL. */
+int gd_ens_get_state(gd_ens *s, double *x, double *v, int64_t *tau, int64_t *dtau);
+
+/* Counters over all clusters (interactions count only pairs within a cluster). */
+int gd_ens_get_stats(gd_ens *s, gd_stats *st);
+
+void gd_ens_free(gd_ens *s);
+const char *gd_ens_last_error(const gd_ens *s);
+
 /* ---- allocation-free variant ---------------------------------------------
  *
  * The paper has no counterpart of this entry point; it exists for callers that

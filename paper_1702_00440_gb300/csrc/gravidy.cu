@@ -16,6 +16,7 @@
 
 #include "gravidy.h"
 #include "kernels.cuh"
+#include "ensemble.cuh"
 
 using namespace gdk;
 
@@ -454,8 +455,12 @@ void gd_opts_default(gd_opts *o)
     o->fused = 0;
 }
 
-int gd_init(gd_ctx **out, int64_t n, const double *m, const double *x, const double *v, double eps, double eta,
-            const gd_opts *opt)
+}  // extern "C"
+
+namespace {
+
+int ctx_init(gd_ctx **out, int64_t n, const double *m, const double *x, const double *v, double eps, double eta,
+             const gd_opts *opt, bool run_first_forces)
 {
     if (!out) return fail(nullptr, GD_EINVAL, "out is null");
     *out = nullptr;
@@ -591,10 +596,22 @@ int gd_init(gd_ctx **out, int64_t n, const double *m, const double *x, const dou
         k_init_pads<<<(d.npad - d.n + 127) / 128, 128, 0, c->stream>>>(d);
         c->launches += 1;
     }
-    if ((rc = first_forces(c))) return bail(rc);
-    if (o.autotune && (rc = autotune(c, 3))) return bail(rc);
+    if (run_first_forces) {
+        if ((rc = first_forces(c))) return bail(rc);
+        if (o.autotune && (rc = autotune(c, 3))) return bail(rc);
+    }
     *out = c;
     return GD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gd_init(gd_ctx **out, int64_t n, const double *m, const double *x, const double *v, double eps, double eta,
+            const gd_opts *opt)
+{
+    return ctx_init(out, n, m, x, v, eps, eta, opt, true);
 }
 
 int gd_autotune(gd_ctx *c, int32_t reps)
@@ -910,6 +927,318 @@ int gd_replay_step(gd_ctx *c, int64_t tick_next, const int32_t *idx, int64_t nac
     c->launches += 2;
     CK(cudaGetLastError());
     return sync_ctrl(c);
+}
+
+}  // extern "C"
+
+// ================================================================ ensembles of clusters
+
+struct gd_ens {
+    gd_ctx *c;           // the padded particle array runs through a single-system context
+    Ens e;
+    int C;
+    std::vector<int> cs, cnp, cn;  // host copies of the cluster layout
+    int64_t nreal;
+    int *d_cs, *d_cnp, *d_cn, *d_cnact, *d_pcl;
+    unsigned int *d_tilecnt;
+    float *d_part;
+    double *d_K, *d_U;
+    cudaGraphExec_t graph;
+    int grid_ens;
+    std::string err;
+};
+
+namespace {
+
+int ens_fail(gd_ens *s, int code, const std::string &msg)
+{
+    if (s)
+        s->err = msg;
+    else
+        g_init_err = msg;
+    return code;
+}
+
+void ens_free_dev(gd_ens *s)
+{
+    void *ps[] = {s->d_cs, s->d_cnp, s->d_cn, s->d_cnact, s->d_pcl, s->d_tilecnt, s->d_part, s->d_K, s->d_U};
+    for (void *p : ps)
+        if (p) cudaFree(p);
+    if (s->graph) cudaGraphExecDestroy(s->graph);
+}
+
+void ens_launch_step(gd_ens *s)
+{
+    gd_ctx *c = s->c;
+    k_ens_select<<<c->grid_sel, ST, 0, c->stream>>>(c->d, s->e, c->nchunks);
+    const EArgs a{c->d, s->e, 1};
+    if (c->soft)
+        k_ens_force<true><<<s->grid_ens, FT, 0, c->stream>>>(a);
+    else
+        k_ens_force<false><<<s->grid_ens, FT, 0, c->stream>>>(a);
+    c->launches += 2;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gd_ens_init(gd_ens **out, int32_t nclusters, const int64_t *n_per, const double *m, const double *x,
+                const double *v, double eps, double eta, const gd_opts *opt)
+{
+    if (!out) return ens_fail(nullptr, GD_EINVAL, "out is null");
+    *out = nullptr;
+    if (nclusters < 1 || nclusters > ENS_CMAX)
+        return ens_fail(nullptr, GD_EINVAL, "nclusters must be in [1, " + std::to_string(ENS_CMAX) + "]");
+    if (!n_per || !m || !x || !v) return ens_fail(nullptr, GD_EINVAL, "n_per, m, x, v are required");
+    gd_opts o;
+    gd_opts_default(&o);
+    if (opt) o = *opt;
+    if (o.precision != GD_MIXED) return ens_fail(nullptr, GD_EINVAL, "ensembles run in GD_MIXED precision");
+    // padded layout
+    std::vector<int> cs(nclusters), cnp(nclusters), cn(nclusters);
+    long long total = 0, nreal = 0;
+    for (int q = 0; q < nclusters; q++) {
+        if (n_per[q] < 1 || n_per[q] > (1 << 24)) return ens_fail(nullptr, GD_EINVAL, "cluster sizes must be in [1, 2^24]");
+        cn[q] = (int)n_per[q];
+        cnp[q] = (cn[q] + ST - 1) / ST * ST;
+        cs[q] = (int)total;
+        total += cnp[q];
+        nreal += cn[q];
+    }
+    if (total > INT_MAX / 8) return ens_fail(nullptr, GD_EINVAL, "ensemble too large");
+    std::vector<double> pm((size_t)total, 0.0), px((size_t)total * 3, 0.0), pv((size_t)total * 3, 0.0);
+    // pads: massless, spread out far apart so no two particles coincide
+    for (int q = 0; q < nclusters; q++)
+        for (int i = cs[q] + cn[q]; i < cs[q] + cnp[q]; i++) {
+            px[3 * (size_t)i] = 1.0e6 + 10.0 * i;
+            px[3 * (size_t)i + 1] = 1.0e6;
+            px[3 * (size_t)i + 2] = 1.0e6;
+        }
+    {
+        long long r = 0;
+        for (int q = 0; q < nclusters; q++)
+            for (int i = cs[q]; i < cs[q] + cn[q]; i++, r++) {
+                pm[i] = m[r];
+                for (int k = 0; k < 3; k++) {
+                    px[3 * (size_t)i + k] = x[3 * r + k];
+                    pv[3 * (size_t)i + k] = v[3 * r + k];
+                }
+            }
+    }
+    gd_ens *s = new (std::nothrow) gd_ens();
+    if (!s) return ens_fail(nullptr, GD_ENOMEM, "host allocation failed");
+    s->C = nclusters;
+    s->cs = cs;
+    s->cnp = cnp;
+    s->cn = cn;
+    s->nreal = nreal;
+    auto bail = [&](int code) {
+        if (code != GD_OK && s->err.empty()) s->err = g_init_err;
+        g_init_err = s->err;
+        ens_free_dev(s);
+        if (s->c) gd_free(s->c);
+        delete s;
+        return code;
+    };
+    // the underlying context on the padded array (its single-system first forces are
+    // skipped: the per-cluster ones follow)
+    gd_opts oc = o;
+    oc.autotune = 0;
+    oc.fused = 0;
+    int rc = ctx_init(&s->c, total, pm.data(), px.data(), pv.data(), eps, eta, &oc, false);
+    if (rc) return bail(rc);
+    gd_ctx *c = s->c;
+    cudaError_t e = cudaSuccess;
+    auto al = [&](void **p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes + 16);
+    };
+    const int ntiles = (int)(total / ENS_TILE) + nclusters + 16;
+    int sms = 0, occ = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, o.device);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->soft ? k_ens_force<true> : k_ens_force<false>, FT, 0);
+    s->grid_ens = sms * std::max(1, occ);
+    const int target = 2 * s->grid_ens;
+    const long long part_items = (long long)target + ntiles + 16;
+    al((void **)&s->d_cs, sizeof(int) * nclusters);
+    al((void **)&s->d_cnp, sizeof(int) * nclusters);
+    al((void **)&s->d_cn, sizeof(int) * nclusters);
+    al((void **)&s->d_cnact, sizeof(int) * nclusters);
+    al((void **)&s->d_pcl, sizeof(int) * total);
+    al((void **)&s->d_tilecnt, sizeof(unsigned int) * ntiles);
+    al((void **)&s->d_part, sizeof(float) * ENS_PART * part_items);
+    al((void **)&s->d_K, sizeof(double) * nclusters);
+    al((void **)&s->d_U, sizeof(double) * nclusters);
+    if (e != cudaSuccess) return bail(ens_fail(s, GD_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)));
+    std::vector<int> pcl((size_t)total);
+    for (int q = 0; q < nclusters; q++)
+        for (int i = cs[q]; i < cs[q] + cnp[q]; i++) pcl[i] = q;
+    e = cudaMemcpy(s->d_cs, cs.data(), sizeof(int) * nclusters, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_cnp, cnp.data(), sizeof(int) * nclusters, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_cn, cn.data(), sizeof(int) * nclusters, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_pcl, pcl.data(), sizeof(int) * total, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(s->d_tilecnt, 0, sizeof(unsigned int) * ntiles);
+    if (e != cudaSuccess) return bail(ens_fail(s, GD_ECUDA, std::string("upload: ") + cudaGetErrorString(e)));
+    s->e = Ens{nclusters, s->d_cs, s->d_cnp, s->d_cn, s->d_cnact, s->d_pcl, s->d_tilecnt, s->d_part,
+               s->d_K, s->d_U, target};
+    // per-cluster first forces (Sec. 2.4 steps 3-4): every real particle active
+    Dev &d = c->d;
+    {
+        cudaStream_t st = c->stream;
+        cudaMemsetAsync(d.a, 0, sizeof(double) * 3 * d.n, st);
+        cudaMemsetAsync(d.jk, 0, sizeof(double) * 3 * d.n, st);
+        cudaMemsetAsync(d.tau, 0, sizeof(long long) * d.n, st);
+        k_predict_all<true><<<(d.n + 255) / 256, 256, 0, st>>>(d, 0);
+        k_iota<<<(d.n + 255) / 256, 256, 0, st>>>(d.act, d.n);
+        k_ens_set_counts<<<(nclusters + 127) / 128, 128, 0, st>>>(s->e);
+        const EArgs a0{d, s->e, 0};
+        if (c->soft)
+            k_ens_force<true><<<s->grid_ens, FT, 0, st>>>(a0);
+        else
+            k_ens_force<false><<<s->grid_ens, FT, 0, st>>>(a0);
+        k_ens_init_steps<<<(d.n + 255) / 256, 256, 0, st>>>(d, s->e);
+        k_resync<<<1, 1024, 0, st>>>(d);
+        c->launches += 6;
+        Ctrl h;
+        e = cudaMemcpyAsync(&h, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return bail(ens_fail(s, GD_ECUDA, std::string("first forces: ") + cudaGetErrorString(e)));
+        // statistics restart for the ensemble: the initial evaluation is per cluster
+        double inter0 = 0.0;
+        for (int q = 0; q < nclusters; q++) inter0 += (double)cn[q] * (double)cn[q];
+        h.interactions = inter0;
+        h.nblock = 0;
+        h.nsteps = 0;
+        e = cudaMemcpyAsync(d.ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return bail(ens_fail(s, GD_ECUDA, std::string("first forces: ") + cudaGetErrorString(e)));
+        if ((rc = sync_ctrl(c))) return bail(ens_fail(s, rc, c->err));
+    }
+    *out = s;
+    return GD_OK;
+}
+
+int gd_ens_evolve(gd_ens *s, double t_end)
+{
+    if (!s) return ens_fail(nullptr, GD_EINVAL, "null ensemble");
+    gd_ctx *c = s->c;
+    int rc = check_usable(c);
+    if (rc) return ens_fail(s, rc, c->err);
+    if (!std::isfinite(t_end)) return ens_fail(s, GD_EINVAL, "t_end must be finite");
+    const long long tick_end = (long long)std::floor(t_end / c->d.dt_min);
+    if (tick_end < c->h_ctrl->T_last) return ens_fail(s, GD_EINVAL, "t_end is before the current time");
+    const int G = c->graph_steps;
+    if (c->opt.use_graph && !s->graph) {
+        cudaGraph_t g;
+        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        const long long before = c->launches;
+        for (int q = 0; q < G; q++) ens_launch_step(s);
+        c->launches = before;
+        if (e == cudaSuccess) e = cudaStreamEndCapture(c->stream, &g);
+        if (e == cudaSuccess) {
+            e = cudaGraphInstantiate(&s->graph, g, 0);
+            cudaGraphDestroy(g);
+        }
+        if (e != cudaSuccess) return ens_fail(s, GD_ECUDA, std::string("graph: ") + cudaGetErrorString(e));
+    }
+    k_set_tick_end<<<1, 1, 0, c->stream>>>(c->d.ctrl, tick_end);
+    for (;;) {
+        if (s->graph) {
+            if (cudaGraphLaunch(s->graph, c->stream) != cudaSuccess) return ens_fail(s, GD_ECUDA, "graph launch");
+            c->launches += 2LL * G;
+        } else {
+            for (int q = 0; q < G; q++) ens_launch_step(s);
+        }
+        if (cudaGetLastError() != cudaSuccess) return ens_fail(s, GD_ECUDA, "launch");
+        if ((rc = sync_ctrl(c))) return ens_fail(s, rc, c->err);
+        if (c->h_ctrl->T_cur > tick_end) break;
+    }
+    k_set_tick_end<<<1, 1, 0, c->stream>>>(c->d.ctrl, LLONG_MAX);
+    if ((rc = sync_ctrl(c))) return ens_fail(s, rc, c->err);
+    return GD_OK;
+}
+
+int gd_ens_step_block(gd_ens *s, double *t_out, int64_t *nact_out)
+{
+    if (!s) return ens_fail(nullptr, GD_EINVAL, "null ensemble");
+    gd_ctx *c = s->c;
+    int rc = check_usable(c);
+    if (rc) return ens_fail(s, rc, c->err);
+    ens_launch_step(s);
+    if (cudaGetLastError() != cudaSuccess) return ens_fail(s, GD_ECUDA, "launch");
+    if ((rc = sync_ctrl(c))) return ens_fail(s, rc, c->err);
+    if (t_out) *t_out = (double)c->h_ctrl->T_last * c->d.dt_min;
+    if (nact_out) *nact_out = c->h_ctrl->last_nact;
+    return GD_OK;
+}
+
+int gd_ens_energy(gd_ens *s, double *K, double *U)
+{
+    if (!s) return ens_fail(nullptr, GD_EINVAL, "null ensemble");
+    gd_ctx *c = s->c;
+    int rc = check_usable(c);
+    if (rc) return ens_fail(s, rc, c->err);
+    const long long T = c->h_ctrl->T_last;
+    Dev &d = c->d;
+    k_predict_all<false><<<(d.n + 255) / 256, 256, 0, c->stream>>>(d, T);
+    k_predict_all<true><<<(d.n + 255) / 256, 256, 0, c->stream>>>(d, T);
+    k_ens_energy_terms<<<d.npad / ET, ET, 0, c->stream>>>(d, s->e);
+    k_ens_energy_sum<<<s->C, 256, 0, c->stream>>>(d, s->e);
+    c->launches += 4;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && K) e = cudaMemcpyAsync(K, s->d_K, sizeof(double) * s->C, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && U) e = cudaMemcpyAsync(U, s->d_U, sizeof(double) * s->C, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return ens_fail(s, GD_ECUDA, std::string("energy: ") + cudaGetErrorString(e));
+    if ((rc = sync_ctrl(c))) return ens_fail(s, rc, c->err);
+    return GD_OK;
+}
+
+int gd_ens_get_state(gd_ens *s, double *x, double *v, int64_t *tau, int64_t *dtau)
+{
+    if (!s) return ens_fail(nullptr, GD_EINVAL, "null ensemble");
+    gd_ctx *c = s->c;
+    const long long n = c->d.n;
+    std::vector<double> bx((size_t)3 * n), bv((size_t)3 * n), ba((size_t)3 * n), bj((size_t)3 * n);
+    std::vector<int64_t> bt((size_t)n), bd((size_t)n);
+    int rc = gd_get_state(c, bx.data(), bv.data(), ba.data(), bj.data(), bt.data(), bd.data());
+    if (rc) return ens_fail(s, rc, c->err);
+    long long r = 0;
+    for (int q = 0; q < s->C; q++)
+        for (int i = s->cs[q]; i < s->cs[q] + s->cn[q]; i++, r++) {
+            for (int k = 0; k < 3; k++) {
+                if (x) x[3 * r + k] = bx[3 * (size_t)i + k];
+                if (v) v[3 * r + k] = bv[3 * (size_t)i + k];
+            }
+            if (tau) tau[r] = bt[i];
+            if (dtau) dtau[r] = bd[i];
+        }
+    return GD_OK;
+}
+
+int gd_ens_get_stats(gd_ens *s, gd_stats *st)
+{
+    if (!s) return ens_fail(nullptr, GD_EINVAL, "null ensemble");
+    const int rc = gd_get_stats(s->c, st);
+    return rc ? ens_fail(s, rc, s->c->err) : GD_OK;
+}
+
+void gd_ens_free(gd_ens *s)
+{
+    if (!s) return;
+    if (s->c) {
+        cudaSetDevice(s->c->dev);
+        cudaStreamSynchronize(s->c->stream);
+    }
+    ens_free_dev(s);
+    if (s->c) gd_free(s->c);
+    delete s;
+}
+
+const char *gd_ens_last_error(const gd_ens *s)
+{
+    if (!s) return g_init_err.c_str();
+    return s->err.c_str();
 }
 
 }  // extern "C"

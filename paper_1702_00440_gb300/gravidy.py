@@ -27,6 +27,8 @@ EXPORTS = (
     "gd_opts_default", "gd_init", "gd_evolve", "gd_step_block", "gd_energy", "gd_get_state",
     "gd_set_state", "gd_get_stats", "gd_kernel_time", "gd_free", "gd_last_error", "gd_force",
     "gd_predict", "gd_active", "gd_replay_step", "gd_force_noalloc", "gd_autotune", "gd_get_tuning",
+    "gd_ens_init", "gd_ens_evolve", "gd_ens_step_block", "gd_ens_energy", "gd_ens_get_state",
+    "gd_ens_get_stats", "gd_ens_free", "gd_ens_last_error",
 )
 
 
@@ -105,6 +107,14 @@ def load(build_if_missing: bool = True):
             "gd_force_noalloc": (ctypes.c_int, [I64, P, P, P, D, P, I64, P, P, P]),
             "gd_autotune": (ctypes.c_int, [P, I32]),
             "gd_get_tuning": (ctypes.c_int, [P, P, P, P, P, I32]),
+            "gd_ens_init": (ctypes.c_int, [P, I32, P, P, P, P, D, D, P]),
+            "gd_ens_evolve": (ctypes.c_int, [P, D]),
+            "gd_ens_step_block": (ctypes.c_int, [P, P, P]),
+            "gd_ens_energy": (ctypes.c_int, [P, P, P]),
+            "gd_ens_get_state": (ctypes.c_int, [P, P, P, P, P]),
+            "gd_ens_get_stats": (ctypes.c_int, [P, P]),
+            "gd_ens_free": (None, [P]),
+            "gd_ens_last_error": (ctypes.c_char_p, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -338,3 +348,73 @@ class Integrator:
 
     def replay_step(self, tick, idx):
         gd_replay_step(self._h, tick, idx)
+
+
+def _check_ens(rc, h=None):
+    if rc != GD_OK:
+        msg = load().gd_ens_last_error(h)
+        raise GravidyError(rc, msg.decode() if msg else "error")
+
+
+class Ensemble:
+    """gd_ens: independent clusters advanced together (mixed precision)."""
+
+    def __init__(self, sizes, m, x, v, eps, eta, **opts):
+        lib = load()
+        sizes = np.ascontiguousarray(sizes, dtype=np.int64)
+        self.sizes = sizes
+        self.C = int(sizes.size)
+        self.n = int(sizes.sum())
+        m = np.ascontiguousarray(np.asarray(m, dtype=np.float64))
+        x = _f64(x, (self.n, 3))
+        v = _f64(v, (self.n, 3))
+        opts.setdefault("precision", "mixed")
+        o = make_opts(**opts)
+        self.dt_min = o.dt_min
+        h = ctypes.c_void_p()
+        _check_ens(lib.gd_ens_init(ctypes.byref(h), self.C, _p(sizes), _p(m), _p(x), _p(v), float(eps), float(eta),
+                                   ctypes.byref(o)))
+        self._h = h
+
+    def close(self):
+        h, self._h = getattr(self, "_h", None), None
+        if h is not None and h.value:
+            load().gd_ens_free(h)
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def evolve(self, t_end):
+        _check_ens(load().gd_ens_evolve(self._h, float(t_end)), self._h)
+
+    def step_block(self):
+        t = ctypes.c_double()
+        k = ctypes.c_int64()
+        _check_ens(load().gd_ens_step_block(self._h, ctypes.byref(t), ctypes.byref(k)), self._h)
+        return t.value, k.value
+
+    def energy(self):
+        K = np.empty(self.C)
+        U = np.empty(self.C)
+        _check_ens(load().gd_ens_energy(self._h, _p(K), _p(U)), self._h)
+        return K, U
+
+    def state(self):
+        x = np.empty((self.n, 3))
+        v = np.empty((self.n, 3))
+        tau = np.empty(self.n, np.int64)
+        dtau = np.empty(self.n, np.int64)
+        _check_ens(load().gd_ens_get_state(self._h, _p(x), _p(v), _p(tau), _p(dtau)), self._h)
+        return dict(x=x, v=v, tau=tau, dtau=dtau)
+
+    def stats(self):
+        s = gd_stats()
+        _check_ens(load().gd_ens_get_stats(self._h, ctypes.byref(s)), self._h)
+        return dict(tick=s.tick, block_steps=s.block_steps, particle_steps=s.particle_steps,
+                    interactions=s.interactions, last_nact=s.last_nact, kernel_launches=s.kernel_launches)

@@ -1,0 +1,101 @@
+"""Ensembles of independent clusters (gd_ens_*) against single-system runs of
+each cluster and against the oracle.
+
+A cluster in an ensemble follows the same scheme as the cluster alone; only
+the j-split of the force sums (so the last bits of the forces) differs, so the
+block schedules agree and the states agree to round-off growth over the run.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1702_00440_gb300 import gravidy, inputs
+
+pytestmark = pytest.mark.gpu
+
+EPS = 1e-4
+ETA = 0.01
+U32 = 2.0 ** -24
+SIZES = [200, 300, 513, 129, 64, 777]
+
+
+def _clusters(sizes, seed0=100):
+    ms, xs, vs = [], [], []
+    for q, n in enumerate(sizes):
+        m, x, v = inputs.plummer(n, seed=seed0 + q)
+        ms.append(m)
+        xs.append(x)
+        vs.append(v)
+    return ms, xs, vs
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    gravidy.load()
+    oracle.build()
+
+
+def test_ensemble_energy_matches_oracle_per_cluster():
+    ms, xs, vs = _clusters(SIZES)
+    with gravidy.Ensemble(SIZES, np.concatenate(ms), np.concatenate(xs), np.concatenate(vs), EPS, ETA) as e:
+        K, U = e.energy()
+    for q in range(len(SIZES)):
+        Ko, Uo = oracle.energy(ms[q], xs[q], vs[q], EPS)
+        assert K[q] == pytest.approx(Ko, rel=1e-13)
+        assert U[q] == pytest.approx(Uo, rel=8 * U32)
+
+
+def test_ensemble_follows_each_cluster_alone():
+    ms, xs, vs = _clusters(SIZES)
+    t_end = 0.25
+    with gravidy.Ensemble(SIZES, np.concatenate(ms), np.concatenate(xs), np.concatenate(vs), EPS, ETA) as e:
+        K0, U0 = e.energy()
+        e.evolve(t_end)
+        K1, U1 = e.energy()
+        st = e.state()
+        es = e.stats()
+    off = np.concatenate([[0], np.cumsum(SIZES)])
+    psteps = 0
+    for q, n in enumerate(SIZES):
+        sl = slice(off[q], off[q + 1])
+        with gravidy.Integrator(ms[q], xs[q], vs[q], EPS, ETA, precision="mixed") as g:
+            g.evolve(t_end)
+            so = g.state()
+            psteps += g.stats()["particle_steps"]
+        agree = np.mean(st["dtau"][sl] == so["dtau"])
+        dx = np.abs(st["x"][sl] - so["x"]).max()
+        assert (st["tau"][sl] == int(t_end / 2.0 ** -22)).all()
+        assert agree > 0.99, agree
+        assert dx < 1e-6, dx
+        # energy error of the cluster vs the oracle's for the same cluster
+        sim = oracle.Sim(ms[q], xs[q], vs[q], EPS, ETA)
+        Ko, Uo = sim.energy()
+        sim.evolve(t_end)
+        Ko1, Uo1 = sim.energy()
+        de_or = abs((Ko1 + Uo1 - Ko - Uo) / (Ko + Uo))
+        de = abs((K1[q] + U1[q] - K0[q] - U0[q]) / (K0[q] + U0[q]))
+        print("cluster %d n=%d: dtau agree %.4f max|dx| %.1e |dE/E| ens %.2e oracle %.2e" % (q, n, agree, dx, de, de_or))
+        assert de <= 2 * de_or + 2e-9
+    # the ensemble's particle steps are the clusters' particle steps
+    assert abs(es["particle_steps"] - psteps) <= 0.01 * psteps
+
+
+def test_ensemble_block_steps_interleave():
+    ms, xs, vs = _clusters([256, 1000], seed0=7)
+    with gravidy.Ensemble([256, 1000], np.concatenate(ms), np.concatenate(xs), np.concatenate(vs), EPS, ETA) as e:
+        last = 0.0
+        for _ in range(200):
+            t, nact = e.step_block()
+            assert t > last and nact >= 1
+            last = t
+        st = e.state()
+    assert (st["tau"] % st["dtau"] == 0).all()
+    assert ((st["dtau"] & (st["dtau"] - 1)) == 0).all()
+
+
+def test_ensemble_rejects_fp64_and_bad_sizes():
+    m, x, v = inputs.plummer(64, seed=1)
+    with pytest.raises(gravidy.GravidyError):
+        gravidy.Ensemble([64], m, x, v, EPS, ETA, precision="fp64")
+    with pytest.raises(gravidy.GravidyError):
+        gravidy.Ensemble([0, 64], m, x, v, EPS, ETA)
