@@ -71,6 +71,9 @@ def _args():
                         "set size); accuracy = N=16384 FP64 vs mixed to t=1; ensemble = 256 clusters of "
                         "log-uniform N in [256, 8192] to t=--ens-t, one ensemble vs the clusters one by one")
     p.add_argument("--ens-t", type=float, default=0.125)
+    p.add_argument("--profile-nact", type=int, default=0, metavar="K",
+                   help="profiling hook: autotune on the --n workload, then evaluate the force of K random "
+                        "particles twice (gd_force), print the tuning table and exit")
     p.add_argument("--profile-steps", type=int, default=0, metavar="K",
                    help="profiling hook: initialise the --n workload and take K block steps one by one "
                         "(no graph), print nothing and exit")
@@ -656,8 +659,25 @@ def profile_steps(a):
     return 0
 
 
+def profile_nact(a):
+    from paper_1702_00440_gb300 import gravidy, inputs
+
+    m, x, v = inputs.plummer(a.n, seed=1)
+    with gravidy.Integrator(m, x, v, EPS, ETA, precision=a.precision, autotune=True) as g:
+        mc, split, mode, ms = g.tuning()
+        nb = int(np.log2(a.n)) + 1
+        print(json.dumps({"n": a.n, "split": split[:nb].tolist(), "mode": mode[:nb].tolist(),
+                          "us": [round(1e3 * float(t), 2) for t in ms[:nb]]}))
+        idx = inputs.random_subset(a.n, a.profile_nact, seed=5)
+        g.force(0, idx)
+        g.force(0, idx)
+    return 0
+
+
 def main():
     a = _args()
+    if a.profile_nact:
+        return profile_nact(a)
     if a.profile_force:
         return profile_force(a)
     if a.profile_steps:

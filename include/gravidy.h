@@ -74,6 +74,11 @@ typedef struct gd_opts {
                            one fused kernel with grid barriers; 0 = three kernels per block step
                            (graph or eager, see use_graph; the default, faster on GB300 at the
                            sizes measured).  Both compute the same results bit for bit. */
+    int32_t pdl;        /* three-kernel path: 1 = launch the step kernels with programmatic
+                           dependent launch (each may start while the previous finishes) */
+    int32_t tail_correct; /* three-kernel path: 1 = the force kernel corrects warp-mode tiles in
+                           their reduction tails and finalizes the step (k_correct then only
+                           handles i-parallel plans); 0 = k_correct always corrects */
 } gd_opts;
 
 typedef struct gd_stats {

@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(ST) k_ens_select(Dev d, Ens e, int nchunks)
         {
             const double dt = (double)(T - ldc(&d.tau[i])) * d.dt_min;
             double xp[3], vp[3];
-            predict64(d, i, dt, xp, vp);
+            predict64<false>(d, i, dt, xp, vp);
             store_jrec<true>(d, i, xp, vp, d.m[i]);
         }
         const unsigned ballot = __ballot_sync(0xffffffffu, act);
@@ -254,29 +254,45 @@ __device__ void ens_plan(const Ens &e, EnsPlanSmem &p)
     __syncthreads();
 }
 
-// Sums the S partials of the ENS_TILE slots of a tile (fixed order) into fsum.
+// Sums the S partials of the ENS_TILE slots of a tile into fsum: every thread takes
+// the items s = t, t + FT, ... (all 48 values of an item are contiguous: twelve
+// float4 loads at once), then a warp-shuffle tree and a four-warp sum in a fixed
+// order.
 __device__ void ens_tile_reduce(const Dev &d, const Ens &e, int item0, int S, int slot0, int nvalid)
 {
-    __shared__ DS s_acc[FT];
-    const int t = threadIdx.x;
-    const int npairs = nvalid * 6;
-    const int G = FT / npairs;  // npairs <= 48, so G >= 2
-    const int pidx = t / G, sub = t % G;
-    DS a;
-    a.zero();
-    if (pidx < npairs) {
-        const int k = pidx / 6, comp = pidx % 6;
-        for (int s = sub; s < S; s += G) a.add(__ldcg(e.part + ((long long)(item0 + s) * ENS_TILE + k) * 6 + comp));
-    }
-    s_acc[t] = a;
-    __syncthreads();
-    if (pidx < npairs && sub == 0) {
-        for (int q = 1; q < G; q++) {
-            a.add(s_acc[t + q].h);
-            a.add(s_acc[t + q].l);
+    __shared__ float s_w[FT / 32][ENS_PART];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    float acc[ENS_PART];
+#pragma unroll
+    for (int q = 0; q < ENS_PART; q++) acc[q] = 0.f;
+    for (int s = t; s < S; s += FT) {
+        const float4 *p4 = (const float4 *)(e.part + (long long)(item0 + s) * ENS_PART);
+        float4 v[ENS_PART / 4];
+#pragma unroll
+        for (int q = 0; q < ENS_PART / 4; q++) v[q] = __ldcg(p4 + q);
+#pragma unroll
+        for (int q = 0; q < ENS_PART / 4; q++) {
+            acc[4 * q] += v[q].x;
+            acc[4 * q + 1] += v[q].y;
+            acc[4 * q + 2] += v[q].z;
+            acc[4 * q + 3] += v[q].w;
         }
-        const int k = pidx / 6, comp = pidx % 6;
-        d.fsum[(long long)comp * d.n + slot0 + k] = a.as_double();
+    }
+#pragma unroll
+    for (int q = 0; q < ENS_PART; q++)
+        for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < ENS_PART; q++) s_w[warp][q] = acc[q];
+    }
+    __syncthreads();
+    if (t < ENS_PART) {
+        const int k = t / 6, comp = t % 6;
+        if (k < nvalid) {
+            double sum = 0.0;
+            for (int w = 0; w < FT / 32; w++) sum += (double)s_w[w][t];
+            d.fsum[(long long)comp * d.n + slot0 + k] = sum;
+        }
     }
     __syncthreads();
 }
@@ -392,7 +408,7 @@ __global__ void __launch_bounds__(FT, 2) k_ens_force(EArgs a)
         if (s_last) {
             __threadfence();
             ens_tile_reduce(d, e, p.item_base[c] + tl * S, S, slot0, nvalid);
-            if (a.correct) correct_slots(d, T, slot0, slot0 + nvalid, warp, FT / 32, mymin, bad);
+            if (a.correct) correct_slots<false>(d, T, slot0, slot0 + nvalid, warp, FT / 32, mymin, bad);
         }
         __syncthreads();
     }

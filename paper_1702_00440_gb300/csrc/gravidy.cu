@@ -11,6 +11,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -96,25 +97,50 @@ Tune effective_tune(const gd_ctx *c)
     return t;
 }
 
-FArgs fargs(const gd_ctx *c) { return FArgs{c->d, c->grid_force, effective_tune(c)}; }
+FArgs fargs(const gd_ctx *c, int tail_ok) { return FArgs{c->d, c->grid_force, effective_tune(c), tail_ok}; }
+
+// Launch with programmatic stream serialisation: the kernel may start while the
+// previous one finishes and waits for it in pdl_wait().
+template <typename... P, typename... A>
+void launch_pdl(bool pdl, void (*kern)(P...), int grid, int block, cudaStream_t st, A &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
+}
 
 void launch_force_with(gd_ctx *c, const FArgs &fa)
 {
     c->launches += 1;
+    const bool p = c->opt.pdl != 0;
+    const int gr = c->grid_force;
     if (c->mixed) {
-        if (c->soft)
-            k_force_mixed<true><<<c->grid_force, FT, 0, c->stream>>>(fa);
+        if (fa.tail_ok)
+            c->soft ? launch_pdl(p, k_force_mixed<true, true>, gr, FT, c->stream, fa)
+                    : launch_pdl(p, k_force_mixed<false, true>, gr, FT, c->stream, fa);
         else
-            k_force_mixed<false><<<c->grid_force, FT, 0, c->stream>>>(fa);
+            c->soft ? launch_pdl(p, k_force_mixed<true, false>, gr, FT, c->stream, fa)
+                    : launch_pdl(p, k_force_mixed<false, false>, gr, FT, c->stream, fa);
     } else {
-        if (c->soft)
-            k_force_fp64<true><<<c->grid_force, FT, 0, c->stream>>>(fa);
+        if (fa.tail_ok)
+            c->soft ? launch_pdl(p, k_force_fp64<true, true>, gr, FT, c->stream, fa)
+                    : launch_pdl(p, k_force_fp64<false, true>, gr, FT, c->stream, fa);
         else
-            k_force_fp64<false><<<c->grid_force, FT, 0, c->stream>>>(fa);
+            c->soft ? launch_pdl(p, k_force_fp64<true, false>, gr, FT, c->stream, fa)
+                    : launch_pdl(p, k_force_fp64<false, false>, gr, FT, c->stream, fa);
     }
 }
 
-void launch_force(gd_ctx *c) { launch_force_with(c, fargs(c)); }
+// force only (no correction): hooks, initial forces, autotuner
+void launch_force(gd_ctx *c) { launch_force_with(c, fargs(c, 0)); }
 
 void launch_predict_all(gd_ctx *c, long long tick, bool mixed_records)
 {
@@ -130,23 +156,29 @@ void launch_select(gd_ctx *c, int slot)
 {
     c->launches += 1;
     if (c->mixed)
-        k_select_predict<true><<<c->grid_sel, ST, 0, c->stream>>>(c->d, slot, c->nchunks);
+        launch_pdl(c->opt.pdl != 0, k_select_predict<true>, c->grid_sel, ST, c->stream, c->d, slot, c->nchunks);
     else
-        k_select_predict<false><<<c->grid_sel, ST, 0, c->stream>>>(c->d, slot, c->nchunks);
+        launch_pdl(c->opt.pdl != 0, k_select_predict<false>, c->grid_sel, ST, c->stream, c->d, slot, c->nchunks);
 }
+
+// The force of a block step: warp-mode tiles are corrected in the force kernel's
+// tile tails, which then finalizes the step; k_correct handles i-parallel plans.
+void launch_force_step(gd_ctx *c) { launch_force_with(c, fargs(c, c->opt.tail_correct ? 1 : 0)); }
 
 void launch_correct(gd_ctx *c)
 {
     c->launches += 1;
-    k_correct<<<c->grid_corr, CT, 0, c->stream>>>(CArgs{c->d});
+    launch_pdl(c->opt.pdl != 0, k_correct, c->grid_corr, CT, c->stream,
+               CArgs{c->d, c->grid_force, effective_tune(c), c->opt.tail_correct ? 1 : 0, c->mixed ? 1 : 0});
 }
 
-// One free-running block step: select+predict, force, correct.
+// One free-running block step: select+predict, force (+ correction of small
+// tiles), correct (larger plans).
 void launch_step(gd_ctx *c, int slot, cudaEvent_t e0, cudaEvent_t e1, bool capturing)
 {
     launch_select(c, slot);
     if (e0) cudaEventRecordWithFlags(e0, c->stream, capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
-    launch_force(c);
+    launch_force_step(c);
     if (e1) cudaEventRecordWithFlags(e1, c->stream, capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
     launch_correct(c);
 }
@@ -351,7 +383,7 @@ int autotune(gd_ctx *c, int reps)
                 Tune t = base;
                 t.mode_b[b] = (signed char)mode;
                 t.s_fixed[b] = (short)std::min(S, 32767);
-                const FArgs fa{d, c->grid_force, t};
+                const FArgs fa{d, c->grid_force, t, 0};
                 k_set_step<<<1, 1, 0, c->stream>>>(d.ctrl, c->h_ctrl->T_cur, nact);
                 c->launches += 1;
                 launch_force_with(c, fa);  // warm
@@ -453,6 +485,8 @@ void gd_opts_default(gd_opts *o)
     o->time_force = 0;
     o->autotune = 0;
     o->fused = 0;
+    o->pdl = 0;
+    o->tail_correct = 0;
 }
 
 }  // extern "C"
@@ -513,11 +547,11 @@ int ctx_init(gd_ctx **out, int64_t n, const double *m, const double *x, const do
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, o.device);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, o.device);
     if (c->mixed)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->soft ? k_force_mixed<true> : k_force_mixed<false>,
-                                                          FT, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &occ, c->soft ? k_force_mixed<true, false> : k_force_mixed<false, false>, FT, 0);
     else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->soft ? k_force_fp64<true> : k_force_fp64<false>,
-                                                          FT, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &occ, c->soft ? k_force_fp64<true, false> : k_force_fp64<false, false>, FT, 0);
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             &occ_sel, c->mixed ? k_select_predict<true> : k_select_predict<false>, ST, 0);
@@ -921,7 +955,7 @@ int gd_replay_step(gd_ctx *c, int64_t tick_next, const int32_t *idx, int64_t nac
     CK(cudaMemcpyAsync(d.act, stage_i64(c, 0), sizeof(int) * nact, cudaMemcpyHostToDevice, c->stream));
     launch_predict_all(c, tick_next, c->mixed);
     k_set_step<<<1, 1, 0, c->stream>>>(d.ctrl, tick_next, (int)nact);
-    launch_force(c);
+    launch_force_step(c);
     launch_correct(c);
     k_resync<<<1, 1024, 0, c->stream>>>(d);
     c->launches += 2;
@@ -1343,8 +1377,10 @@ int noalloc_setup(int dev, NoAllocDevice **out)
         if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress(g_noalloc_scratch)");
         int sms = 0, occ_s = 0, occ_u = 0;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, k_force_mixed<true>, FT, 0);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_u, k_force_mixed<false>, FT, 0);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, k_force_mixed<true, false>, FT, 0);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_u, k_force_mixed<false, false>, FT, 0);
         if (e != cudaSuccess) return cuda_fail(nullptr, e, "device query");
         s.scratch = (unsigned char *)p;
         s.grid = sms * std::max(1, std::min(occ_s, occ_u));
@@ -1395,11 +1431,11 @@ extern "C" int gd_force_noalloc(int64_t n, const double *m, const double *x, con
     const Tune tn = default_tune(true, 0);
     const int g = std::max((d.npad + 255) / 256, (NOALLOC_TILES + 255) / 256);
     k_noalloc_pack<<<g, 256, 0, st>>>(d, m, x, v, idx, (int)nact, bad);
-    const FArgs fa{d, s->grid, tn};
+    const FArgs fa{d, s->grid, tn, 0};
     if (eps > 0)
-        k_force_mixed<true><<<s->grid, FT, 0, st>>>(fa);
+        k_force_mixed<true, false><<<s->grid, FT, 0, st>>>(fa);
     else
-        k_force_mixed<false><<<s->grid, FT, 0, st>>>(fa);
+        k_force_mixed<false, false><<<s->grid, FT, 0, st>>>(fa);
     k_noalloc_out<<<(int)((nact + 255) / 256), 256, 0, st>>>(d, (int)nact, bad, acc, jerk);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "gd_force_noalloc launch");

@@ -52,6 +52,8 @@ class gd_opts(ctypes.Structure):
         ("time_force", ctypes.c_int32),
         ("autotune", ctypes.c_int32),
         ("fused", ctypes.c_int32),
+        ("pdl", ctypes.c_int32),
+        ("tail_correct", ctypes.c_int32),
     ]
 
 
@@ -139,7 +141,8 @@ def _check(rc, ctx=None):
 
 
 def make_opts(dt_min=2.0 ** -22, dt_max=0.125, precision="mixed", device=0, stream=None, use_graph=True,
-              graph_steps=16, jsplit=0, mode_cut=0, time_force=False, autotune=False, fused=False):
+              graph_steps=16, jsplit=0, mode_cut=0, time_force=False, autotune=False, fused=False, pdl=None,
+              tail_correct=None):
     o = gd_opts()
     load().gd_opts_default(ctypes.byref(o))
     o.dt_min = float(dt_min)
@@ -154,6 +157,10 @@ def make_opts(dt_min=2.0 ** -22, dt_max=0.125, precision="mixed", device=0, stre
     o.time_force = 1 if time_force else 0
     o.autotune = 1 if autotune else 0
     o.fused = 1 if fused else 0
+    if pdl is not None:
+        o.pdl = 1 if pdl else 0
+    if tail_correct is not None:
+        o.tail_correct = 1 if tail_correct else 0
     return o
 
 
