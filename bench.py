@@ -75,8 +75,8 @@ def _args():
                    help="profiling hook: autotune on the --n workload, then evaluate the force of K random "
                         "particles twice (gd_force), print the tuning table and exit")
     p.add_argument("--profile-steps", type=int, default=0, metavar="K",
-                   help="profiling hook: initialise the --n workload and take K block steps one by one "
-                        "(no graph), print nothing and exit")
+                   help="profiling hook: integrate the --n workload to t = 0.375, then advance K/64 "
+                        "N-body time units between cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return p.parse_args()
 
 
@@ -650,12 +650,22 @@ def profile_force(a):
 
 
 def profile_steps(a):
+    """Integrates to t = 0.375 (the start of the timed window), then runs the next
+    1/64 N-body time unit between cudaProfilerStart/Stop, so that
+    `ncu --profile-from-start off` sees only steady-state block steps."""
+    import torch
     from paper_1702_00440_gb300 import gravidy, inputs
 
     m, x, v = inputs.plummer(a.n, seed=1)
-    with gravidy.Integrator(m, x, v, EPS, ETA, precision=a.precision, use_graph=False) as g:
-        for _ in range(a.profile_steps):
-            g.step_block()
+    with gravidy.Integrator(m, x, v, EPS, ETA, precision=a.precision, autotune=True) as g:
+        g.evolve(0.375)
+        s0 = g.stats()
+        torch.cuda.profiler.start()
+        g.evolve(0.375 + a.profile_steps / 64.0)
+        torch.cuda.profiler.stop()
+        s1 = g.stats()
+        print(json.dumps({"block_steps": s1["block_steps"] - s0["block_steps"],
+                          "kernel_launches": s1["kernel_launches"] - s0["kernel_launches"]}))
     return 0
 
 

@@ -935,7 +935,10 @@ int gd_active(gd_ctx *c, int32_t *idx, int64_t *nact, int64_t *tick_next)
     CK(cudaMemcpyAsync(idx, d.act, sizeof(int) * na, cudaMemcpyDeviceToHost, c->stream));
     k_resync<<<1, 1024, 0, c->stream>>>(d);
     c->launches += 1;
-    return sync_ctrl(c);
+    rc = sync_ctrl(c);
+    // the device list is in the order the chunks claimed their places
+    std::sort(idx, idx + na);
+    return rc;
 }
 
 int gd_replay_step(gd_ctx *c, int64_t tick_next, const int32_t *idx, int64_t nact)

@@ -3,9 +3,9 @@
 //
 // One block step (Sec. 2.4 steps 5-7) is three kernels and no host round trip:
 //   k_select_predict  predict every particle to the block time (step 7a) and list
-//                     the active ones in ascending index order (step 5) with a
-//                     single-pass decoupled look-back scan; start the minimum of
-//                     the next block time over the inactive ones.
+//                     the active ones (step 5), each chunk of particles claiming
+//                     its place with one atomic add; start the minimum of the
+//                     next block time over the inactive ones.
 //   k_force_*         force and jerk of the active set against all N predicted
 //                     particles (step 7c, Sec. 2.5): a persistent kernel over
 //                     (i-tile x j-chunk) work items; the j-range is split when the
@@ -64,11 +64,12 @@ struct Ctrl {
     double K, U;           // energy results
     int nact;              // active count of the current step
     int last_nact;
-    unsigned int epoch;    // look-back tag, advanced once per step
+    unsigned int epoch;    // step counter (parity slots of the fused kernel, look-back tag of the ensemble)
     unsigned int done;     // finished-CTA counter of k_correct
     int err;               // first device-side fault (gd_status), 0 = none
     int pad_;
     unsigned long long ph_ns[3];  // fused kernel, CTA 0's clock: select, force, correct phases
+    unsigned long long sel_acc;   // select: arrived chunks (high word), active count (low word); 0 between steps
 };
 
 __device__ __forceinline__ void set_err(Ctrl *c, int code) { atomicCAS(&c->err, 0, code); }
@@ -114,7 +115,7 @@ struct Dev {
     long long cap;            // partial capacity (entries per component)
     double *fsum;             // summed force of active slot k: fsum[c*n + k], c < 3 a, c >= 3 jerk
     unsigned int *tilecnt;    // per i-tile arrival counters (zero between launches)
-    unsigned long long *status;  // look-back words, one per chunk of ST particles
+    unsigned long long *status;  // ensemble look-back words, one per chunk of ST particles
     double *eu, *ek;          // per-particle energy terms
     int *nact_hist;           // nact of each step slot of a captured graph
     unsigned int *bar;        // grid-barrier counters of the fused kernel (see grid_sync)
@@ -188,11 +189,6 @@ __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned lon
 {
     return *(const volatile unsigned long long *)p;
 }
-
-// Publishes a look-back word (flag and value travel in one 64-bit word).  An atomic
-// exchange is performed at L2 at once, where the polling CTAs read; measured about
-// 4 us per block step faster at N = 16384 than a volatile store.
-__device__ __forceinline__ void publish_lb(unsigned long long *p, unsigned long long v) { atomicExch(p, v); }
 
 // Programmatic dependent launch: a kernel launched with programmatic stream
 // serialisation may start while the previous kernel in the stream still runs;
@@ -289,21 +285,23 @@ __device__ __forceinline__ void store_jrec(const Dev &d, int i, const double xp[
 
 // ---------------------------------------------------------------- kernel: select + predict
 
-// Predicts every particle to T = ctrl->T_cur and writes the ascending list of the
-// particles whose next time equals T.  The grid never exceeds the number of CTAs
-// that can be resident at once, and each CTA walks its chunks in increasing order,
-// so a chunk's look-back only waits on chunks that are being or have been
-// processed; every wait is bounded.  `slot` >= 0 records nact in nact_hist[slot].
+// Predicts every particle to T = ctrl->T_cur and writes the list of the particles
+// whose next time equals T (Sec. 2.4 steps 5-6).  Each chunk of ST particles claims
+// its place in the list with one 64-bit atomic add on ctrl->sel_acc: the low word
+// counts active particles (the returned value is the chunk's offset), the high word
+// counts arrived chunks, so the chunk that arrives last knows the total, publishes
+// it as ctrl->nact and clears the word for the next step.  The list is in arrival
+// order, not ascending: every later per-particle computation (force sums over j in
+// a fixed order, correction, step choice) is independent of a particle's slot, so
+// the results do not depend on it.  `slot` >= 0 records nact in nact_hist[slot].
 template <bool MIXED, bool COH>
-__device__ void phase_select(const Dev &d, long long T, unsigned epoch, int slot, int nchunks,
-                             unsigned long long *Tacc)
+__device__ void phase_select(const Dev &d, long long T, int slot, int nchunks, unsigned long long *Tacc)
 {
     Ctrl *ctrl = d.ctrl;
-    __shared__ unsigned s_excl;
+    __shared__ unsigned s_base;
     __shared__ unsigned s_wcnt[ST / 32];
     __shared__ long long s_wmin[ST / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned ep = epoch & 0x3FFFFFFFu;
     long long mn_all = LLONG_MAX;
     for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
         const int i = chunk * ST + threadIdx.x;
@@ -320,66 +318,31 @@ __device__ void phase_select(const Dev &d, long long T, unsigned epoch, int slot
         const unsigned ballot = __ballot_sync(0xffffffffu, act);
         if (lane == 0) s_wcnt[warp] = __popc(ballot);
         __syncthreads();
-        if (warp == 0) {
-            const unsigned cnt = lane < ST / 32 ? s_wcnt[lane] : 0u;
-            unsigned incl = cnt;
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
+        if (threadIdx.x == 0) {
+            unsigned tot = 0;
+#pragma unroll
+            for (int w = 0; w < ST / 32; w++) {
+                const unsigned c = s_wcnt[w];
+                s_wcnt[w] = tot;  // exclusive offset of warp w within the chunk
+                tot += c;
             }
-            const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
-            if (lane < ST / 32) s_wcnt[lane] = incl - cnt;  // exclusive offsets
-            unsigned excl = 0;
-            if (chunk == 0) {
-                if (lane == 0) publish_lb(&d.status[0], lb_pack(ep, 2u, total));
-            } else {
-                if (lane == 0) publish_lb(&d.status[chunk], lb_pack(ep, 1u, total));
-                int base = chunk - 1;
-                int spins = 0;
-                for (;;) {
-                    const int p = base - lane;
-                    unsigned f = 2u, val = 0u;
-                    if (p >= 0) {
-                        const unsigned long long w = ld_volatile_u64(&d.status[p]);
-                        f = ((unsigned)(w >> 34) == ep) ? (unsigned)((w >> 32) & 3u) : 0u;
-                        val = (unsigned)w;
-                    }
-                    const unsigned notready = __ballot_sync(0xffffffffu, f == 0u);
-                    const unsigned prefix = __ballot_sync(0xffffffffu, f == 2u);
-                    const int first = prefix ? __ffs(prefix) - 1 : 31;
-                    const unsigned need = first == 31 ? 0xffffffffu : ((2u << first) - 1u);
-                    if (notready & need) {
-                        if (++spins > SPIN_LIMIT) {
-                            if (lane == 0) set_err(ctrl, ST_ETIMEOUT);
-                            break;
-                        }
-                        __nanosleep(32);
-                        continue;
-                    }
-                    unsigned contrib = lane <= first ? val : 0u;
-                    for (int o = 16; o > 0; o >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
-                    excl += contrib;
-                    if (prefix) break;
-                    base -= 32;
+            const unsigned long long old = atomicAdd(&ctrl->sel_acc, (1ull << 32) | (unsigned long long)tot);
+            s_base = (unsigned)old;
+            if ((unsigned)(old >> 32) == (unsigned)(nchunks - 1)) {
+                // every other chunk has added its count: the total is known
+                unsigned long long na = (unsigned long long)(unsigned)old + tot;
+                if (na > (unsigned long long)d.n) {
+                    set_err(ctrl, ST_ETIMEOUT);
+                    na = 0;
                 }
-                if (lane == 0) publish_lb(&d.status[chunk], lb_pack(ep, 2u, excl + total));
-            }
-            if (lane == 0) {
-                s_excl = excl;
-                if (chunk == nchunks - 1) {
-                    int na = (int)(excl + total);
-                    if (excl + total > (unsigned)d.n) {
-                        set_err(ctrl, ST_ETIMEOUT);
-                        na = 0;
-                    }
-                    ctrl->nact = na;
-                    if (slot >= 0) d.nact_hist[slot] = na;
-                }
+                ctrl->nact = (int)na;
+                if (slot >= 0) d.nact_hist[slot] = (int)na;
+                atomicExch(&ctrl->sel_acc, 0ull);
             }
         }
         __syncthreads();
         if (act) {
-            const unsigned pos = s_excl + s_wcnt[warp] + __popc(ballot & ((1u << lane) - 1u));
+            const unsigned pos = s_base + s_wcnt[warp] + __popc(ballot & ((1u << lane) - 1u));
             if (pos < (unsigned)d.n) d.act[pos] = i;
         }
         __syncthreads();
@@ -409,7 +372,7 @@ __global__ void __launch_bounds__(ST) k_select_predict(Dev d, int slot, int nchu
         }
         return;
     }
-    phase_select<MIXED, false>(d, T, ctrl->epoch, slot, nchunks, (unsigned long long *)&ctrl->T_acc);
+    phase_select<MIXED, false>(d, T, slot, nchunks, (unsigned long long *)&ctrl->T_acc);
 }
 
 // Predict all particles to `tick` (no selection): the hooks and gd_energy.
@@ -667,98 +630,83 @@ struct Acc<double> {
     __device__ double value() const { return v; }
 };
 
-// a += p[s * stride] for s = s0, s0 + ds, ... < S, in that order, with eight loads
-// in flight (the partials come from L2).
+// Every (component, slot) sum of the S j-split partials is taken in one canonical
+// order, whatever the tile's occupancy and whichever reduction routine runs: eight
+// interleaved running sums q_r over s = r, r + 8, r + 16, ... (ascending), then
+// ((q0 + q1) + (q2 + q3)) + ((q4 + q5) + (q6 + q7)).  A particle's force therefore
+// does not depend on its slot in the active list, nor on which tile it shares.
+constexpr int RED_R = 8;
+
 template <class P>
-__device__ __forceinline__ void sum_strided(Acc<P> &a, const P *p, long long stride, int s0, int S, int ds)
+__device__ __forceinline__ double combine8(Acc<P> q[RED_R])
 {
-    int s = s0;
-    for (; s + 7 * ds < S; s += 8 * ds) {
-        P v[8];
-#pragma unroll
-        for (int u = 0; u < 8; u++) v[u] = __ldcg(p + (long long)(s + u * ds) * stride);
-#pragma unroll
-        for (int u = 0; u < 8; u++) a.add(v[u]);
-    }
-    for (; s < S; s += ds) a.add(__ldcg(p + (long long)s * stride));
+    q[0].add(q[1]);
+    q[2].add(q[3]);
+    q[4].add(q[5]);
+    q[6].add(q[7]);
+    q[0].add(q[2]);
+    q[4].add(q[6]);
+    q[0].add(q[4]);
+    return q[0].value();
 }
 
-// Sums the S partials of slots [k0, k0 + nvalid) into fsum, in a fixed order
-// (deterministic whichever CTA arrives last).  Partials written by other CTAs are
-// read through L2 (__ldcg).
+// Sums the S partials of slots [k0, k0 + nvalid) into fsum (large tiles): one
+// thread per (component, slot) pair keeps the eight running sums, loading eight
+// consecutive splits at a time.  Partials written by other CTAs are read through
+// L2 (__ldcg).
 template <class P>
 __device__ void tile_reduce(const Dev &d, int nact, int S, int k0, int nvalid)
 {
-    __shared__ Acc<P> s_acc[FT];
     const P *part = (const P *)d.part;
     const int npairs = nvalid * 6;
-    const int t = threadIdx.x;
-    const int G = npairs >= FT ? 1 : FT / npairs;  // threads per (slot, component) pair
-    if (G == 1) {
-        for (int pidx = t; pidx < npairs; pidx += FT) {
-            const int c = pidx / nvalid, k = k0 + pidx % nvalid;
-            Acc<P> a;
-            a.zero();
-            sum_strided<P>(a, part + (long long)c * nact + k, 6LL * nact, 0, S, 1);
-            d.fsum[(long long)c * d.n + k] = a.value();
+    for (int pidx = threadIdx.x; pidx < npairs; pidx += FT) {
+        const int c = pidx / nvalid, k = k0 + pidx % nvalid;
+        const P *p = part + (long long)c * nact + k;
+        const long long stride = 6LL * nact;
+        Acc<P> q[RED_R];
+#pragma unroll
+        for (int r = 0; r < RED_R; r++) q[r].zero();
+        for (int s0 = 0; s0 < S; s0 += RED_R) {
+            P v[RED_R];
+#pragma unroll
+            for (int r = 0; r < RED_R; r++) v[r] = s0 + r < S ? __ldcg(p + (long long)(s0 + r) * stride) : P(0);
+#pragma unroll
+            for (int r = 0; r < RED_R; r++)
+                if (s0 + r < S) q[r].add(v[r]);
         }
-    } else {
-        const int pidx = t / G, sub = t % G;
-        Acc<P> a;
-        a.zero();
-        if (pidx < npairs) {
-            const int c = pidx / nvalid, k = k0 + pidx % nvalid;
-            sum_strided<P>(a, part + (long long)c * nact + k, 6LL * nact, sub, S, G);
-        }
-        s_acc[t] = a;
-        __syncthreads();
-        if (pidx < npairs && sub == 0) {
-            for (int q = 1; q < G; q++) a.add(s_acc[t + q]);
-            const int c = pidx / nvalid, k = k0 + pidx % nvalid;
-            d.fsum[(long long)c * d.n + k] = a.value();
-        }
+        d.fsum[(long long)c * d.n + k] = combine8<P>(q);
     }
 }
 
-// The same for a small tile (at most MAXK slots, the warp-mode tiles): every thread
-// takes the splits s = t, t + FT, ... and loads all the tile's (slot, component)
-// partials of each at once, sums them in its own accumulators, and a warp-shuffle
-// tree and a four-warp sum (fixed order) give the totals.  The loads of a thread
-// are independent, so the latency is one round trip per FT splits.
+// The same sums for a small tile (at most MAXK slots, the warp-mode tiles): the
+// (pair, residue) running sums are spread over the CTA's threads, so every load of
+// a thread is independent and the latency is about one round trip per eight splits
+// a residue holds; the eight sums of a pair meet in shared memory.
 template <class P, int MAXK>
 __device__ void tile_reduce_small(const Dev &d, int nact, int S, int k0, int nvalid)
 {
-    __shared__ P s_w[FT / 32][6 * MAXK];
+    __shared__ Acc<P> s_q[6 * MAXK][RED_R];
     const P *part = (const P *)d.part;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    P acc[6 * MAXK];
-#pragma unroll
-    for (int q = 0; q < 6 * MAXK; q++) acc[q] = P(0);
-    for (int s = t; s < S; s += FT) {
-        P v[6 * MAXK];
-#pragma unroll
-        for (int c = 0; c < 6; c++)
-#pragma unroll
-            for (int kk = 0; kk < MAXK; kk++)
-                v[c * MAXK + kk] = kk < nvalid ? __ldcg(part + ((long long)s * 6 + c) * nact + k0 + kk) : P(0);
-#pragma unroll
-        for (int q = 0; q < 6 * MAXK; q++) acc[q] += v[q];
-    }
-#pragma unroll
-    for (int q = 0; q < 6 * MAXK; q++)
-        for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
-    if (lane == 0) {
-#pragma unroll
-        for (int q = 0; q < 6 * MAXK; q++) s_w[warp][q] = acc[q];
+    const int npairs = nvalid * 6;
+    const long long stride = 6LL * nact;
+    for (int w = threadIdx.x; w < npairs * RED_R; w += FT) {
+        const int pidx = w / RED_R, r = w % RED_R;
+        const int c = pidx / nvalid, k = k0 + pidx % nvalid;
+        const P *p = part + (long long)c * nact + k;
+        Acc<P> q;
+        q.zero();
+#pragma unroll 8
+        for (int s = r; s < S; s += RED_R) q.add(__ldcg(p + (long long)s * stride));
+        s_q[pidx][r] = q;
     }
     __syncthreads();
-    if (t < 6 * MAXK) {
-        const int c = t / MAXK, kk = t % MAXK;
-        if (kk < nvalid) {
-            double sum = 0.0;
-            for (int w = 0; w < FT / 32; w++) sum += (double)s_w[w][t];
-            d.fsum[(long long)c * d.n + k0 + kk] = sum;
-        }
+    if (threadIdx.x < npairs) {
+        const int pidx = threadIdx.x;
+        const int c = pidx / nvalid, k = k0 + pidx % nvalid;
+        Acc<P> q[RED_R];
+#pragma unroll
+        for (int r = 0; r < RED_R; r++) q[r] = s_q[pidx][r];
+        d.fsum[(long long)c * d.n + k] = combine8<P>(q);
     }
     __syncthreads();
 }
@@ -1179,6 +1127,7 @@ __global__ void k_resync(Dev d)
             c->T_acc2[1] = LLONG_MAX;
             c->epoch += 1;
             c->done = 0;
+            c->sel_acc = 0ull;
         }
     }
 }
@@ -1371,7 +1320,7 @@ __global__ void __launch_bounds__(FT, 4) k_steps(SArgs a)
             break;
         }
         const unsigned long long t0 = global_ns();
-        phase_select<true, true>(d, T, g, -1, a.nchunks, acc);
+        phase_select<true, true>(d, T, -1, a.nchunks, acc);
         grid_sync(d.bar, ctrl);
         const unsigned long long t1 = global_ns();
         const int nact = min(ldc(&ctrl->nact), d.n);

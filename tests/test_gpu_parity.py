@@ -140,6 +140,23 @@ def test_force_duplicates_and_order(prec):
     np.testing.assert_allclose(a, a_or, rtol=1e-5)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("nact", [3, 13, 300, 777])
+@pytest.mark.parametrize("mode_cut", [1, 10 ** 9])
+def test_force_independent_of_slot(prec, nact, mode_cut):
+    """A particle's force is bit-identical wherever it sits in the active list
+    (the free-running step lists active particles in the order their chunks
+    claim places, not ascending): permuting the list permutes the results."""
+    n = 5000
+    m, x, v = inputs.plummer(n, seed=21)
+    idx = inputs.random_subset(n, nact, seed=nact)
+    perm = np.random.default_rng(nact).permutation(nact)
+    with gravidy.Integrator(m, x, v, EPS, ETA, precision=prec, mode_cut=mode_cut) as g:
+        a, j = g.force(0, idx)
+        ap, jp = g.force(0, idx[perm])
+    assert np.array_equal(ap, a[perm]) and np.array_equal(jp, j[perm])
+
+
 def _random_state(n, seed):
     rng = np.random.default_rng(seed)
     m, x, v = inputs.plummer(n, seed=seed)
