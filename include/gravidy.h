@@ -50,9 +50,13 @@ typedef enum gd_status {
 typedef enum gd_precision {
     /* all pair arithmetic in FP64 */
     GD_FP64 = 0,
-    /* pair arithmetic in FP32 on double-single (hi+lo float) positions, sums
-     * folded into FP64; prediction, correction, steps and energy in FP64
-     * (the mixed-precision alternative of Sec. 2.3) */
+    /* pair arithmetic in FP32 on double-single (hi+lo float) positions with
+     * compensated sums; positions and velocities kept double-single (about 48
+     * significant bits, every value an FP64 number, so gd_get_state /
+     * gd_set_state round trips are exact), accelerations and jerks FP32;
+     * prediction and correction in FP32/double-single arithmetic, energy sums in
+     * FP64 (the mixed-precision alternative of Sec. 2.3).  Needs dt_min >= 2^-24
+     * and dt_max/dt_min <= 2^24. */
     GD_MIXED = 1
 } gd_precision;
 

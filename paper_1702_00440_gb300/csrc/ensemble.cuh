@@ -72,12 +72,7 @@ __global__ void __launch_bounds__(ST) k_ens_select(Dev d, Ens e, int nchunks)
         const long long tn = ldc(&d.tnext[i]);
         const bool act = (tn == T);
         if (!act) mn_all = tn < mn_all ? tn : mn_all;
-        {
-            const double dt = (double)(T - ldc(&d.tau[i])) * d.dt_min;
-            double xp[3], vp[3];
-            predict64<false>(d, i, dt, xp, vp);
-            store_jrec<true>(d, i, xp, vp, d.m[i]);
-        }
+        predict_store_ds<false>(d, i, T - ldc(&d.tau[i]));
         const unsigned ballot = __ballot_sync(0xffffffffu, act);
         if (lane == 0) s_wcnt[warp] = __popc(ballot);
         __syncthreads();
@@ -289,9 +284,10 @@ __device__ void ens_tile_reduce(const Dev &d, const Ens &e, int item0, int S, in
     if (t < ENS_PART) {
         const int k = t / 6, comp = t % 6;
         if (k < nvalid) {
-            double sum = 0.0;
-            for (int w = 0; w < FT / 32; w++) sum += (double)s_w[w][t];
-            d.fsum[(long long)comp * d.n + slot0 + k] = sum;
+            DS sum;
+            sum.zero();
+            for (int w = 0; w < FT / 32; w++) sum.add(s_w[w][t]);
+            store_fsum<float>(d, comp, slot0 + k, __fadd_rn(sum.h, sum.l));
         }
     }
     __syncthreads();
@@ -408,7 +404,7 @@ __global__ void __launch_bounds__(FT, 2) k_ens_force(EArgs a)
         if (s_last) {
             __threadfence();
             ens_tile_reduce(d, e, p.item_base[c] + tl * S, S, slot0, nvalid);
-            if (a.correct) correct_slots<false>(d, T, slot0, slot0 + nvalid, warp, FT / 32, mymin, bad);
+            if (a.correct) correct_slots<true, false>(d, T, slot0, slot0 + nvalid, warp, FT / 32, mymin, bad);
         }
         __syncthreads();
     }
@@ -453,12 +449,7 @@ __global__ void k_ens_init_steps(Dev d, Ens e)
         return;
     }
     double a[3], j[3];
-    for (int q = 0; q < 3; q++) {
-        a[q] = d.fsum[(long long)q * n + i];
-        j[q] = d.fsum[(long long)(3 + q) * n + i];
-        d.a[q * n + i] = a[q];
-        d.jk[q * n + i] = j[q];
-    }
+    take_force<true>(d, i, i, a, j);
     const double na = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
     const double nj = sqrt(j[0] * j[0] + j[1] * j[1] + j[2] * j[2]);
     const double dt0 = d.eta * na / nj;

@@ -146,10 +146,12 @@ void launch_predict_all(gd_ctx *c, long long tick, bool mixed_records)
 {
     const int g = (c->d.n + 255) / 256;
     c->launches += 1;
-    if (mixed_records)
-        k_predict_all<true><<<g, 256, 0, c->stream>>>(c->d, tick);
+    if (c->mixed && mixed_records)
+        k_predict_all<true, true><<<g, 256, 0, c->stream>>>(c->d, tick);
+    else if (c->mixed)
+        k_predict_all<true, false><<<g, 256, 0, c->stream>>>(c->d, tick);
     else
-        k_predict_all<false><<<g, 256, 0, c->stream>>>(c->d, tick);
+        k_predict_all<false, false><<<g, 256, 0, c->stream>>>(c->d, tick);
 }
 
 void launch_select(gd_ctx *c, int slot)
@@ -168,8 +170,11 @@ void launch_force_step(gd_ctx *c) { launch_force_with(c, fargs(c, c->opt.tail_co
 void launch_correct(gd_ctx *c)
 {
     c->launches += 1;
-    launch_pdl(c->opt.pdl != 0, k_correct, c->grid_corr, CT, c->stream,
-               CArgs{c->d, c->grid_force, effective_tune(c), c->opt.tail_correct ? 1 : 0, c->mixed ? 1 : 0});
+    const CArgs a{c->d, c->grid_force, effective_tune(c), c->opt.tail_correct ? 1 : 0, c->mixed ? 1 : 0};
+    if (c->mixed)
+        launch_pdl(c->opt.pdl != 0, k_correct<true>, c->grid_corr, CT, c->stream, a);
+    else
+        launch_pdl(c->opt.pdl != 0, k_correct<false>, c->grid_corr, CT, c->stream, a);
 }
 
 // One free-running block step: select+predict, force (+ correction of small
@@ -235,7 +240,8 @@ void free_all(gd_ctx *c)
 {
     Dev &d = c->d;
     void *ps[] = {d.x,  d.v,   d.a,    d.jk,   d.m,       d.tau,    d.dtau, d.tnext, d.jA,        d.jB,   d.jC,
-                  d.pd, d.act, d.part, d.fsum, d.tilecnt, d.status, d.eu,   d.ek,    d.nact_hist, d.bar, d.ctrl};
+                  d.pd, d.act, d.part, d.fsum, d.tilecnt, d.status, d.eu,   d.ek,    d.nact_hist, d.bar, d.ctrl,
+                  d.xs, d.vs,  d.af,   d.jf,   d.mf};
     for (void *p : ps)
         if (p) cudaFree(p);
     if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
@@ -287,14 +293,22 @@ int first_forces(gd_ctx *c)
     Dev &d = c->d;
     const int n = d.n;
     // a = jerk = 0 and tau = 0, so the prediction to tick 0 is exact
-    CK(cudaMemsetAsync(d.a, 0, sizeof(double) * 3 * n, c->stream));
-    CK(cudaMemsetAsync(d.jk, 0, sizeof(double) * 3 * n, c->stream));
+    if (c->mixed) {
+        CK(cudaMemsetAsync(d.af, 0, sizeof(float) * 3 * n, c->stream));
+        CK(cudaMemsetAsync(d.jf, 0, sizeof(float) * 3 * n, c->stream));
+    } else {
+        CK(cudaMemsetAsync(d.a, 0, sizeof(double) * 3 * n, c->stream));
+        CK(cudaMemsetAsync(d.jk, 0, sizeof(double) * 3 * n, c->stream));
+    }
     CK(cudaMemsetAsync(d.tau, 0, sizeof(long long) * n, c->stream));
     launch_predict_all(c, 0, c->mixed);
     k_iota<<<(n + 255) / 256, 256, 0, c->stream>>>(d.act, n);
     k_set_step<<<1, 1, 0, c->stream>>>(d.ctrl, 0, n);
     launch_force(c);
-    k_init_steps<<<(n + 255) / 256, 256, 0, c->stream>>>(d);
+    if (c->mixed)
+        k_init_steps<true><<<(n + 255) / 256, 256, 0, c->stream>>>(d);
+    else
+        k_init_steps<false><<<(n + 255) / 256, 256, 0, c->stream>>>(d);
     k_resync<<<1, 1024, 0, c->stream>>>(d);
     c->launches += 4;
     CK(cudaGetLastError());
@@ -511,6 +525,9 @@ int ctx_init(gd_ctx **out, int64_t n, const double *m, const double *x, const do
         return fail(nullptr, GD_EINVAL, "dt_min and dt_max must be powers of two with dt_min <= dt_max");
     if (o.dt_max / o.dt_min > std::ldexp(1.0, 40)) return fail(nullptr, GD_EINVAL, "dt_max/dt_min too large");
     if (o.precision != GD_FP64 && o.precision != GD_MIXED) return fail(nullptr, GD_EINVAL, "bad precision");
+    // the mixed path counts steps in FP32: tick counts up to dtau_max and dt_min^5 stay exact
+    if (o.precision == GD_MIXED && (o.dt_min < std::ldexp(1.0, -24) || o.dt_max / o.dt_min > std::ldexp(1.0, 24)))
+        return fail(nullptr, GD_EINVAL, "mixed precision needs dt_min >= 2^-24 and dt_max/dt_min <= 2^24");
     for (int64_t i = 0; i < n; i++) {
         if (!std::isfinite(m[i]) || m[i] < 0) return fail(nullptr, GD_EINVAL, "masses must be finite and >= 0");
         for (int k = 0; k < 3; k++)
@@ -572,6 +589,9 @@ int ctx_init(gd_ctx **out, int64_t n, const double *m, const double *x, const do
     d.eta = eta;
     d.eps2 = eps * eps;
     d.eps2f = (float)(eps * eps);
+    d.dt_min_f = (float)o.dt_min;
+    d.inv_dt_min_f = (float)(1.0 / o.dt_min);
+    d.eta_f = (float)eta;
     c->nchunks = (d.n + ST - 1) / ST;
     // the select kernel's chunks wait on lower chunks: keep its grid co-resident
     c->grid_sel = std::max(1, std::min(c->nchunks, sms * std::max(1, occ_sel)));
@@ -591,6 +611,9 @@ int ctx_init(gd_ctx **out, int64_t n, const double *m, const double *x, const do
         (rc = dalloc(c, &d.status, (size_t)c->nchunks)) || (rc = dalloc(c, &d.eu, (size_t)d.n)) ||
         (rc = dalloc(c, &d.ek, (size_t)d.n)) || (rc = dalloc(c, &d.nact_hist, (size_t)64)) ||
         (rc = dalloc(c, &d.bar, (size_t)BAR_WORDS)) || (rc = dalloc(c, &d.ctrl, (size_t)1)))
+        return bail(rc);
+    if (c->mixed && ((rc = dalloc(c, &d.xs, 2 * n3)) || (rc = dalloc(c, &d.vs, 2 * n3)) || (rc = dalloc(c, &d.af, n3)) ||
+                     (rc = dalloc(c, &d.jf, n3)) || (rc = dalloc(c, &d.mf, (size_t)d.n))))
         return bail(rc);
     e = cudaMallocHost((void **)&c->h_ctrl, sizeof(Ctrl));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_hist, sizeof(int) * 64);
@@ -624,6 +647,10 @@ int ctx_init(gd_ctx **out, int64_t n, const double *m, const double *x, const do
     if (e == cudaSuccess) e = cudaMemcpyAsync(d.m, m, sizeof(double) * d.n, cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "upload"));
     if ((rc = upload_aos(c, d.x, x, 0)) || (rc = upload_aos(c, d.v, v, 1))) return bail(rc);
+    if (c->mixed) {
+        k_state_to_ds<<<(d.n + 255) / 256, 256, 0, c->stream>>>(d, 0);
+        c->launches += 1;
+    }
     e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "upload"));
     if (d.npad > d.n) {
@@ -765,6 +792,10 @@ int gd_get_state(gd_ctx *c, double *x, double *v, double *a, double *jerk, int64
     int rc = check_usable(c);
     if (rc) return rc;
     const Dev &d = c->d;
+    if (c->mixed) {  // double-single / FP32 state -> the FP64 staging planes (exact)
+        k_state_from_ds<<<(d.n + 255) / 256, 256, 0, c->stream>>>(d);
+        c->launches += 1;
+    }
     if (x && (rc = download_planes(c, d.x, d.n, 0, d.n))) return rc;
     if (v && (rc = download_planes(c, d.v, d.n, 1, d.n))) return rc;
     if (a && (rc = download_planes(c, d.a, d.n, 2, d.n))) return rc;
@@ -806,6 +837,10 @@ int gd_set_state(gd_ctx *c, const double *x, const double *v, const double *a, c
     if ((rc = upload_aos(c, d.x, x, 0)) || (rc = upload_aos(c, d.v, v, 1)) || (rc = upload_aos(c, d.a, a, 2)) ||
         (rc = upload_aos(c, d.jk, jerk, 3)))
         return rc;
+    if (c->mixed) {
+        k_state_to_ds<<<(d.n + 255) / 256, 256, 0, c->stream>>>(d, 1);
+        c->launches += 1;
+    }
     std::memcpy(stage_i64(c, 0), tau, sizeof(long long) * d.n);
     std::memcpy(stage_i64(c, 1), dtau, sizeof(long long) * d.n);
     std::memcpy(stage_i64(c, 2), tn.data(), sizeof(long long) * d.n);
@@ -888,9 +923,18 @@ int gd_force(gd_ctx *c, int64_t tick, const int32_t *idx, int64_t nact, double *
     launch_force(c);
     if (c->opt.time_force) CK(cudaEventRecord(c->ev[1], c->stream));
     CK(cudaGetLastError());
-    // fsum planes (stride n) -> staging, first nact rows
-    if ((rc = download_planes(c, d.fsum, d.n, 0, (int)nact))) return rc;
-    if ((rc = download_planes(c, d.fsum + 3 * (size_t)d.n, d.n, 1, (int)nact))) return rc;
+    // fsum planes (stride n) -> staging, first nact rows (the mixed path's FP32
+    // sums widened into the FP64 planes pd first)
+    const double *fs = d.fsum;
+    long long fstride = d.n;
+    if (c->mixed) {
+        k_fsum_widen<<<(int)((nact + 255) / 256), 256, 0, c->stream>>>(d, (int)nact, d.pd);
+        c->launches += 1;
+        fs = d.pd;
+        fstride = nact;
+    }
+    if ((rc = download_planes(c, fs, fstride, 0, (int)nact))) return rc;
+    if ((rc = download_planes(c, fs + 3 * (size_t)fstride, fstride, 1, (int)nact))) return rc;
     CK(cudaStreamSynchronize(c->stream));
     unstage_aos(c, acc, 0, (int)nact);
     unstage_aos(c, jerk, 1, (int)nact);
@@ -1122,10 +1166,10 @@ int gd_ens_init(gd_ens **out, int32_t nclusters, const int64_t *n_per, const dou
     Dev &d = c->d;
     {
         cudaStream_t st = c->stream;
-        cudaMemsetAsync(d.a, 0, sizeof(double) * 3 * d.n, st);
-        cudaMemsetAsync(d.jk, 0, sizeof(double) * 3 * d.n, st);
+        cudaMemsetAsync(d.af, 0, sizeof(float) * 3 * d.n, st);
+        cudaMemsetAsync(d.jf, 0, sizeof(float) * 3 * d.n, st);
         cudaMemsetAsync(d.tau, 0, sizeof(long long) * d.n, st);
-        k_predict_all<true><<<(d.n + 255) / 256, 256, 0, st>>>(d, 0);
+        k_predict_all<true, true><<<(d.n + 255) / 256, 256, 0, st>>>(d, 0);
         k_iota<<<(d.n + 255) / 256, 256, 0, st>>>(d.act, d.n);
         k_ens_set_counts<<<(nclusters + 127) / 128, 128, 0, st>>>(s->e);
         const EArgs a0{d, s->e, 0};
@@ -1217,8 +1261,8 @@ int gd_ens_energy(gd_ens *s, double *K, double *U)
     if (rc) return ens_fail(s, rc, c->err);
     const long long T = c->h_ctrl->T_last;
     Dev &d = c->d;
-    k_predict_all<false><<<(d.n + 255) / 256, 256, 0, c->stream>>>(d, T);
-    k_predict_all<true><<<(d.n + 255) / 256, 256, 0, c->stream>>>(d, T);
+    k_predict_all<true, false><<<(d.n + 255) / 256, 256, 0, c->stream>>>(d, T);
+    k_predict_all<true, true><<<(d.n + 255) / 256, 256, 0, c->stream>>>(d, T);
     k_ens_energy_terms<<<d.npad / ET, ET, 0, c->stream>>>(d, s->e);
     k_ens_energy_sum<<<s->C, 256, 0, c->stream>>>(d, s->e);
     c->launches += 4;
@@ -1361,8 +1405,9 @@ __global__ void k_noalloc_out(Dev d, int nact, const int *bad_flags, double *acc
         const bool bad = bad_flags[k] != 0;
         const double nan = __longlong_as_double(0x7ff8000000000000LL);
         for (int c = 0; c < 3; c++) {
-            acc[3 * (long long)k + c] = bad ? nan : d.fsum[(long long)c * d.n + k];
-            jerk[3 * (long long)k + c] = bad ? nan : d.fsum[(long long)(3 + c) * d.n + k];
+            const float *fs = (const float *)d.fsum;
+            acc[3 * (long long)k + c] = bad ? nan : (double)fs[(long long)c * d.n + k];
+            jerk[3 * (long long)k + c] = bad ? nan : (double)fs[(long long)(3 + c) * d.n + k];
         }
     }
 }

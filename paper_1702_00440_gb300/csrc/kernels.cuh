@@ -101,8 +101,15 @@ struct Dev {
     double eta;
     double eps2;
     float eps2f;
-    // FP64 state at each particle's own time, structure of arrays (plane c at +c*n)
+    float dt_min_f, inv_dt_min_f, eta_f;  // FP32 copies (dt_min is a power of two: exact)
+    // FP64 state at each particle's own time, structure of arrays (plane c at +c*n);
+    // on the mixed path these planes only stage the state in and out (k_state_to_ds,
+    // k_state_from_ds)
     double *x, *v, *a, *jk, *m;
+    // mixed-path state: x and v double-single, planes c = hi x, y, z and 3 + c = lo
+    // (canonical: hi = the float nearest the value, hi + lo an FP64 number, see
+    // ds_canon); a and jerk FP32 (the mixed forces carry FP32 accuracy); masses FP32
+    float *xs, *vs, *af, *jf, *mf;
     long long *tau, *dtau, *tnext;
     // predicted j-records, mixed: A = (x_hi, y_hi, z_hi, m), B = (x_lo, y_lo, z_lo, vx),
     // C = (vy, vz); padded to npad with massless far-away particles
@@ -114,6 +121,7 @@ struct Dev {
     void *part;               // j-split partials (float mixed, double FP64), (s*6 + c)*nact + k
     long long cap;            // partial capacity (entries per component)
     double *fsum;             // summed force of active slot k: fsum[c*n + k], c < 3 a, c >= 3 jerk
+                              // (FP64 path; the mixed path stores floats, see fsum_f)
     unsigned int *tilecnt;    // per i-tile arrival counters (zero between launches)
     unsigned long long *status;  // ensemble look-back words, one per chunk of ST particles
     double *eu, *ek;          // per-particle energy terms
@@ -244,6 +252,139 @@ struct DS {
     __device__ __forceinline__ double as_double() const { return (double)h + (double)l; }
 };
 
+// ---------------------------------------------------------------- double-single values
+//
+// The mixed path keeps positions and velocities as unevaluated sums h + l of two
+// floats (about 48 significant bits) and does its updates with FP32 instructions:
+// on this GPU one FP64 warp instruction costs as much issue time as about 78 FP32
+// ones.  Error-free transformations: Knuth's two-sum (any magnitudes) and
+// Dekker's fast two-sum (|a| >= |b|); products by an exact power of two are exact.
+// Explicit __fadd_rn / __fmul_rn keep the compiler from contracting them.
+
+struct F2 {
+    float h, l;
+};
+
+__device__ __forceinline__ F2 two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fadd_rn(s, -a);
+    const float e = __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb));
+    return F2{s, e};
+}
+
+__device__ __forceinline__ F2 fast_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return F2{s, __fadd_rn(b, -__fadd_rn(s, -a))};
+}
+
+// (a.h + a.l) + b, normalised (h = the float nearest the sum)
+__device__ __forceinline__ F2 ds_add_f(F2 a, float b)
+{
+    const F2 s = two_sum(a.h, b);
+    return fast_two_sum(s.h, __fadd_rn(s.l, a.l));
+}
+
+// Canonical form of a normalised double-single value: lo rounded to a multiple of
+// 2^(E - 51), E the binary exponent of hi, then renormalised.  The value is then
+// an FP64 number (even if renormalising moves hi to the next binade), so FP64 ->
+// double-single -> FP64 conversions are exact and a state read out and written
+// back continues bit for bit.  Values below 2^-46 (and zero) are left as they are.
+__device__ __forceinline__ F2 ds_canon(F2 a)
+{
+    const int eb = (int)((__float_as_uint(a.h) >> 23) & 0xFFu);  // biased exponent of hi
+    if (eb < 81 || eb > 250) return a;
+    const float g = __uint_as_float((unsigned)(eb - 51) << 23);    // 2^(E - 51)
+    const float ig = __uint_as_float((unsigned)(305 - eb) << 23);  // 2^(51 - E)
+    const float lq = __fmul_rn(rintf(__fmul_rn(a.l, ig)), g);
+    return fast_two_sum(a.h, lq);
+}
+
+// FP64 -> canonical double-single (state upload) and back (exact for canonical values)
+__device__ __forceinline__ F2 ds_from_double(double x)
+{
+    const float h = __double2float_rn(x);
+    const float l = __double2float_rn(x - (double)h);
+    return ds_canon(fast_two_sum(h, l));
+}
+
+__device__ __forceinline__ double ds_to_double(F2 a) { return (double)a.h + (double)a.l; }
+
+__device__ __forceinline__ F2 ld_ds(const float *p, int n, int c, int i) { return F2{p[c * n + i], p[(3 + c) * n + i]}; }
+
+template <bool COH>
+__device__ __forceinline__ F2 ldx_ds(const float *p, int n, int c, int i)
+{
+    if (COH) return F2{__ldcg(p + c * n + i), __ldcg(p + (3 + c) * n + i)};
+    return F2{p[c * n + i], p[(3 + c) * n + i]};
+}
+
+__device__ __forceinline__ void st_ds(float *p, int n, int c, int i, F2 a)
+{
+    p[c * n + i] = a.h;
+    p[(3 + c) * n + i] = a.l;
+}
+
+// Step length in FP32 from ticks: exact for dtick < 2^24 (every step the
+// integrator takes; dtau_max is at most 2^20 ticks here), with 1/dt exact when
+// dtick is a power of two (always, in free-running steps).
+__device__ __forceinline__ void step_f(const Dev &d, long long dtick, float &dt, float &idt)
+{
+    dt = __fmul_rn((float)dtick, d.dt_min_f);
+    if (dtick > 0 && (dtick & (dtick - 1)) == 0) {
+        const int e = 63 - __clzll(dtick);
+        idt = __fmul_rn(d.inv_dt_min_f, __uint_as_float((unsigned)(127 - e) << 23));
+    } else {
+        idt = 1.0f / dt;
+    }
+}
+
+// Taylor prediction (Sec. 2.4 step 7a) of one component on the mixed path:
+//   xp = x + dt v + dt^2/2 a + dt^3/6 jerk,   vp = v + dt a + dt^2/2 jerk.
+// dt v is formed exactly (dt * v.h as a product and its FMA residual); the a and
+// jerk terms are FP32 like the forces they come from; the sum is double-single.
+__device__ __forceinline__ F2 ds_pred_x(F2 x0, F2 v0, float a0, float j0, float dt, float h2, float h3)
+{
+    const float p = __fmul_rn(dt, v0.h);
+    const float pe = fmaf(dt, v0.h, -p);
+    const float small = fmaf(h3, j0, __fmul_rn(h2, a0));
+    const F2 s = two_sum(x0.h, p);
+    const float e = __fadd_rn(__fadd_rn(__fadd_rn(s.l, x0.l), fmaf(dt, v0.l, pe)), small);
+    return two_sum(s.h, e);
+}
+
+__device__ __forceinline__ F2 ds_pred_v(F2 v0, float a0, float j0, float dt, float h2)
+{
+    const float t = fmaf(h2, j0, __fmul_rn(dt, a0));
+    const F2 s = two_sum(v0.h, t);
+    return two_sum(s.h, __fadd_rn(s.l, v0.l));
+}
+
+// Predicts particle i to T on the mixed path and stores its j-record.
+template <bool COH>
+__device__ __forceinline__ void predict_store_ds(const Dev &d, int i, long long dtick)
+{
+    const int n = d.n;
+    float dt, idt;
+    step_f(d, dtick, dt, idt);
+    const float h2 = __fmul_rn(0.5f, __fmul_rn(dt, dt));
+    const float h3 = __fmul_rn(__fmul_rn(__fmul_rn(dt, dt), dt), 1.0f / 6.0f);
+    F2 xp[3];
+    float vp[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const F2 x0 = ldx_ds<COH>(d.xs, n, c, i), v0 = ldx_ds<COH>(d.vs, n, c, i);
+        const float a0 = ldx<COH>(&d.af[c * n + i]), j0 = ldx<COH>(&d.jf[c * n + i]);
+        xp[c] = ds_pred_x(x0, v0, a0, j0, dt, h2, h3);
+        const F2 v = ds_pred_v(v0, a0, j0, dt, h2);
+        vp[c] = __fadd_rn(v.h, v.l);
+    }
+    d.jA[i] = make_float4(xp[0].h, xp[1].h, xp[2].h, d.mf[i]);
+    d.jB[i] = make_float4(xp[0].l, xp[1].l, xp[2].l, vp[0]);
+    d.jC[i] = make_float2(vp[1], vp[2]);
+}
+
 // Taylor prediction of particle i over dt (Sec. 2.4 step 7a), FP64.
 template <bool COH>
 __device__ __forceinline__ void predict64(const Dev &d, int i, double dt, double xp[3], double vp[3])
@@ -254,6 +395,20 @@ __device__ __forceinline__ void predict64(const Dev &d, int i, double dt, double
     for (int c = 0; c < 3; c++) {
         const double x0 = ldx<COH>(&d.x[c * n + i]), v0 = ldx<COH>(&d.v[c * n + i]),
                      a0 = ldx<COH>(&d.a[c * n + i]), j0 = ldx<COH>(&d.jk[c * n + i]);
+        xp[c] = fma(j0, h3, fma(a0, h2, fma(v0, dt, x0)));
+        vp[c] = fma(j0, h2, fma(a0, dt, v0));
+    }
+}
+
+// The same FP64 prediction from the mixed path's state (hooks and energy).
+__device__ __forceinline__ void predict64_ds(const Dev &d, int i, double dt, double xp[3], double vp[3])
+{
+    const int n = d.n;
+    const double h2 = 0.5 * dt * dt, h3 = dt * dt * dt * (1.0 / 6.0);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const double x0 = ds_to_double(ld_ds(d.xs, n, c, i)), v0 = ds_to_double(ld_ds(d.vs, n, c, i));
+        const double a0 = d.af[c * n + i], j0 = d.jf[c * n + i];
         xp[c] = fma(j0, h3, fma(a0, h2, fma(v0, dt, x0)));
         vp[c] = fma(j0, h2, fma(a0, dt, v0));
     }
@@ -310,10 +465,14 @@ __device__ void phase_select(const Dev &d, long long T, int slot, int nchunks, u
             const long long tn = ldx<COH>(&d.tnext[i]);
             act = (tn == T);
             if (!act) mn_all = tn < mn_all ? tn : mn_all;
-            const double dt = (double)(T - ldx<COH>(&d.tau[i])) * d.dt_min;
-            double xp[3], vp[3];
-            predict64<COH>(d, i, dt, xp, vp);
-            store_jrec<MIXED>(d, i, xp, vp, d.m[i]);
+            const long long dtick = T - ldx<COH>(&d.tau[i]);
+            if (MIXED) {
+                predict_store_ds<COH>(d, i, dtick);
+            } else {
+                double xp[3], vp[3];
+                predict64<COH>(d, i, (double)dtick * d.dt_min, xp, vp);
+                store_jrec<false>(d, i, xp, vp, d.m[i]);
+            }
         }
         const unsigned ballot = __ballot_sync(0xffffffffu, act);
         if (lane == 0) s_wcnt[warp] = __popc(ballot);
@@ -375,16 +534,67 @@ __global__ void __launch_bounds__(ST) k_select_predict(Dev d, int slot, int nchu
     phase_select<MIXED, false>(d, T, slot, nchunks, (unsigned long long *)&ctrl->T_acc);
 }
 
-// Predict all particles to `tick` (no selection): the hooks and gd_energy.
-template <bool MIXED>
+// Predict all particles to `tick` (no selection): the hooks, gd_energy and the
+// initial forces.  DS: the state is the mixed path's; RECS: mixed j-records (else
+// the FP64 planes pd).
+template <bool DS_STATE, bool RECS>
 __global__ void k_predict_all(Dev d, long long tick)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
-    const double dt = (double)(tick - d.tau[i]) * d.dt_min;
+    const long long dtick = tick - d.tau[i];
+    if (DS_STATE && RECS) {
+        predict_store_ds<false>(d, i, dtick);
+        return;
+    }
+    const double dt = (double)dtick * d.dt_min;
     double xp[3], vp[3];
-    predict64<false>(d, i, dt, xp, vp);
-    store_jrec<MIXED>(d, i, xp, vp, d.m[i]);
+    if (DS_STATE)
+        predict64_ds(d, i, dt, xp, vp);
+    else
+        predict64<false>(d, i, dt, xp, vp);
+    store_jrec<RECS>(d, i, xp, vp, d.m[i]);
+}
+
+// Mixed path: FP64 staging planes -> state (x, v double-single canonical, a and
+// jerk FP32), and back.
+__global__ void k_state_to_ds(Dev d, int with_aj)
+{
+    const int n = d.n;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int c = 0; c < 3; c++) {
+        st_ds(d.xs, n, c, i, ds_from_double(d.x[c * n + i]));
+        st_ds(d.vs, n, c, i, ds_from_double(d.v[c * n + i]));
+        if (with_aj) {
+            d.af[c * n + i] = __double2float_rn(d.a[c * n + i]);
+            d.jf[c * n + i] = __double2float_rn(d.jk[c * n + i]);
+        }
+    }
+    d.mf[i] = __double2float_rn(d.m[i]);
+}
+
+// Mixed path: the FP32 summed forces of the first rows slots, widened into FP64
+// planes dst[c * rows + k] (the force hook's download).
+__global__ void k_fsum_widen(Dev d, int rows, double *dst)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= rows) return;
+    const float *fs = (const float *)d.fsum;
+    for (int c = 0; c < 6; c++) dst[(long long)c * rows + k] = (double)fs[(long long)c * d.n + k];
+}
+
+__global__ void k_state_from_ds(Dev d)
+{
+    const int n = d.n;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int c = 0; c < 3; c++) {
+        d.x[c * n + i] = ds_to_double(ld_ds(d.xs, n, c, i));
+        d.v[c * n + i] = ds_to_double(ld_ds(d.vs, n, c, i));
+        d.a[c * n + i] = (double)d.af[c * n + i];
+        d.jk[c * n + i] = (double)d.jf[c * n + i];
+    }
 }
 
 // Padding records: massless particles far away, so the inner loops need no tail test.
@@ -507,6 +717,182 @@ __device__ __forceinline__ long long next_block_step(const Dev &d, double num, d
     return dtau_old;
 }
 
+// ---------------------------------------------------------------- mixed-path time step
+//
+// The same rules as next_block_step, with the Aarseth estimate from FP32 norms.
+// FP32 cannot hold the products of the criterion (|a3|^2 reaches 1e47 at the
+// smallest steps), so every quantity is kept as m * 2^e with m in [1, 2) and an
+// integer exponent: products and sums of the criterion never overflow, and the
+// comparisons with powers of two stay exact.
+
+struct XF {
+    float m;  // 0, or in [1, 2)
+    int e;
+};
+
+__device__ __forceinline__ XF xf_of(float x)  // x >= 0 finite
+{
+    if (!(x > 0.f)) return XF{0.f, 0};
+    int sh = 0;
+    if (x < 1.1754944e-38f) {  // subnormal: scale up exactly first
+        x = __fmul_rn(x, 1.8446744e19f);  // 2^64
+        sh = 64;
+    }
+    const unsigned b = __float_as_uint(x);
+    return XF{__uint_as_float((b & 0x007FFFFFu) | 0x3F800000u), (int)((b >> 23) & 0xFFu) - 127 - sh};
+}
+
+__device__ __forceinline__ XF xf_norm(float m, int e)  // m in [0, 4)
+{
+    if (m >= 2.f) return XF{__fmul_rn(m, 0.5f), e + 1};
+    return XF{m, e};
+}
+
+__device__ __forceinline__ XF xf_mul(XF a, XF b)
+{
+    if (a.m == 0.f || b.m == 0.f) return XF{0.f, 0};
+    return xf_norm(__fmul_rn(a.m, b.m), a.e + b.e);
+}
+
+__device__ __forceinline__ XF xf_add(XF a, XF b)
+{
+    if (a.m == 0.f) return b;
+    if (b.m == 0.f) return a;
+    if (a.e < b.e) {
+        const XF t = a;
+        a = b;
+        b = t;
+    }
+    const int k = a.e - b.e;
+    if (k > 60) return a;
+    return xf_norm(__fadd_rn(a.m, __fmul_rn(b.m, __uint_as_float((unsigned)(127 - k) << 23))), a.e);
+}
+
+// a < b for non-negative values
+__device__ __forceinline__ bool xf_lt(XF a, XF b)
+{
+    if (a.m == 0.f) return b.m > 0.f;
+    if (b.m == 0.f) return false;
+    return a.e < b.e || (a.e == b.e && a.m < b.m);
+}
+
+// Euclidean norm of the 3-vector whose components sit on lanes 0-2 of each group of
+// four (lane 3 passes 0), scaled by a power of two so the squares cannot overflow.
+__device__ __forceinline__ float norm3_group(float x)
+{
+    float mx = fabsf(x);
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+    const int eb = (int)((__float_as_uint(mx) >> 23) & 0xFFu);
+    const bool plain = !(mx > 0.f) || eb == 0 || eb > 253;  // zero, subnormal, huge, Inf or NaN
+    const float sc = plain ? 1.f : __uint_as_float((unsigned)(254 - eb) << 23);  // 2^-(E)
+    const float y = __fmul_rn(x, sc);
+    float q = __fmul_rn(y, y);
+    q = __fadd_rn(q, __shfl_xor_sync(0xffffffffu, q, 1));
+    q = __fadd_rn(q, __shfl_xor_sync(0xffffffffu, q, 2));
+    if (plain) return eb == 0 && mx > 0.f ? mx : (mx > 0.f ? __fsqrt_rn(q) : 0.f);
+    return __fmul_rn(__fsqrt_rn(q), __uint_as_float((unsigned)eb << 23));  // * 2^E
+}
+
+__device__ __forceinline__ long long next_block_step_f(const Dev &d, float na1, float nj1, float na2, float na3,
+                                                       long long dtau_old, long long T)
+{
+    const bool finite = isfinite(na1) && isfinite(nj1) && isfinite(na2) && isfinite(na3);
+    // num = eta (|a1||a2e| + |j1|^2), den = |j1||a3| + |a2e|^2
+    const XF A = xf_of(na1), J = xf_of(nj1), B = xf_of(na2), C = xf_of(na3);
+    const XF num = xf_mul(xf_of(d.eta_f), xf_add(xf_mul(A, B), xf_mul(J, J)));
+    const XF den = xf_add(xf_mul(J, C), xf_mul(B, B));
+    const bool unconstrained = !finite || den.m == 0.f;
+    if (!unconstrained) {
+        if (num.m == 0.f) return 1;
+        // dt_old^2 = 2^(2k), k = log2(dtau_old) + log2(dt_min)
+        const int lt = 63 - __clzll(dtau_old);
+        const int ldm = (int)((__float_as_uint(d.dt_min_f) >> 23) & 0xFFu) - 127;
+        const XF lim{den.m, den.e + 2 * (lt + ldm)};
+        if (xf_lt(num, lim)) {
+            // floor(log2(num / (den dt_min^2)))
+            const int fl = num.e - (den.e + 2 * ldm) - (num.m < den.m ? 1 : 0);
+            const int lvl = fl >> 1;
+            if (lvl < 0) return 1;
+            return 1LL << lvl;
+        }
+        const XF lim4{den.m, lim.e + 2};
+        if (xf_lt(num, lim4)) return dtau_old;
+    }
+    if (2 * dtau_old <= d.dtau_max && (T & (2 * dtau_old - 1)) == 0) return 2 * dtau_old;
+    return dtau_old;
+}
+
+// Correction (Sec. 2.4 step 7d, Hermite scheme) on the mixed path, laid out as
+// correct_slots64 (four lanes per particle): FP32 Hermite derivatives and
+// correction terms (the forces they come from are FP32-accurate), double-single
+// position and velocity sums, canonical results, the step from next_block_step_f.
+template <bool COH>
+__device__ __forceinline__ void correct_slots_ds(const Dev &d, long long T, int k_lo, int k_hi, int w0, int ws,
+                                                 long long &mymin, int &bad)
+{
+    const int n = d.n;
+    const int lane = threadIdx.x & 31;
+    const int q = lane & 3;
+    const int c = q < 3 ? q : 2;
+    const bool real = q < 3;
+    const float *fs = (const float *)d.fsum;
+    for (int kw = k_lo + w0 * 8; kw < k_hi; kw += ws * 8) {
+        const int k = kw + (lane >> 2);
+        const bool valid = k < k_hi;
+        const int kk = valid ? k : k_hi - 1;
+        const int i = ldx<COH>(&d.act[kk]);
+        const long long tau0 = ldx<COH>(&d.tau[i]);
+        const long long dtau_old = ldx<COH>(&d.dtau[i]);
+        const long long dtick = T - tau0;
+        const bool behind = dtick > 0;
+        float dt, idt;
+        step_f(d, behind ? dtick : 1, dt, idt);
+        const float dt2 = __fmul_rn(dt, dt), dt3 = __fmul_rn(dt2, dt), dt4 = __fmul_rn(dt3, dt);
+        const float dt5 = __fmul_rn(dt4, dt);
+        const float idt2 = __fmul_rn(idt, idt), idt3 = __fmul_rn(idt2, idt);
+        const float h2 = __fmul_rn(0.5f, dt2), h3 = __fmul_rn(dt3, 1.0f / 6.0f);
+        const float h4 = __fmul_rn(dt4, 1.0f / 24.0f), h5 = __fmul_rn(dt5, 1.0f / 120.0f);
+        const F2 x0 = ldx_ds<COH>(d.xs, n, c, i), v0 = ldx_ds<COH>(d.vs, n, c, i);
+        const float a0 = ldx<COH>(&d.af[c * n + i]), j0 = ldx<COH>(&d.jf[c * n + i]);
+        const float a1 = ldc(&fs[c * n + kk]), j1 = ldc(&fs[(3 + c) * n + kk]);
+        // prediction of this component (Sec. 2.4 step 7a)
+        const F2 xp = ds_pred_x(x0, v0, a0, j0, dt, h2, h3);
+        const F2 vp = ds_pred_v(v0, a0, j0, dt, h2);
+        // 2nd and 3rd derivative at the start of the step from the end-point values
+        const float da = __fadd_rn(a0, -a1);
+        const float a2 = __fmul_rn(fmaf(-6.0f, da, -__fmul_rn(dt, fmaf(4.0f, j0, __fmul_rn(2.0f, j1)))), idt2);
+        const float a3 = __fmul_rn(fmaf(12.0f, da, __fmul_rn(__fmul_rn(6.0f, dt), __fadd_rn(j0, j1))), idt3);
+        const F2 x1 = ds_canon(ds_add_f(xp, fmaf(a3, h5, __fmul_rn(a2, h4))));
+        const F2 v1 = ds_canon(ds_add_f(vp, fmaf(a3, h4, __fmul_rn(a2, h3))));
+        const float a2e = fmaf(dt, a3, a2);  // 2nd derivative at the end of the step
+        const float na1 = norm3_group(real ? a1 : 0.f), nj1 = norm3_group(real ? j1 : 0.f);
+        const float na2 = norm3_group(real ? a2e : 0.f), na3 = norm3_group(real ? a3 : 0.f);
+        const long long dtau = next_block_step_f(d, na1, nj1, na2, na3, dtau_old, T);
+        const bool fin = isfinite(x1.h) && isfinite(v1.h) && isfinite(a1) && isfinite(j1);
+        if (valid) {
+            if (!behind) {
+                bad |= 2;
+            } else {
+                if (real) {
+                    if (!fin) bad |= 1;
+                    st_ds(d.xs, n, c, i, x1);
+                    st_ds(d.vs, n, c, i, v1);
+                    d.af[c * n + i] = a1;
+                    d.jf[c * n + i] = j1;
+                }
+                if (q == 0) {
+                    d.tau[i] = T;
+                    d.dtau[i] = dtau;
+                    const long long tn = T + dtau;
+                    d.tnext[i] = tn;
+                    mymin = tn < mymin ? tn : mymin;
+                }
+            }
+        }
+    }
+}
+
 // Correction (Sec. 2.4 step 7d, Hermite scheme) of active slots [k_lo, k_hi) with
 // the new force in fsum, at block time T: the calling warps w0, w0 + ws, ... take
 // eight particles at a time, four lanes per particle -- lanes 0-2 the x, y, z
@@ -515,8 +901,8 @@ __device__ __forceinline__ long long next_block_step(const Dev &d, double num, d
 // roots side by side.  mymin collects the new next times, bad the fault bits
 // (1 non-finite, 2 a particle not behind T, which is left untouched).
 template <bool COH>
-__device__ __forceinline__ void correct_slots(const Dev &d, long long T, int k_lo, int k_hi, int w0, int ws,
-                                              long long &mymin, int &bad)
+__device__ __forceinline__ void correct_slots64(const Dev &d, long long T, int k_lo, int k_hi, int w0, int ws,
+                                                long long &mymin, int &bad)
 {
     const int n = d.n;
     const int lane = threadIdx.x & 31;
@@ -597,6 +983,16 @@ __device__ __forceinline__ void correct_slots(const Dev &d, long long T, int k_l
     }
 }
 
+template <bool MIXED, bool COH>
+__device__ __forceinline__ void correct_slots(const Dev &d, long long T, int k_lo, int k_hi, int w0, int ws,
+                                              long long &mymin, int &bad)
+{
+    if (MIXED)
+        correct_slots_ds<COH>(d, T, k_lo, k_hi, w0, ws, mymin, bad);
+    else
+        correct_slots64<COH>(d, T, k_lo, k_hi, w0, ws, mymin, bad);
+}
+
 // ---------------------------------------------------------------- j-split reduction
 
 template <class P>
@@ -620,6 +1016,7 @@ struct Acc<float> {
         v.add(o.v.l);
     }
     __device__ double value() const { return v.as_double(); }
+    __device__ float result() const { return __fadd_rn(v.h, v.l); }
 };
 template <>
 struct Acc<double> {
@@ -628,6 +1025,7 @@ struct Acc<double> {
     __device__ void add(double f) { v += f; }
     __device__ void add(const Acc &o) { v += o.v; }
     __device__ double value() const { return v; }
+    __device__ double result() const { return v; }
 };
 
 // Every (component, slot) sum of the S j-split partials is taken in one canonical
@@ -638,7 +1036,7 @@ struct Acc<double> {
 constexpr int RED_R = 8;
 
 template <class P>
-__device__ __forceinline__ double combine8(Acc<P> q[RED_R])
+__device__ __forceinline__ P combine8(Acc<P> q[RED_R])
 {
     q[0].add(q[1]);
     q[2].add(q[3]);
@@ -647,7 +1045,15 @@ __device__ __forceinline__ double combine8(Acc<P> q[RED_R])
     q[0].add(q[2]);
     q[4].add(q[6]);
     q[0].add(q[4]);
-    return q[0].value();
+    return q[0].result();
+}
+
+// The summed force of slot k, component c: FP64 on the FP64 path, FP32 on the
+// mixed path (see fsum_f).
+template <class P>
+__device__ __forceinline__ void store_fsum(const Dev &d, int c, int k, P v)
+{
+    ((P *)d.fsum)[(long long)c * d.n + k] = v;
 }
 
 // Sums the S partials of slots [k0, k0 + nvalid) into fsum (large tiles): one
@@ -674,7 +1080,7 @@ __device__ void tile_reduce(const Dev &d, int nact, int S, int k0, int nvalid)
             for (int r = 0; r < RED_R; r++)
                 if (s0 + r < S) q[r].add(v[r]);
         }
-        d.fsum[(long long)c * d.n + k] = combine8<P>(q);
+        store_fsum<P>(d, c, k, combine8<P>(q));
     }
 }
 
@@ -706,7 +1112,7 @@ __device__ void tile_reduce_small(const Dev &d, int nact, int S, int k0, int nva
         Acc<P> q[RED_R];
 #pragma unroll
         for (int r = 0; r < RED_R; r++) q[r] = s_q[pidx][r];
-        d.fsum[(long long)c * d.n + k] = combine8<P>(q);
+        store_fsum<P>(d, c, k, combine8<P>(q));
     }
     __syncthreads();
 }
@@ -743,7 +1149,7 @@ __device__ __forceinline__ void finish_item(const Dev &d, int nact, const Plan &
             __syncthreads();
             long long mymin = LLONG_MAX;
             int bad = 0;
-            correct_slots<COH>(d, T, k0, k0 + nvalid, threadIdx.x >> 5, FT / 32, mymin, bad);
+            correct_slots<sizeof(P) == 4, COH>(d, T, k0, k0 + nvalid, threadIdx.x >> 5, FT / 32, mymin, bad);
             if (bad & 2) set_err(d.ctrl, ST_EINVAL);
             if (bad & 1) set_err(d.ctrl, ST_ENONFINITE);
             mymin = warp_min_ll(mymin);
@@ -907,14 +1313,17 @@ __device__ void phase_force_mixed(const Dev &d, int nact, const Plan &pl, bool t
 
 // The last CTA to finish a kernel that corrected in its tile tails turns the
 // running minimum into the next block time and counts the step.
-__device__ __forceinline__ void finalize_step(const Dev &d, int nact, long long T)
+// Only the CTAs that took work items (the first min(grid, items)) count in.
+__device__ __forceinline__ void finalize_step(const Dev &d, int nact, long long T, long long items)
 {
     Ctrl *ctrl = d.ctrl;
+    const unsigned nin = (unsigned)min((long long)gridDim.x, items);
+    if (blockIdx.x >= nin) return;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         const unsigned prev = atomicAdd(&ctrl->done, 1u);
-        if (prev == gridDim.x - 1) {
+        if (prev == nin - 1) {
             __threadfence();
             const long long next = (long long)atomicAdd((unsigned long long *)&ctrl->T_acc, 0ull);
             ctrl->T_last = T;
@@ -944,7 +1353,7 @@ __global__ void __launch_bounds__(FT, 4) k_force_mixed(FArgs fa)
     if (TAIL && pl.mode == 1) {
         const long long T = d.ctrl->T_cur;
         phase_force_mixed<SOFT, false>(d, nact, pl, true, T, (unsigned long long *)&d.ctrl->T_acc);
-        finalize_step(d, nact, T);
+        finalize_step(d, nact, T, pl.items);
     } else {
         phase_force_mixed<SOFT, false>(d, nact, pl, false, 0, nullptr);
     }
@@ -1014,7 +1423,7 @@ __global__ void __launch_bounds__(FT, 4) k_force_fp64(FArgs fa)
         }
         finish_item<double, false>(d, nact, pl, it, tail, T, (unsigned long long *)&d.ctrl->T_acc);
     }
-    if (tail) finalize_step(d, nact, T);
+    if (tail) finalize_step(d, nact, T, pl.items);
 }
 
 struct CArgs {
@@ -1027,6 +1436,7 @@ struct CArgs {
 
 // Corrects every active particle and (last CTA) turns the running minimum into the
 // next block time.
+template <bool MIXED>
 __global__ void __launch_bounds__(CT) k_correct(CArgs ca)
 {
     pdl_trigger();
@@ -1036,14 +1446,19 @@ __global__ void __launch_bounds__(CT) k_correct(CArgs ca)
     const int nact = min(ctrl->nact, d.n);
     if (nact <= 0) return;
     if (ca.tail_ok && make_plan(nact, d.npad, ca.grid, ca.tn, ca.mixed != 0, d.cap).mode == 1) return;
+    // only the CTAs that have particles to correct take part (eight per warp); the
+    // others leave at once, so a small active set costs a few CTAs, not the grid
+    constexpr int PER_CTA = (CT / 32) * 8;
+    const int ncta = min((int)gridDim.x, (nact + PER_CTA - 1) / PER_CTA);
+    if ((int)blockIdx.x >= ncta) return;
     const long long T = ctrl->T_cur;
     const int n = d.n;
     const int lane = threadIdx.x & 31;
     const int gwarp = (blockIdx.x * CT + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * CT) >> 5;
+    const int nwarps = (ncta * CT) >> 5;
     long long mymin = LLONG_MAX;
     int bad = 0;
-    correct_slots<false>(d, T, 0, nact, gwarp, nwarps, mymin, bad);
+    correct_slots<MIXED, false>(d, T, 0, nact, gwarp, nwarps, mymin, bad);
     if (bad & 2) set_err(ctrl, ST_EINVAL);
     if (bad & 1) set_err(ctrl, ST_ENONFINITE);
     mymin = warp_min_ll(mymin);
@@ -1053,7 +1468,7 @@ __global__ void __launch_bounds__(CT) k_correct(CArgs ca)
     if (threadIdx.x == 0) {
         __threadfence();
         const unsigned prev = atomicAdd(&ctrl->done, 1u);
-        if (prev == gridDim.x - 1) {
+        if (prev == (unsigned)ncta - 1) {
             __threadfence();
             const long long next = (long long)atomicAdd((unsigned long long *)&ctrl->T_acc, 0ull);
             ctrl->T_last = T;
@@ -1071,18 +1486,37 @@ __global__ void __launch_bounds__(CT) k_correct(CArgs ca)
 
 // Initial steps after the first full force evaluation (Sec. 2.4 steps 3-4 and the
 // initial step dt = eta |a| / |jerk|), and a = fsum, jerk = fsum.
+// Reads the summed force of slot i into a[], jerk[] and stores it as the state's
+// a and jerk (FP64 planes, or the mixed path's FP32 ones).
+template <bool MIXED>
+__device__ __forceinline__ void take_force(const Dev &d, int slot, int i, double a[3], double j[3])
+{
+    const int n = d.n;
+    for (int c = 0; c < 3; c++) {
+        if (MIXED) {
+            const float *fs = (const float *)d.fsum;
+            const float af = fs[(long long)c * n + slot], jf = fs[(long long)(3 + c) * n + slot];
+            d.af[c * n + i] = af;
+            d.jf[c * n + i] = jf;
+            a[c] = af;
+            j[c] = jf;
+        } else {
+            a[c] = d.fsum[(long long)c * n + slot];
+            j[c] = d.fsum[(long long)(3 + c) * n + slot];
+            d.a[c * n + i] = a[c];
+            d.jk[c * n + i] = j[c];
+        }
+    }
+}
+
+template <bool MIXED>
 __global__ void k_init_steps(Dev d)
 {
     const int n = d.n;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double a[3], j[3];
-    for (int c = 0; c < 3; c++) {
-        a[c] = d.fsum[(long long)c * n + i];
-        j[c] = d.fsum[(long long)(3 + c) * n + i];
-        d.a[c * n + i] = a[c];
-        d.jk[c * n + i] = j[c];
-    }
+    take_force<MIXED>(d, i, i, a, j);
     const double na = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
     const double nj = sqrt(j[0] * j[0] + j[1] * j[1] + j[2] * j[2]);
     const double dt0 = d.eta * na / nj;
@@ -1180,8 +1614,8 @@ __global__ void __launch_bounds__(ET) k_energy_fp64(Dev d)
 // Mixed path: the same sums with FP32 pair arithmetic on the double-single
 // j-records (one Newton step refines rsqrt.approx to about one float ulp) and a
 // compensated accumulator per term, so the sum adds no error beyond the terms'
-// own rounding; FP64 result; kinetic terms from the FP64 state predicted by
-// k_predict_all<false>.
+// own rounding; FP64 result; kinetic terms from the FP64 prediction of the state
+// in the planes pd (k_predict_all<true, false>).
 __global__ void __launch_bounds__(ET) k_energy_mixed(Dev d)
 {
     const int n = d.n, np = d.npad;
@@ -1335,7 +1769,7 @@ __global__ void __launch_bounds__(FT, 4) k_steps(SArgs a)
             int bad = 0;
             const int gwarp = (blockIdx.x * FT + threadIdx.x) >> 5;
             const int nwarps = (gridDim.x * FT) >> 5;
-            correct_slots<true>(d, T, 0, nact, gwarp, nwarps, mymin, bad);
+            correct_slots<true, true>(d, T, 0, nact, gwarp, nwarps, mymin, bad);
             if (bad & 2) set_err(ctrl, ST_EINVAL);
             if (bad & 1) set_err(ctrl, ST_ENONFINITE);
             mymin = warp_min_ll(mymin);
