@@ -83,6 +83,13 @@ typedef struct gd_opts {
     int32_t tail_correct; /* three-kernel path: 1 = the force kernel corrects warp-mode tiles in
                            their reduction tails and finalizes the step (k_correct then only
                            handles i-parallel plans); 0 = k_correct always corrects */
+    int32_t cluster;    /* GD_MIXED, gd_evolve: 1 (default) = block steps with few active
+                           particles run inside one thread-block cluster that holds the whole
+                           system in its shared memory (no kernel launch per step), larger
+                           steps on the full GPU; used when n fits (about 20000 particles with
+                           16-CTA clusters) and the GPU can launch the cluster, else ignored.
+                           0 = every step on the full GPU.  The two differ in the order of
+                           the force sums (last bits); each is deterministic. */
 } gd_opts;
 
 typedef struct gd_stats {
@@ -92,9 +99,11 @@ typedef struct gd_stats {
     double interactions;   /* sum of N_act * N over all force evaluations */
     int64_t last_nact;     /* N_act of the last block step */
     int64_t kernel_launches; /* CUDA kernels this context has launched (host count) */
-    double phase_ms[3];    /* fused gd_evolve path: time spent in its select/predict, force
-                              (+ small-set correction) and correction phases, each up to and
-                              including its grid barrier (one CTA's device clock) */
+    double phase_ms[3];    /* time spent in the select/predict, force (+ small-set correction)
+                              and correction phases of the fused gd_evolve kernel and of the
+                              small-step cluster kernel, each up to and including its grid or
+                              cluster barrier (one CTA's device clock); 0 on the three-kernel
+                              path */
 } gd_stats;
 
 typedef struct gd_ctx gd_ctx;
@@ -155,14 +164,30 @@ int gd_get_tuning(gd_ctx *c, int32_t *mode_cut, int16_t *split, int8_t *mode, fl
 /* Counters since gd_init. */
 int gd_get_stats(gd_ctx *c, gd_stats *s);
 
-/* Device time of the force-kernel launches recorded (CUDA events on the
- * context's stream) since the last call, for launches with a non-empty active
- * set (needs opts.time_force = 1): *ms_total summed milliseconds, *launches
+/* Device time of the full-GPU force-kernel launches recorded (CUDA events on
+ * the context's stream) since the last call, for launches with a non-empty
+ * active set (needs opts.time_force = 1; the small-step cluster's steps are
+ * timed by gd_cluster_time): *ms_total summed milliseconds, *launches
  * their count, *interactions the sum of N_act * N they computed.  With the fused
  * gd_evolve path the timed kernel is the fused block-step kernel (prediction,
  * force and correction together).  Any pointer may be NULL.  Resets the
  * counters. */
 int gd_kernel_time(gd_ctx *c, double *ms_total, int64_t *launches, double *interactions);
+
+/* The small-step cluster gd_evolve uses (opts.cluster): *csize CTAs per
+ * cluster (0 = not used: FP64 context, option off, n too large for its shared
+ * memory, or no such cluster can be launched), *per_cta particles each CTA
+ * holds, *max_nact the largest active count a cluster step takes (larger steps
+ * run on the full GPU).  Any pointer may be NULL. */
+int gd_cluster_info(gd_ctx *c, int32_t *csize, int32_t *per_cta, int32_t *max_nact);
+
+/* Device time of the small-step cluster launches of gd_evolve's graph or eager
+ * path recorded since the last call (needs opts.time_force = 1): *ms_total
+ * summed milliseconds, *launches their count (a launch takes zero or more block
+ * steps).  The block steps and interactions of the cluster are the context's
+ * totals (gd_get_stats) minus those gd_kernel_time reports.  Any pointer may be
+ * NULL.  Resets the counters. */
+int gd_cluster_time(gd_ctx *c, double *ms_total, int64_t *launches);
 
 void gd_free(gd_ctx *c);
 

@@ -29,7 +29,9 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = SRC + [os.path.join(INCLUDE, "gravidy.h"), os.path.join(HERE, "csrc", "kernels.cuh")]
+    csrc = os.path.join(HERE, "csrc")
+    deps = SRC + [os.path.join(INCLUDE, "gravidy.h")] + [
+        os.path.join(csrc, f) for f in os.listdir(csrc) if f.endswith((".cu", ".cuh", ".h"))]
     return any(os.path.getmtime(p) > t for p in deps)
 
 

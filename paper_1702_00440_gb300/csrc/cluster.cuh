@@ -1,0 +1,455 @@
+// cluster.cuh -- small block steps inside one thread-block cluster (mixed path).
+// Included once, by gravidy.cu, after kernels.cuh.
+//
+// Most block steps of a collisional system move only a handful of particles
+// (Sec. 2.2: the active set at a block time is the set of particles whose next
+// time equals it), and for those the three full-GPU kernels of a step cost far more
+// in launch and memory round trips than in arithmetic.  k_cluster_steps runs such
+// steps with the whole system resident in the shared memory of one cluster of C
+// CTAs (C = 16 where the GPU allows it): CTA r owns particles [r P, (r + 1) P).
+// Per block step T (Sec. 2.4 steps 5-7):
+//   1. every CTA predicts its own particles to T into its j-records (shared
+//      memory) and lists its active ones;                      cluster barrier
+//   2. every CTA reads the C active counts (the same total everywhere), gathers
+//      the active particles' j-records from their owners, and sums the force of
+//      every active particle over its own j-range; the partial sums go to the
+//      owner's shared memory (distributed shared memory);      cluster barrier
+//   3. owners add the C partials in rank order, correct, choose the new steps
+//      (the same arithmetic as the mixed three-kernel path), and post their
+//      minimum next time;                                      cluster barrier
+//   4. every CTA takes the minimum over the C posts: the next block time; owners
+//      write their corrected particles through to global memory.
+// The loop stops, with the same decision in every CTA, when a step has more than
+// `ns` active particles (then the full-GPU kernels take that step), when the block
+// time passes tick_end, after max_steps steps, or on a fault.  All cluster
+// barriers are unconditional in the loop body, so every CTA passes the same
+// sequence of them; a last barrier keeps every CTA's shared memory alive until no
+// CTA can still read it.
+#pragma once
+
+#include <cooperative_groups.h>
+
+namespace gdk {
+
+namespace cgx = cooperative_groups;
+
+constexpr int CL_T = 512;     // threads per CTA (one CTA per SM)
+constexpr int CL_W = CL_T / 32;
+constexpr int CL_MAXC = 16;   // largest cluster
+constexpr int CL_NS = 128;    // most active particles a cluster step takes
+constexpr int CL_ROUNDS = 3;  // particles per thread at most (P <= CL_ROUNDS * CL_T)
+
+// Shared-memory layout of a CTA owning up to P particles (P a multiple of 32).
+struct ClLayout {
+    int P;
+    size_t xh, xl, vh, vl, af, jf, mf, tau, dtau, jA, jB, jC, lact, iA, iB, iC, aown, oA, oB, oC, aloc, part, tp, bytes;
+    __host__ __device__ ClLayout(int P_) : P(P_)
+    {
+        size_t o = 0;
+        auto take = [&](size_t bytes) {
+            const size_t at = o;
+            o += (bytes + 15) / 16 * 16;
+            return at;
+        };
+        jA = take(sizeof(float4) * P);
+        jB = take(sizeof(float4) * P);
+        iA = take(sizeof(float4) * CL_NS);
+        iB = take(sizeof(float4) * CL_NS);
+        tau = take(sizeof(long long) * P);
+        dtau = take(sizeof(long long) * P);
+        jC = take(sizeof(float2) * P);
+        iC = take(sizeof(float2) * CL_NS);
+        xh = take(sizeof(float) * 3 * P);
+        xl = take(sizeof(float) * 3 * P);
+        vh = take(sizeof(float) * 3 * P);
+        vl = take(sizeof(float) * 3 * P);
+        af = take(sizeof(float) * 3 * P);
+        jf = take(sizeof(float) * 3 * P);
+        mf = take(sizeof(float) * P);
+        lact = take(sizeof(int) * CL_NS);
+        aown = take(sizeof(int) * CL_NS);
+        oA = take(sizeof(float4) * CL_NS);
+        oB = take(sizeof(float4) * CL_NS);
+        oC = take(sizeof(float2) * CL_NS);
+        aloc = take(sizeof(int) * CL_NS);
+        part = take(sizeof(float) * CL_NS * CL_MAXC * 6);
+        tp = take(sizeof(float) * CL_W * 6);
+        bytes = o;
+    }
+};
+
+struct ClArgs {
+    Dev d;
+    int P;          // particles per CTA
+    int ns;         // largest active count taken here (<= CL_NS)
+    int max_steps;  // block steps per launch
+};
+
+// Mailbox a CTA posts for the others (read through distributed shared memory).
+struct ClBox {
+    int cnt;         // active particles of this CTA in the current step
+    int bad;         // fault bits seen by this CTA (1 non-finite)
+    long long mn;    // minimum next time over this CTA's particles after the step
+};
+
+template <bool SOFT>
+__global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
+{
+    cgx::cluster_group cl = cgx::this_cluster();
+    const int C = (int)cl.num_blocks();
+    const int r = (int)cl.block_rank();
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const Dev &d = a.d;
+    const int n = d.n, P = a.P;
+    const ClLayout L(P);
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *xh = (float *)(smem + L.xh), *xl = (float *)(smem + L.xl);
+    float *vh = (float *)(smem + L.vh), *vl = (float *)(smem + L.vl);
+    float *af = (float *)(smem + L.af), *jf = (float *)(smem + L.jf), *mf = (float *)(smem + L.mf);
+    long long *tau = (long long *)(smem + L.tau), *dtau = (long long *)(smem + L.dtau);
+    float4 *jA = (float4 *)(smem + L.jA), *jB = (float4 *)(smem + L.jB);
+    float2 *jC = (float2 *)(smem + L.jC);
+    int *lact = (int *)(smem + L.lact), *aown = (int *)(smem + L.aown), *aloc = (int *)(smem + L.aloc);
+    float4 *oA = (float4 *)(smem + L.oA), *oB = (float4 *)(smem + L.oB);  // outbox: own active
+    float2 *oC = (float2 *)(smem + L.oC);                                 // particles' j-records
+    float4 *iA = (float4 *)(smem + L.iA), *iB = (float4 *)(smem + L.iB);
+    float2 *iC = (float2 *)(smem + L.iC);
+    float *part = (float *)(smem + L.part);  // [slot][rank][6]
+    float *tp = (float *)(smem + L.tp);      // [task][6]
+    __shared__ ClBox box;
+    __shared__ int s_off[CL_MAXC + 1];
+    __shared__ int s_wc[CL_ROUNDS * CL_W];
+    __shared__ int s_base;
+    __shared__ long long s_wmin[CL_W];
+    __shared__ int s_wbad[CL_W];
+    __shared__ long long s_T;
+    __shared__ int s_bad;
+
+    const int p0 = r * P;
+    const int Pr = max(0, min(P, n - p0));
+    for (int p = t; p < Pr; p += CL_T) {
+        const int i = p0 + p;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            xh[c * P + p] = d.xs[c * n + i];
+            xl[c * P + p] = d.xs[(3 + c) * n + i];
+            vh[c * P + p] = d.vs[c * n + i];
+            vl[c * P + p] = d.vs[(3 + c) * n + i];
+            af[c * P + p] = d.af[c * n + i];
+            jf[c * P + p] = d.jf[c * n + i];
+        }
+        mf[p] = d.mf[i];
+        tau[p] = d.tau[i];
+        dtau[p] = d.dtau[i];
+    }
+    Ctrl *ctrl = d.ctrl;
+    long long T = ctrl->T_cur;
+    const long long tick_end = ctrl->tick_end;
+    long long T_last = 0, psteps = 0;
+    int last_n = 0, steps = 0;
+    unsigned long long ph[3] = {0ull, 0ull, 0ull};  // CTA 0's clock: predict, force, correct
+    const float eps2 = d.eps2f;
+    __syncthreads();
+
+    for (;;) {
+        // the exit tests read values every CTA holds identically
+        if (T > tick_end || steps >= a.max_steps) break;
+
+        // ---- 1. predict own particles, list own active ones (ascending local index)
+        const unsigned long long t0 = global_ns();
+        long long mn = LLONG_MAX;
+        unsigned bal[CL_ROUNDS];
+        float4 rA[CL_ROUNDS], rB[CL_ROUNDS];
+        float2 rC[CL_ROUNDS];
+#pragma unroll
+        for (int rd = 0; rd < CL_ROUNDS; rd++) {
+            const int p = rd * CL_T + t;
+            bool act = false;
+            if (p < Pr) {
+                const long long tn = tau[p] + dtau[p];
+                act = tn == T;
+                if (!act) mn = tn < mn ? tn : mn;
+                float dt, idt;
+                step_f(d, T - tau[p], dt, idt);
+                const float h2 = __fmul_rn(0.5f, __fmul_rn(dt, dt));
+                const float h3 = __fmul_rn(__fmul_rn(__fmul_rn(dt, dt), dt), 1.0f / 6.0f);
+                F2 xp[3];
+                float vp[3];
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    const F2 x0{xh[c * P + p], xl[c * P + p]}, v0{vh[c * P + p], vl[c * P + p]};
+                    xp[c] = ds_pred_x(x0, v0, af[c * P + p], jf[c * P + p], dt, h2, h3);
+                    vp[c] = ds_pred_v_rec(v0, af[c * P + p], jf[c * P + p], dt, h2);
+                }
+                rA[rd] = make_float4(xp[0].h, xp[1].h, xp[2].h, mf[p]);
+                rB[rd] = make_float4(xp[0].l, xp[1].l, xp[2].l, vp[0]);
+                rC[rd] = make_float2(vp[1], vp[2]);
+                jA[p] = rA[rd];
+                jB[p] = rB[rd];
+                jC[p] = rC[rd];
+            }
+            bal[rd] = __ballot_sync(0xffffffffu, act);
+            if (lane == 0) s_wc[rd * CL_W + warp] = __popc(bal[rd]);
+        }
+        __syncthreads();
+        if (warp == 0) {  // exclusive scan of the (round, warp) counts: ascending particle order
+            static_assert(CL_ROUNDS * CL_W <= 64, "two counts per lane");
+            const int c0 = s_wc[lane], c1 = lane + 32 < CL_ROUNDS * CL_W ? s_wc[lane + 32] : 0;
+            // entries 0-31 on the lanes in order, then entries 32-47
+            int e0 = c0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, e0, o);
+                if (lane >= o) e0 += y;
+            }
+            const int tot0 = __shfl_sync(0xffffffffu, e0, 31);
+            int e1 = c1;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, e1, o);
+                if (lane >= o) e1 += y;
+            }
+            __syncwarp();
+            s_wc[lane] = e0 - c0;
+            if (lane + 32 < CL_ROUNDS * CL_W) s_wc[lane + 32] = tot0 + e1 - c1;
+            if (lane == 31) s_base = tot0 + e1;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int rd = 0; rd < CL_ROUNDS; rd++) {
+            if ((bal[rd] >> lane) & 1u) {
+                const int pos = s_wc[rd * CL_W + warp] + __popc(bal[rd] & ((1u << lane) - 1u));
+                if (pos < CL_NS) {
+                    lact[pos] = rd * CL_T + t;
+                    oA[pos] = rA[rd];
+                    oB[pos] = rB[rd];
+                    oC[pos] = rC[rd];
+                }
+            }
+        }
+        if (t == 0) box.cnt = s_base;
+        cl.sync();  // B1: j-records, active lists and counts of every CTA are visible
+
+        // ---- 2. the step's active set: counts of all CTAs, prefix offsets
+        if (warp == 0) {  // lane q reads CTA q's count; a shuffle scan gives the offsets
+            const int cq = lane < C ? cl.map_shared_rank(&box, lane)->cnt : 0;
+            int inc = cq;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (lane < C) s_off[lane] = inc - cq;
+            if (lane == 31) s_off[C] = inc;
+            // owner table of the step's active slots (only needed if the cluster takes it)
+            if (__shfl_sync(0xffffffffu, inc, 31) <= a.ns)
+                for (int k = inc - cq; k < inc; k++) {
+                    aown[k] = lane;
+                    aloc[k] = k - (inc - cq);
+                }
+        }
+        __syncthreads();
+        const int nact = s_off[C];
+        const unsigned long long t1 = global_ns();
+        ph[0] += t1 - t0;
+        if (nact > a.ns) break;  // a large step: the full-GPU kernels take it
+        // gather the active particles' j-records (i-records of this step)
+        for (int k = t; k < nact; k += CL_T) {
+            const int q = aown[k], kl = aloc[k];
+            iA[k] = cl.map_shared_rank(oA, q)[kl];
+            iB[k] = cl.map_shared_rank(oB, q)[kl];
+            iC[k] = cl.map_shared_rank(oC, q)[kl];
+        }
+        __syncthreads();
+        // forces over this CTA's j-range: tasks (active, j-segment); with fewer than
+        // CL_W active particles each one's j-range is cut into Sw = 2^lgS segments
+        int lgS = 0;
+        if (nact < CL_W) lgS = 31 - __clz(CL_W / nact);
+        const int Sw = 1 << lgS;
+        const int seg = (((Pr + Sw - 1) >> lgS) + 31) & ~31;
+        const int ntask = nact << lgS;
+        for (int task = warp; task < ntask; task += CL_W) {
+            const int k = task >> lgS, sg = task & (Sw - 1);
+            const int jb = sg * seg, je = min(jb + seg, Pr);
+            const float4 Ai = iA[k], Bi = iB[k];
+            const float2 Ci = iC[k];
+            float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+            for (int j = jb + lane; j < je; j += 32)
+                pair_mixed<SOFT>(jA[j], jB[j], jC[j], Ai.x, Ai.y, Ai.z, Bi.x, Bi.y, Bi.z, Bi.w, Ci.x, Ci.y, eps2, f);
+#pragma unroll
+            for (int c = 0; c < 6; c++)
+                for (int o = 16; o > 0; o >>= 1) f[c] = __fadd_rn(f[c], __shfl_xor_sync(0xffffffffu, f[c], o));
+            // lane c < 6 stores component c (selected without indexing the array)
+            float mine_c = f[0];
+#pragma unroll
+            for (int c = 1; c < 6; c++) mine_c = lane == c ? f[c] : mine_c;
+            if (Sw == 1) {
+                if (lane < 6) {
+                    float *dst = cl.map_shared_rank(part, aown[k]);
+                    dst[(aloc[k] * CL_MAXC + r) * 6 + lane] = mine_c;
+                }
+            } else if (lane < 6) {
+                tp[task * 6 + lane] = mine_c;
+            }
+        }
+        if (Sw > 1) {
+            // this CTA's partial of active k: a pairwise tree over its Sw segment sums
+            for (int lh = lgS - 1; lh >= 0; lh--) {
+                const int h = 1 << lh;
+                __syncthreads();
+                for (int w = t; w < (nact * 6) << lh; w += CL_T) {
+                    const int c = w % 6, ks = w / 6, k = ks >> lh, sg = ks & (h - 1);
+                    const int at = (((k << lgS) + sg) * 6) + c;
+                    tp[at] = __fadd_rn(tp[at], tp[at + h * 6]);
+                }
+            }
+            __syncthreads();
+            for (int w = t; w < nact * 6; w += CL_T) {
+                const int k = w / 6, c = w % 6;
+                float *dst = cl.map_shared_rank(part, aown[k]);
+                dst[(aloc[k] * CL_MAXC + r) * 6 + c] = tp[((k << lgS) * 6) + c];
+            }
+        }
+        cl.sync();  // B2: every partial has reached its owner
+        const unsigned long long t2 = global_ns();
+        ph[1] += t2 - t1;
+
+        // ---- 3. owners: sum the C partials (rank order), correct, new steps
+        const int mine = s_off[r + 1] - s_off[r];
+        int bad = 0;
+        {
+            const int q4 = lane & 3;
+            const int c = q4 < 3 ? q4 : 2;
+            const bool real = q4 < 3;
+            const int k = warp * 8 + (lane >> 2);
+            if (warp * 8 < mine) {
+                const bool valid = k < mine;
+                const int kk = valid ? k : mine - 1;
+                const int p = lact[kk];
+                // the C partials in a fixed pairwise tree (absent ranks count zero)
+                float pa[CL_MAXC], pj[CL_MAXC];
+#pragma unroll
+                for (int q = 0; q < CL_MAXC; q++) {
+                    pa[q] = q < C ? part[(kk * CL_MAXC + q) * 6 + c] : 0.f;
+                    pj[q] = q < C ? part[(kk * CL_MAXC + q) * 6 + 3 + c] : 0.f;
+                }
+#pragma unroll
+                for (int h = CL_MAXC / 2; h >= 1; h >>= 1)
+#pragma unroll
+                    for (int q = 0; q < h; q++) {
+                        pa[q] = __fadd_rn(pa[q], pa[q + h]);
+                        pj[q] = __fadd_rn(pj[q], pj[q + h]);
+                    }
+                const float a1 = pa[0], j1 = pj[0];
+                const F2 x0{xh[c * P + p], xl[c * P + p]}, v0{vh[c * P + p], vl[c * P + p]};
+                const float a0 = af[c * P + p], j0 = jf[c * P + p];
+                const long long dtau_old = dtau[p];
+                F2 x1, v1;
+                long long dtn;
+                ds_correct(d, real, T - tau[p], dtau_old, T, x0, v0, a0, j0, a1, j1, x1, v1, dtn);
+                const bool fin = isfinite(x1.h) && isfinite(v1.h) && isfinite(a1) && isfinite(j1);
+                __syncwarp();
+                if (valid) {
+                    if (real) {
+                        if (!fin) bad |= 1;
+                        xh[c * P + p] = x1.h;
+                        xl[c * P + p] = x1.l;
+                        vh[c * P + p] = v1.h;
+                        vl[c * P + p] = v1.l;
+                        af[c * P + p] = a1;
+                        jf[c * P + p] = j1;
+                    }
+                    if (q4 == 0) {
+                        tau[p] = T;
+                        dtau[p] = dtn;
+                        mn = T + dtn < mn ? T + dtn : mn;
+                    }
+                }
+            }
+        }
+        mn = warp_min_ll(mn);
+        bad = __reduce_or_sync(0xffffffffu, bad);
+        if (lane == 0) {
+            s_wmin[warp] = mn;
+            s_wbad[warp] = bad;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            long long m = lane < CL_W ? s_wmin[lane] : LLONG_MAX;
+            int b = lane < CL_W ? s_wbad[lane] : 0;
+            m = warp_min_ll(m);
+            b = __reduce_or_sync(0xffffffffu, b);
+            if (lane == 0) {
+                box.mn = m;
+                box.bad = b;
+            }
+        }
+        cl.sync();  // B3: corrected state and the posts of every CTA are visible
+
+        // write the corrected particles through to global memory; issued after the
+        // barrier, whose release would otherwise wait for these stores to reach L2
+        for (int k = t; k < mine; k += CL_T) {
+            const int p = lact[k], i = p0 + p;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                d.xs[c * n + i] = xh[c * P + p];
+                d.xs[(3 + c) * n + i] = xl[c * P + p];
+                d.vs[c * n + i] = vh[c * P + p];
+                d.vs[(3 + c) * n + i] = vl[c * P + p];
+                d.af[c * n + i] = af[c * P + p];
+                d.jf[c * n + i] = jf[c * P + p];
+            }
+            d.tau[i] = tau[p];
+            d.dtau[i] = dtau[p];
+            d.tnext[i] = tau[p] + dtau[p];
+        }
+
+        // ---- 4. next block time: minimum over the C posts
+        if (warp == 0) {  // lane q reads CTA q's post
+            long long m = LLONG_MAX;
+            int b = 0;
+            if (lane < C) {
+                const ClBox *bx = cl.map_shared_rank(&box, lane);
+                m = bx->mn;
+                b = bx->bad;
+            }
+            m = warp_min_ll(m);
+            b = __reduce_or_sync(0xffffffffu, b);
+            if (lane == 0) {
+                s_T = m;
+                s_bad = b;
+            }
+        }
+        __syncthreads();
+        ph[2] += global_ns() - t2;
+        T_last = T;
+        last_n = nact;
+        psteps += nact;
+        steps++;
+        T = s_T;
+        const bool stop = s_bad != 0;
+        __syncthreads();  // s_T, s_bad are rewritten next step
+        if (stop) {
+            if (t == 0 && r == 0) set_err(ctrl, ST_ENONFINITE);
+            break;
+        }
+    }
+    cl.sync();  // no CTA leaves while another may still read its shared memory
+    if (r == 0 && t == 0) {
+        ctrl->T_cur = T;
+        ctrl->ph_ns[0] += ph[0];
+        ctrl->ph_ns[1] += ph[1];
+        ctrl->ph_ns[2] += ph[2];
+        if (steps > 0) {
+            ctrl->T_last = T_last;
+            ctrl->last_nact = last_n;
+            ctrl->nblock += steps;
+            ctrl->nsteps += psteps;
+            ctrl->interactions += (double)psteps * (double)n;
+            ctrl->epoch += (unsigned)steps;
+        }
+    }
+}
+
+}  // namespace gdk

@@ -18,6 +18,7 @@
 #include "gravidy.h"
 #include "kernels.cuh"
 #include "ensemble.cuh"
+#include "cluster.cuh"
 
 using namespace gdk;
 
@@ -30,6 +31,8 @@ struct gd_ctx {
     Tune tn;
     float tune_ms[32];  // autotuner: best force time per bucket (ms), 0 = not measured
     int grid_force, grid_sel, nchunks, grid_corr, grid_steps;
+    int cl_C, cl_P, cl_ns;  // small-step cluster: CTAs, particles per CTA, largest step; cl_C = 0: off
+    size_t cl_smem;
     bool mixed, soft;
     Ctrl *h_ctrl;       // pinned mirror
     Ctrl *h_snap;       // two pinned snapshots for the pipelined gd_evolve
@@ -43,6 +46,8 @@ struct gd_ctx {
     double force_ms;
     long long force_launches;
     double force_interactions;
+    double cl_ms;             // timed cluster launches (time_force)
+    long long cl_launches;
     std::string err;
     int sticky;
 };
@@ -188,6 +193,97 @@ void launch_step(gd_ctx *c, int slot, cudaEvent_t e0, cudaEvent_t e1, bool captu
     launch_correct(c);
 }
 
+// Small block steps inside one cluster (cluster.cuh), up to CL_STEPS per launch.
+constexpr int CL_STEPS = 4096;
+constexpr int CL_EV = 2 * 64;  // first timing event of the cluster launches (after the force pairs)
+
+void launch_cluster(gd_ctx *c)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c->cl_C);
+    cfg.blockDim = dim3(CL_T);
+    cfg.dynamicSmemBytes = c->cl_smem;
+    cfg.stream = c->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = c->cl_C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const ClArgs a{c->d, c->cl_P, c->cl_ns, CL_STEPS};
+    c->launches += 1;
+    if (c->soft)
+        cudaLaunchKernelEx(&cfg, k_cluster_steps<true>, a);
+    else
+        cudaLaunchKernelEx(&cfg, k_cluster_steps<false>, a);
+}
+
+// One cycle of gd_evolve: small steps in the cluster (when enabled) until a large
+// one, which the three step kernels then take.
+void launch_cycle(gd_ctx *c, int slot, cudaEvent_t e0, cudaEvent_t e1, bool capturing)
+{
+    if (c->cl_C) {
+        const unsigned fl = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+        if (c->opt.time_force) cudaEventRecordWithFlags(c->ev[CL_EV + 2 * slot], c->stream, fl);
+        launch_cluster(c);
+        if (c->opt.time_force) cudaEventRecordWithFlags(c->ev[CL_EV + 2 * slot + 1], c->stream, fl);
+    }
+    launch_step(c, slot, e0, e1, capturing);
+}
+
+// Chooses the cluster for small steps: 16 CTAs where the GPU can launch them (else
+// 8), each owning P particles in shared memory; leaves cl_C = 0 when n does not
+// fit or no such cluster can be resident.
+void cluster_setup(gd_ctx *c)
+{
+    c->cl_C = 0;
+    if (!c->mixed || !c->opt.cluster) return;
+    const void *fn = c->soft ? (const void *)k_cluster_steps<true> : (const void *)k_cluster_steps<false>;
+    int maxdyn = 0;
+    cudaDeviceGetAttribute(&maxdyn, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    for (int C : {CL_MAXC, 8}) {
+        const int P = (c->d.n + C - 1) / C;
+        const int P32 = (P + 31) / 32 * 32;
+        if (P32 > CL_ROUNDS * CL_T) continue;
+        const size_t bytes = ClLayout(P32).bytes;
+        if (bytes + fa.sharedSizeBytes > (size_t)maxdyn) continue;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess ||
+            cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, C > 8 ? 1 : 0) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(C);
+        cfg.blockDim = dim3(CL_T);
+        cfg.dynamicSmemBytes = bytes;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = C;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess || nclusters < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        c->cl_C = C;
+        c->cl_P = P32;
+        c->cl_smem = bytes;
+        // a small step costs the cluster about nact * n pair terms on C SMs; above
+        // about 2^21 terms the full GPU is faster
+        c->cl_ns = std::min(CL_NS, std::max(16, (1 << 21) / std::max(1, c->d.n)));
+        return;
+    }
+}
+
 bool use_fused(const gd_ctx *c) { return c->mixed && c->opt.fused && c->grid_steps > 0; }
 
 // One cooperative launch of up to max_steps fused block steps.
@@ -325,7 +421,7 @@ int build_graph(gd_ctx *c)
     for (int s = 0; s < G; s++) {
         cudaEvent_t e0 = c->opt.time_force ? c->ev[2 * s] : nullptr;
         cudaEvent_t e1 = c->opt.time_force ? c->ev[2 * s + 1] : nullptr;
-        launch_step(c, s, e0, e1, true);
+        launch_cycle(c, s, e0, e1, true);
     }
     c->launches = before;  // counted when the graph is launched
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
@@ -346,7 +442,7 @@ void drop_graph(gd_ctx *c)
 }
 
 // Adds the timed force launches of the last chunk (slots with nact > 0).
-int harvest_times(gd_ctx *c, int slots)
+int harvest_times(gd_ctx *c, int slots, bool with_cluster)
 {
     if (!c->opt.time_force) return GD_OK;
     CK(cudaMemcpyAsync(c->h_hist, c->d.nact_hist, sizeof(int) * slots, cudaMemcpyDeviceToHost, c->stream));
@@ -358,6 +454,14 @@ int harvest_times(gd_ctx *c, int slots)
         c->force_ms += ms;
         c->force_launches += 1;
         c->force_interactions += (double)c->h_hist[s] * (double)c->d.n;
+    }
+    if (c->cl_C && with_cluster) {
+        for (int s = 0; s < slots; s++) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, c->ev[CL_EV + 2 * s], c->ev[CL_EV + 2 * s + 1]));
+            c->cl_ms += ms;
+            c->cl_launches += 1;
+        }
     }
     return GD_OK;
 }
@@ -439,6 +543,19 @@ int autotune(gd_ctx *c, int reps)
 // and the launches are not overlapped.
 constexpr int FUSED_STEPS = 1024;
 
+// One launch chunk of the fused path: cluster cycles (small steps in the cluster,
+// then one fused step) when the cluster is enabled, else FUSED_STEPS fused steps.
+int fused_chunk(gd_ctx *c)
+{
+    if (!c->cl_C) return launch_fused(c, FUSED_STEPS);
+    for (int s = 0; s < c->graph_steps; s++) {
+        launch_cluster(c);
+        int rc = launch_fused(c, 1);
+        if (rc) return rc;
+    }
+    return GD_OK;
+}
+
 int evolve_fused(gd_ctx *c, long long tick_end)
 {
     int rc;
@@ -448,7 +565,7 @@ int evolve_fused(gd_ctx *c, long long tick_end)
         for (;;) {
             const double before = c->h_ctrl->interactions;
             CK(cudaEventRecord(c->ev[0], c->stream));
-            if ((rc = launch_fused(c, FUSED_STEPS))) return rc;
+            if ((rc = fused_chunk(c))) return rc;
             CK(cudaEventRecord(c->ev[1], c->stream));
             if ((rc = sync_ctrl(c))) return rc;
             const double done = c->h_ctrl->interactions - before;
@@ -462,12 +579,12 @@ int evolve_fused(gd_ctx *c, long long tick_end)
             if (c->h_ctrl->T_cur > tick_end) break;
         }
     } else {
-        if ((rc = launch_fused(c, FUSED_STEPS))) return rc;
+        if ((rc = fused_chunk(c))) return rc;
         CK(cudaMemcpyAsync(&c->h_snap[0], c->d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
         CK(cudaEventRecord(c->ev_snap[0], c->stream));
         for (long long k = 0;; k++) {
             const int cur = (int)(k & 1), nxt = 1 - cur;
-            if ((rc = launch_fused(c, FUSED_STEPS))) return rc;
+            if ((rc = fused_chunk(c))) return rc;
             CK(cudaMemcpyAsync(&c->h_snap[nxt], c->d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
             CK(cudaEventRecord(c->ev_snap[nxt], c->stream));
             CK(cudaEventSynchronize(c->ev_snap[cur]));
@@ -501,6 +618,7 @@ void gd_opts_default(gd_opts *o)
     o->fused = 0;
     o->pdl = 0;
     o->tail_correct = 0;
+    o->cluster = 1;
 }
 
 }  // extern "C"
@@ -596,6 +714,7 @@ int ctx_init(gd_ctx **out, int64_t n, const double *m, const double *x, const do
     // the select kernel's chunks wait on lower chunks: keep its grid co-resident
     c->grid_sel = std::max(1, std::min(c->nchunks, sms * std::max(1, occ_sel)));
     c->grid_corr = std::max(1, std::min((d.n + 8 * (CT / 32) - 1) / (8 * (CT / 32)), sms * 8));
+    cluster_setup(c);
     // partial capacity: S * nact entries per component (make_plan clamps S to it)
     d.cap = std::max<long long>((long long)d.npad, 4LL * c->grid_force * ITILE_A_MIX) + d.npad;
     const size_t n3 = (size_t)3 * d.n;
@@ -623,7 +742,7 @@ int ctx_init(gd_ctx **out, int64_t n, const double *m, const double *x, const do
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_snap[1], cudaEventDisableTiming);
     if (e != cudaSuccess) return bail(fail(c, GD_ENOMEM, "pinned host allocation failed"));
     if (o.time_force) {
-        c->ev.resize(2 * 64);
+        c->ev.resize(4 * 64);
         for (auto &ev : c->ev) {
             e = cudaEventCreate(&ev);
             if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaEventCreate"));
@@ -715,12 +834,12 @@ int gd_evolve(gd_ctx *c, double t_end)
     auto chunk = [&]() -> int {
         if (c->opt.use_graph) {
             CK(cudaGraphLaunch(c->graph, c->stream));
-            c->launches += 3LL * G;
+            c->launches += (c->cl_C ? 4LL : 3LL) * G;
         } else {
             for (int s = 0; s < G; s++) {
                 cudaEvent_t e0 = c->opt.time_force ? c->ev[2 * s] : nullptr;
                 cudaEvent_t e1 = c->opt.time_force ? c->ev[2 * s + 1] : nullptr;
-                launch_step(c, s, e0, e1, false);
+                launch_cycle(c, s, e0, e1, false);
             }
         }
         CK(cudaGetLastError());
@@ -731,7 +850,7 @@ int gd_evolve(gd_ctx *c, double t_end)
         for (;;) {
             if ((rc = chunk())) return rc;
             if ((rc = sync_ctrl(c))) return rc;
-            if ((rc = harvest_times(c, G))) return rc;
+            if ((rc = harvest_times(c, G, true))) return rc;
             if (c->h_ctrl->T_cur > tick_end) break;
         }
     } else {
@@ -760,7 +879,7 @@ int gd_step_block(gd_ctx *c, double *t_out, int64_t *nact_out)
     launch_step(c, 0, c->opt.time_force ? c->ev[0] : nullptr, c->opt.time_force ? c->ev[1] : nullptr, false);
     CK(cudaGetLastError());
     if ((rc = sync_ctrl(c))) return rc;
-    if ((rc = harvest_times(c, 1))) return rc;
+    if ((rc = harvest_times(c, 1, false))) return rc;
     if (t_out) *t_out = (double)c->h_ctrl->T_last * c->d.dt_min;
     if (nact_out) *nact_out = c->h_ctrl->last_nact;
     return GD_OK;
@@ -884,6 +1003,26 @@ int gd_kernel_time(gd_ctx *c, double *ms_total, int64_t *launches, double *inter
     c->force_ms = 0;
     c->force_launches = 0;
     c->force_interactions = 0;
+    return GD_OK;
+}
+
+int gd_cluster_time(gd_ctx *c, double *ms_total, int64_t *launches)
+{
+    if (!c) return fail(nullptr, GD_EINVAL, "null context");
+    if (!c->opt.time_force) return fail(c, GD_ESTATE, "time_force was not enabled");
+    if (ms_total) *ms_total = c->cl_ms;
+    if (launches) *launches = c->cl_launches;
+    c->cl_ms = 0;
+    c->cl_launches = 0;
+    return GD_OK;
+}
+
+int gd_cluster_info(gd_ctx *c, int32_t *csize, int32_t *per_cta, int32_t *max_nact)
+{
+    if (!c) return fail(nullptr, GD_EINVAL, "null context");
+    if (csize) *csize = c->cl_C;
+    if (per_cta) *per_cta = c->cl_C ? c->cl_P : 0;
+    if (max_nact) *max_nact = c->cl_C ? c->cl_ns : 0;
     return GD_OK;
 }
 

@@ -361,6 +361,12 @@ __device__ __forceinline__ F2 ds_pred_v(F2 v0, float a0, float j0, float dt, flo
     return two_sum(s.h, __fadd_rn(s.l, v0.l));
 }
 
+// The predicted velocity as the j-record's FP32 value: v.h + (v.l + dt a + dt^2/2 jerk).
+__device__ __forceinline__ float ds_pred_v_rec(F2 v0, float a0, float j0, float dt, float h2)
+{
+    return __fadd_rn(v0.h, fmaf(h2, j0, fmaf(dt, a0, v0.l)));
+}
+
 // Predicts particle i to T on the mixed path and stores its j-record.
 template <bool COH>
 __device__ __forceinline__ void predict_store_ds(const Dev &d, int i, long long dtick)
@@ -377,8 +383,7 @@ __device__ __forceinline__ void predict_store_ds(const Dev &d, int i, long long 
         const F2 x0 = ldx_ds<COH>(d.xs, n, c, i), v0 = ldx_ds<COH>(d.vs, n, c, i);
         const float a0 = ldx<COH>(&d.af[c * n + i]), j0 = ldx<COH>(&d.jf[c * n + i]);
         xp[c] = ds_pred_x(x0, v0, a0, j0, dt, h2, h3);
-        const F2 v = ds_pred_v(v0, a0, j0, dt, h2);
-        vp[c] = __fadd_rn(v.h, v.l);
+        vp[c] = ds_pred_v_rec(v0, a0, j0, dt, h2);
     }
     d.jA[i] = make_float4(xp[0].h, xp[1].h, xp[2].h, d.mf[i]);
     d.jB[i] = make_float4(xp[0].l, xp[1].l, xp[2].l, vp[0]);
@@ -827,6 +832,36 @@ __device__ __forceinline__ long long next_block_step_f(const Dev &d, float na1, 
 // correct_slots64 (four lanes per particle): FP32 Hermite derivatives and
 // correction terms (the forces they come from are FP32-accurate), double-single
 // position and velocity sums, canonical results, the step from next_block_step_f.
+// One component of the mixed-path correction (lanes 0-2 of a group of four hold
+// x, y, z; lane 3 repeats z and is ignored): prediction, Hermite derivatives from
+// the end-point forces, corrected x and v (canonical double-single), and the new
+// block step (every lane of the group gets the same).  dtick > 0.
+__device__ __forceinline__ void ds_correct(const Dev &d, bool real, long long dtick, long long dtau_old, long long T,
+                                           F2 x0, F2 v0, float a0, float j0, float a1, float j1, F2 &x1, F2 &v1,
+                                           long long &dtau)
+{
+    float dt, idt;
+    step_f(d, dtick, dt, idt);
+    const float dt2 = __fmul_rn(dt, dt), dt3 = __fmul_rn(dt2, dt), dt4 = __fmul_rn(dt3, dt);
+    const float dt5 = __fmul_rn(dt4, dt);
+    const float idt2 = __fmul_rn(idt, idt), idt3 = __fmul_rn(idt2, idt);
+    const float h2 = __fmul_rn(0.5f, dt2), h3 = __fmul_rn(dt3, 1.0f / 6.0f);
+    const float h4 = __fmul_rn(dt4, 1.0f / 24.0f), h5 = __fmul_rn(dt5, 1.0f / 120.0f);
+    // prediction of this component (Sec. 2.4 step 7a)
+    const F2 xp = ds_pred_x(x0, v0, a0, j0, dt, h2, h3);
+    const F2 vp = ds_pred_v(v0, a0, j0, dt, h2);
+    // 2nd and 3rd derivative at the start of the step from the end-point values
+    const float da = __fadd_rn(a0, -a1);
+    const float a2 = __fmul_rn(fmaf(-6.0f, da, -__fmul_rn(dt, fmaf(4.0f, j0, __fmul_rn(2.0f, j1)))), idt2);
+    const float a3 = __fmul_rn(fmaf(12.0f, da, __fmul_rn(__fmul_rn(6.0f, dt), __fadd_rn(j0, j1))), idt3);
+    x1 = ds_canon(ds_add_f(xp, fmaf(a3, h5, __fmul_rn(a2, h4))));
+    v1 = ds_canon(ds_add_f(vp, fmaf(a3, h4, __fmul_rn(a2, h3))));
+    const float a2e = fmaf(dt, a3, a2);  // 2nd derivative at the end of the step
+    const float na1 = norm3_group(real ? a1 : 0.f), nj1 = norm3_group(real ? j1 : 0.f);
+    const float na2 = norm3_group(real ? a2e : 0.f), na3 = norm3_group(real ? a3 : 0.f);
+    dtau = next_block_step_f(d, na1, nj1, na2, na3, dtau_old, T);
+}
+
 template <bool COH>
 __device__ __forceinline__ void correct_slots_ds(const Dev &d, long long T, int k_lo, int k_hi, int w0, int ws,
                                                  long long &mymin, int &bad)
@@ -846,29 +881,12 @@ __device__ __forceinline__ void correct_slots_ds(const Dev &d, long long T, int 
         const long long dtau_old = ldx<COH>(&d.dtau[i]);
         const long long dtick = T - tau0;
         const bool behind = dtick > 0;
-        float dt, idt;
-        step_f(d, behind ? dtick : 1, dt, idt);
-        const float dt2 = __fmul_rn(dt, dt), dt3 = __fmul_rn(dt2, dt), dt4 = __fmul_rn(dt3, dt);
-        const float dt5 = __fmul_rn(dt4, dt);
-        const float idt2 = __fmul_rn(idt, idt), idt3 = __fmul_rn(idt2, idt);
-        const float h2 = __fmul_rn(0.5f, dt2), h3 = __fmul_rn(dt3, 1.0f / 6.0f);
-        const float h4 = __fmul_rn(dt4, 1.0f / 24.0f), h5 = __fmul_rn(dt5, 1.0f / 120.0f);
         const F2 x0 = ldx_ds<COH>(d.xs, n, c, i), v0 = ldx_ds<COH>(d.vs, n, c, i);
         const float a0 = ldx<COH>(&d.af[c * n + i]), j0 = ldx<COH>(&d.jf[c * n + i]);
         const float a1 = ldc(&fs[c * n + kk]), j1 = ldc(&fs[(3 + c) * n + kk]);
-        // prediction of this component (Sec. 2.4 step 7a)
-        const F2 xp = ds_pred_x(x0, v0, a0, j0, dt, h2, h3);
-        const F2 vp = ds_pred_v(v0, a0, j0, dt, h2);
-        // 2nd and 3rd derivative at the start of the step from the end-point values
-        const float da = __fadd_rn(a0, -a1);
-        const float a2 = __fmul_rn(fmaf(-6.0f, da, -__fmul_rn(dt, fmaf(4.0f, j0, __fmul_rn(2.0f, j1)))), idt2);
-        const float a3 = __fmul_rn(fmaf(12.0f, da, __fmul_rn(__fmul_rn(6.0f, dt), __fadd_rn(j0, j1))), idt3);
-        const F2 x1 = ds_canon(ds_add_f(xp, fmaf(a3, h5, __fmul_rn(a2, h4))));
-        const F2 v1 = ds_canon(ds_add_f(vp, fmaf(a3, h4, __fmul_rn(a2, h3))));
-        const float a2e = fmaf(dt, a3, a2);  // 2nd derivative at the end of the step
-        const float na1 = norm3_group(real ? a1 : 0.f), nj1 = norm3_group(real ? j1 : 0.f);
-        const float na2 = norm3_group(real ? a2e : 0.f), na3 = norm3_group(real ? a3 : 0.f);
-        const long long dtau = next_block_step_f(d, na1, nj1, na2, na3, dtau_old, T);
+        F2 x1, v1;
+        long long dtau;
+        ds_correct(d, real, behind ? dtick : 1, dtau_old, T, x0, v0, a0, j0, a1, j1, x1, v1, dtau);
         const bool fin = isfinite(x1.h) && isfinite(v1.h) && isfinite(a1) && isfinite(j1);
         if (valid) {
             if (!behind) {

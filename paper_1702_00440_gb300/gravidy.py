@@ -27,6 +27,7 @@ EXPORTS = (
     "gd_opts_default", "gd_init", "gd_evolve", "gd_step_block", "gd_energy", "gd_get_state",
     "gd_set_state", "gd_get_stats", "gd_kernel_time", "gd_free", "gd_last_error", "gd_force",
     "gd_predict", "gd_active", "gd_replay_step", "gd_force_noalloc", "gd_autotune", "gd_get_tuning",
+    "gd_cluster_info", "gd_cluster_time",
     "gd_ens_init", "gd_ens_evolve", "gd_ens_step_block", "gd_ens_energy", "gd_ens_get_state",
     "gd_ens_get_stats", "gd_ens_free", "gd_ens_last_error",
 )
@@ -54,6 +55,7 @@ class gd_opts(ctypes.Structure):
         ("fused", ctypes.c_int32),
         ("pdl", ctypes.c_int32),
         ("tail_correct", ctypes.c_int32),
+        ("cluster", ctypes.c_int32),
     ]
 
 
@@ -100,6 +102,8 @@ def load(build_if_missing: bool = True):
             "gd_set_state": (ctypes.c_int, [P, P, P, P, P, P, P]),
             "gd_get_stats": (ctypes.c_int, [P, P]),
             "gd_kernel_time": (ctypes.c_int, [P, P, P, P]),
+            "gd_cluster_info": (ctypes.c_int, [P, P, P, P]),
+            "gd_cluster_time": (ctypes.c_int, [P, P, P]),
             "gd_free": (None, [P]),
             "gd_last_error": (ctypes.c_char_p, [P]),
             "gd_force": (ctypes.c_int, [P, I64, P, I64, P, P]),
@@ -142,7 +146,7 @@ def _check(rc, ctx=None):
 
 def make_opts(dt_min=2.0 ** -22, dt_max=0.125, precision="mixed", device=0, stream=None, use_graph=True,
               graph_steps=16, jsplit=0, mode_cut=0, time_force=False, autotune=False, fused=False, pdl=None,
-              tail_correct=None):
+              tail_correct=None, cluster=None):
     o = gd_opts()
     load().gd_opts_default(ctypes.byref(o))
     o.dt_min = float(dt_min)
@@ -161,6 +165,8 @@ def make_opts(dt_min=2.0 ** -22, dt_max=0.125, precision="mixed", device=0, stre
         o.pdl = 1 if pdl else 0
     if tail_correct is not None:
         o.tail_correct = 1 if tail_correct else 0
+    if cluster is not None:
+        o.cluster = 1 if cluster else 0
     return o
 
 
@@ -232,6 +238,23 @@ def gd_kernel_time(ctx):
     it = ctypes.c_double()
     _check(load().gd_kernel_time(ctx, ctypes.byref(ms), ctypes.byref(k), ctypes.byref(it)), ctx)
     return ms.value, k.value, it.value
+
+
+def gd_cluster_info(ctx):
+    """(CTAs per cluster or 0, particles per CTA, largest cluster step) of gd_evolve."""
+    cs = ctypes.c_int32()
+    pc = ctypes.c_int32()
+    mx = ctypes.c_int32()
+    _check(load().gd_cluster_info(ctx, ctypes.byref(cs), ctypes.byref(pc), ctypes.byref(mx)), ctx)
+    return cs.value, pc.value, mx.value
+
+
+def gd_cluster_time(ctx):
+    """(milliseconds, launches) of the timed small-step cluster launches."""
+    ms = ctypes.c_double()
+    k = ctypes.c_int64()
+    _check(load().gd_cluster_time(ctx, ctypes.byref(ms), ctypes.byref(k)), ctx)
+    return ms.value, k.value
 
 
 def gd_autotune(ctx, reps=3):
@@ -340,6 +363,12 @@ class Integrator:
 
     def autotune(self, reps=3):
         gd_autotune(self._h, reps)
+
+    def cluster_info(self):
+        return gd_cluster_info(self._h)
+
+    def cluster_time(self):
+        return gd_cluster_time(self._h)
 
     def tuning(self):
         return gd_get_tuning(self._h)

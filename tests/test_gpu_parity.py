@@ -331,6 +331,57 @@ def test_graph_eager_and_fused_paths_identical(prec, n):
             assert np.array_equal(out[0][k], other[k]), k
 
 
+@pytest.mark.parametrize("n", [1000, 4097, 20000])
+def test_cluster_small_steps_vs_full_gpu(n):
+    """Small block steps inside one thread-block cluster (the default) against
+    every step on the full GPU: the same scheme and arithmetic, the force sums
+    taken in another order, so the runs agree to round-off growth."""
+    m, x, v = inputs.plummer(n, seed=12)
+    t_end = 0.125
+    res = {}
+    for cl in (True, False):
+        with gravidy.Integrator(m, x, v, EPS, ETA, precision="mixed", cluster=cl) as g:
+            info = g.cluster_info()
+            E0 = sum(g.energy())
+            g.evolve(t_end)
+            E1 = sum(g.energy())
+            res[cl] = (info, g.state(), g.stats(), (E1 - E0) / E0)
+    (info1, st1, s1, de1), (info0, st0, s0, de0) = res[True], res[False]
+    print("n=%d cluster %s: blocks %d/%d psteps %d/%d dE/E %.3e/%.3e"
+          % (n, info1, s1["block_steps"], s0["block_steps"], s1["particle_steps"], s0["particle_steps"], de1, de0))
+    assert info0[0] == 0
+    assert info1[0] in (8, 16) and info1[1] * info1[0] >= n and 16 <= info1[2] <= 128
+    tick = int(t_end / DT_MIN)
+    assert (st1["tau"] == tick).all() and (st0["tau"] == tick).all()
+    assert np.mean(st1["dtau"] == st0["dtau"]) > 0.99
+    assert np.abs(st1["x"] - st0["x"]).max() < 1e-6
+    assert abs(s1["particle_steps"] - s0["particle_steps"]) <= 0.01 * s0["particle_steps"]
+    assert abs(de1) <= 2 * abs(de0) + 1e-9
+
+
+def test_cluster_unsoftened_and_sizes():
+    """eps = 0 (the unsoftened kernel instance) through the cluster path, and
+    the sizes at which the cluster is not used."""
+    m, x, v = inputs.plummer(500, seed=13)
+    out = {}
+    for cl in (True, False):
+        with gravidy.Integrator(m, x, v, 0.0, ETA, precision="mixed", cluster=cl) as g:
+            assert (g.cluster_info()[0] in (8, 16)) == cl
+            E0 = sum(g.energy())
+            g.evolve(0.125)  # dt_max: every particle's step divides it
+            out[cl] = (g.state(), (sum(g.energy()) - E0) / E0)
+    for cl, (st, de) in out.items():
+        assert (st["tau"] == int(0.125 / DT_MIN)).all()
+        assert np.isfinite(st["x"]).all() and np.isfinite(st["v"]).all()
+    assert abs(out[True][1]) <= 2 * abs(out[False][1]) + 1e-9
+    m, x, v = inputs.plummer(30000, seed=13)
+    with gravidy.Integrator(m, x, v, EPS, ETA, precision="mixed") as g:
+        assert g.cluster_info() == (0, 0, 0)
+    m, x, v = inputs.plummer(300, seed=13)
+    with gravidy.Integrator(m, x, v, EPS, ETA, precision="fp64") as g:
+        assert g.cluster_info()[0] == 0
+
+
 def test_step_block_matches_oracle_schedule():
     m, x, v = inputs.plummer(700, seed=9)
     sim = oracle.Sim(m, x, v, EPS, ETA)
@@ -367,15 +418,23 @@ def test_replay_rejects_a_particle_not_behind_the_block_time():
 
 
 @pytest.mark.parametrize("fused", [False, True])
-def test_kernel_timing_hook(fused):
+@pytest.mark.parametrize("cluster", [False, True])
+def test_kernel_timing_hook(fused, cluster):
     m, x, v = inputs.plummer(2000, seed=2)
-    with gravidy.Integrator(m, x, v, EPS, ETA, time_force=True, fused=fused) as g:
+    with gravidy.Integrator(m, x, v, EPS, ETA, time_force=True, fused=fused, cluster=cluster) as g:
         g.evolve(0.125)
         ms, launches, inter = g.kernel_time()
+        cms, claunch = g.cluster_time()
         st = g.stats()
+    total = st["interactions"] - 2000.0 ** 2   # all but the initial evaluation
     if fused:
+        # the fused path times whole launches (cluster cycles included)
         assert 1 <= launches <= st["block_steps"]
+        assert inter == total
+    elif not cluster:
+        assert launches == st["block_steps"] and inter == total and claunch == 0
     else:
-        assert launches == st["block_steps"]
-    assert inter == st["interactions"] - 2000.0 ** 2   # all but the initial evaluation
+        # the full-GPU force launches take the large steps, the cluster the rest
+        assert 1 <= launches < st["block_steps"] and 0 < inter < total
+        assert claunch >= 1 and cms > 0
     assert ms > 0
