@@ -44,9 +44,13 @@ FLOP_PER_INTERACTION = 60
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 L2_FLUSH_BYTES = 512 << 20
-# DRAM traffic of one force launch per ncu capture, keyed by the SHA-256 of the
-# kernel source it was measured on (a changed source reports null).
-FORCE_TRAFFIC_PER_LAUNCH = {}
+# DRAM bytes (read + write) of one launch per kernel, from one ncu --set full
+# capture of the steady-state block steps of this workload (ncu's default cache
+# control: caches flushed before the launch), keyed by the SHA-256 of the kernel
+# sources the capture ran on; a changed source reports null.
+TRAFFIC_PER_LAUNCH = {
+    "1be20146": {"k_cluster_steps": 1564032, "k_force_mixed": 713728},
+}
 
 
 def _args():
@@ -259,11 +263,20 @@ def run_reference(a):
 
 # ------------------------------------------------------------------ main arm
 
-def _traffic():
-    src = os.path.join(ROOT, "paper_1702_00440_gb300", "csrc", "gravidy.cu")
-    with open(src, "rb") as f:
-        h = hashlib.sha256(f.read()).hexdigest()
-    return FORCE_TRAFFIC_PER_LAUNCH.get(h)
+def _csrc_hash():
+    """SHA-256 over the CUDA sources (file names and contents, sorted by name)."""
+    d = os.path.join(ROOT, "paper_1702_00440_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(name.encode())
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()
+
+
+def _traffic(kernel):
+    return TRAFFIC_PER_LAUNCH.get(_csrc_hash()[:8], {}).get(kernel)
 
 
 def run_gravidy(a):
@@ -304,6 +317,9 @@ def run_gravidy(a):
         total_ms = 0.0
         per = []
         E = None
+        # cudaProfilerStart/Stop bracket the timed steps, so that a profiler run with
+        # --profile-from-start off sees exactly them (no effect otherwise)
+        torch.cuda.profiler.start()
         for _ in range(a.steps):
             flush_l2()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -319,6 +335,7 @@ def run_gravidy(a):
             total_ms += ms
             E = Kx + Ux
         torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
         comm.barrier()
         clocks = sampler.stop()
         s1 = g.stats()
@@ -344,6 +361,8 @@ def run_gravidy(a):
                             autotune=not a.no_autotune)
     g2.set_state(state_end["x"], state_end["v"], state_end["a"], state_end["j"], state_end["tau"], state_end["dtau"])
     g2.kernel_time()
+    g2.cluster_time()
+    s2a = g2.stats()
     t2 = t
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -358,19 +377,39 @@ def run_gravidy(a):
         e1.synchronize()
         region_ms += e0.elapsed_time(e1)
     f_ms, f_launches, f_inter = g2.kernel_time()
+    c_ms, c_launches = g2.cluster_time()
+    cl_size, _, cl_ns = g2.cluster_info()
+    s2b = g2.stats()
     g2.close()
-    achieved = FLOP_PER_INTERACTION * f_inter / (f_ms / 1e3) / 1e12
-    traffic = _traffic()
-    roofline = {
-        "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-        "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-        "kernel": "k_force_%s" % ("mixed" if a.precision == "mixed" else "fp64"),
-        "peak_basis": "FP32 non-tensor: 152 SMs x 128 lanes x 2 flop x 2070 MHz (unit counts x max clock)",
-        "flop_per_interaction": FLOP_PER_INTERACTION, "launches": f_launches,
-        "avg_launch_us": 1e3 * f_ms / max(1, f_launches),
-        "interactions_per_launch": f_inter / max(1, f_launches),
-        "share_of_step_time": f_ms / region_ms if region_ms > 0 else None,
-    }
+    # the block steps the cluster took: every interaction of the region outside
+    # the full-GPU force launches
+    c_inter = max(0.0, (s2b["interactions"] - s2a["interactions"]) - f_inter)
+    peak_basis = "FP32 non-tensor: 152 SMs x 128 lanes x 2 flop x 2070 MHz (unit counts x max clock)"
+    kernels = {}
+    fname = "k_force_%s" % ("mixed" if a.precision == "mixed" else "fp64")
+    for name, ms, nl, inter in ((fname, f_ms, f_launches, f_inter),
+                                ("k_cluster_steps", c_ms, c_launches, c_inter)):
+        if nl <= 0 or ms <= 0:
+            continue
+        ach = FLOP_PER_INTERACTION * inter / (ms / 1e3) / 1e12
+        kernels[name] = {
+            "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP32_PEAK_TFLOPS, "traffic": _traffic(name), "kernel": name,
+            "peak_basis": peak_basis, "flop_per_interaction": FLOP_PER_INTERACTION, "launches": nl,
+            "avg_launch_us": 1e3 * ms / nl, "interactions_per_launch": inter / nl,
+            "share_of_step_time": ms / region_ms if region_ms > 0 else None,
+        }
+    if "k_cluster_steps" in kernels:
+        # the cluster runs on cl_size SMs by design (small steps are latency bound)
+        kc = kernels["k_cluster_steps"]
+        kc["cluster_ctas"] = cl_size
+        kc["max_nact_per_step"] = cl_ns
+        kc["frac_of_cluster_sms"] = kc["frac"] * SMS / cl_size
+        kc["block_steps_per_launch"] = (s2b["block_steps"] - s2a["block_steps"] - f_launches) / kc["launches"]
+    # the roofline object is the kernel with the largest share of the step time
+    dominant = max(kernels.values(), key=lambda q: q["share_of_step_time"] or 0.0)
+    roofline = dict(dominant)
+    roofline["other_kernels"] = {k: q for k, q in kernels.items() if k != dominant["kernel"]}
 
     extras = {}
     cpu = None
