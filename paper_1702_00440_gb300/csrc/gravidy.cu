@@ -102,7 +102,14 @@ Tune effective_tune(const gd_ctx *c)
     return t;
 }
 
-FArgs fargs(const gd_ctx *c, int tail_ok) { return FArgs{c->d, c->grid_force, effective_tune(c), tail_ok}; }
+// The block-step kernels leave i-parallel plans' j-split partials to k_correct
+// (FArgs::defer): summing them there uses the whole GPU instead of one CTA per tile.
+constexpr int DEFER_SUMS = 1;
+
+FArgs fargs(const gd_ctx *c, int tail_ok, int defer = 0)
+{
+    return FArgs{c->d, c->grid_force, effective_tune(c), tail_ok, defer};
+}
 
 // Launch with programmatic stream serialisation: the kernel may start while the
 // previous one finishes and waits for it in pdl_wait().
@@ -170,12 +177,12 @@ void launch_select(gd_ctx *c, int slot)
 
 // The force of a block step: warp-mode tiles are corrected in the force kernel's
 // tile tails, which then finalizes the step; k_correct handles i-parallel plans.
-void launch_force_step(gd_ctx *c) { launch_force_with(c, fargs(c, c->opt.tail_correct ? 1 : 0)); }
+void launch_force_step(gd_ctx *c) { launch_force_with(c, fargs(c, c->opt.tail_correct ? 1 : 0, DEFER_SUMS)); }
 
 void launch_correct(gd_ctx *c)
 {
     c->launches += 1;
-    const CArgs a{c->d, c->grid_force, effective_tune(c), c->opt.tail_correct ? 1 : 0, c->mixed ? 1 : 0};
+    const CArgs a{c->d, c->grid_force, effective_tune(c), c->opt.tail_correct ? 1 : 0, c->mixed ? 1 : 0, DEFER_SUMS};
     if (c->mixed)
         launch_pdl(c->opt.pdl != 0, k_correct<true>, c->grid_corr, CT, c->stream, a);
     else
@@ -501,14 +508,28 @@ int autotune(gd_ctx *c, int reps)
                 Tune t = base;
                 t.mode_b[b] = (signed char)mode;
                 t.s_fixed[b] = (short)std::min(S, 32767);
-                const FArgs fa{d, c->grid_force, t, 0};
+                const FArgs fa{d, c->grid_force, t, 0, DEFER_SUMS};
+                // a deferred i-parallel plan is timed with the sums k_correct will take
+                const Plan pl = make_plan(nact, d.npad, c->grid_force, t, c->mixed, d.cap);
+                const bool sums = DEFER_SUMS && pl.mode == 0;
+                auto launch_timed = [&]() {
+                    launch_force_with(c, fa);
+                    if (sums) {
+                        const int g = (3 * nact + 255) / 256;
+                        if (c->mixed)
+                            k_part_sum<float><<<g, 256, 0, c->stream>>>(d, nact, pl.S);
+                        else
+                            k_part_sum<double><<<g, 256, 0, c->stream>>>(d, nact, pl.S);
+                        c->launches += 1;
+                    }
+                };
                 k_set_step<<<1, 1, 0, c->stream>>>(d.ctrl, c->h_ctrl->T_cur, nact);
                 c->launches += 1;
-                launch_force_with(c, fa);  // warm
+                launch_timed();  // warm
                 std::vector<float> ts;
                 for (int r = 0; r < reps; r++) {
                     CK(cudaEventRecord(e0, c->stream));
-                    launch_force_with(c, fa);
+                    launch_timed();
                     CK(cudaEventRecord(e1, c->stream));
                     CK(cudaEventSynchronize(e1));
                     float ms = 0.f;

@@ -678,8 +678,77 @@ struct FArgs {
     Dev d;
     int grid;
     Tune tn;
-    int tail_ok;  // unused by the kernels (TAIL is a template parameter); kept for the plan's callers
+    int tail_ok;  // the host's choice of the TAIL kernel instance (the kernels use the template parameter)
+    int defer;    // 1: i-parallel plans leave their j-split partials to k_correct (see finish_item)
 };
+
+// ---------------------------------------------------------------- canonical sums of j-split partials
+
+template <class P>
+struct Acc;
+template <>
+struct Acc<float> {
+    DS v;
+    __device__ void zero() { v.zero(); }
+    __device__ void add(float f) { v.add(f); }
+    __device__ void add(const Acc &o)
+    {
+        v.add(o.v.h);
+        v.add(o.v.l);
+    }
+    __device__ double value() const { return v.as_double(); }
+    __device__ float result() const { return __fadd_rn(v.h, v.l); }
+};
+template <>
+struct Acc<double> {
+    double v;
+    __device__ void zero() { v = 0.0; }
+    __device__ void add(double f) { v += f; }
+    __device__ void add(const Acc &o) { v += o.v; }
+    __device__ double value() const { return v; }
+    __device__ double result() const { return v; }
+};
+
+// Every (component, slot) sum of the S j-split partials is taken in one canonical
+// order, whatever the tile's occupancy and whichever reduction routine runs: eight
+// interleaved running sums q_r over s = r, r + 8, r + 16, ... (ascending), then
+// ((q0 + q1) + (q2 + q3)) + ((q4 + q5) + (q6 + q7)).  A particle's force therefore
+// does not depend on its slot in the active list, nor on which tile it shares.
+constexpr int RED_R = 8;
+
+template <class P>
+__device__ __forceinline__ P combine8(Acc<P> q[RED_R])
+{
+    q[0].add(q[1]);
+    q[2].add(q[3]);
+    q[4].add(q[5]);
+    q[6].add(q[7]);
+    q[0].add(q[2]);
+    q[4].add(q[6]);
+    q[0].add(q[4]);
+    return q[0].result();
+}
+
+// The canonical sum of the S partials of slot k, component c (partials at
+// part[(s * 6 + c) * nact + k], written by other CTAs: read through L2).
+template <class P>
+__device__ __forceinline__ P part_sum(const Dev &d, int nact, int S, int c, int k)
+{
+    const P *p = (const P *)d.part + (long long)c * nact + k;
+    const long long stride = 6LL * nact;
+    Acc<P> q[RED_R];
+#pragma unroll
+    for (int r = 0; r < RED_R; r++) q[r].zero();
+    for (int s0 = 0; s0 < S; s0 += RED_R) {
+        P v[RED_R];
+#pragma unroll
+        for (int r = 0; r < RED_R; r++) v[r] = s0 + r < S ? __ldcg(p + (long long)(s0 + r) * stride) : P(0);
+#pragma unroll
+        for (int r = 0; r < RED_R; r++)
+            if (s0 + r < S) q[r].add(v[r]);
+    }
+    return combine8<P>(q);
+}
 
 // ---------------------------------------------------------------- corrector + time step
 
@@ -862,9 +931,11 @@ __device__ __forceinline__ void ds_correct(const Dev &d, bool real, long long dt
     dtau = next_block_step_f(d, na1, nj1, na2, na3, dtau_old, T);
 }
 
+// S > 0: the new force of slot k is the canonical sum of its S j-split partials
+// (part_sum, over nact slots); S = 0: it is read from fsum.
 template <bool COH>
 __device__ __forceinline__ void correct_slots_ds(const Dev &d, long long T, int k_lo, int k_hi, int w0, int ws,
-                                                 long long &mymin, int &bad)
+                                                 long long &mymin, int &bad, int S, int nact)
 {
     const int n = d.n;
     const int lane = threadIdx.x & 31;
@@ -883,7 +954,8 @@ __device__ __forceinline__ void correct_slots_ds(const Dev &d, long long T, int 
         const bool behind = dtick > 0;
         const F2 x0 = ldx_ds<COH>(d.xs, n, c, i), v0 = ldx_ds<COH>(d.vs, n, c, i);
         const float a0 = ldx<COH>(&d.af[c * n + i]), j0 = ldx<COH>(&d.jf[c * n + i]);
-        const float a1 = ldc(&fs[c * n + kk]), j1 = ldc(&fs[(3 + c) * n + kk]);
+        const float a1 = S > 0 ? part_sum<float>(d, nact, S, c, kk) : ldc(&fs[c * n + kk]);
+        const float j1 = S > 0 ? part_sum<float>(d, nact, S, 3 + c, kk) : ldc(&fs[(3 + c) * n + kk]);
         F2 x1, v1;
         long long dtau;
         ds_correct(d, real, behind ? dtick : 1, dtau_old, T, x0, v0, a0, j0, a1, j1, x1, v1, dtau);
@@ -920,7 +992,7 @@ __device__ __forceinline__ void correct_slots_ds(const Dev &d, long long T, int 
 // (1 non-finite, 2 a particle not behind T, which is left untouched).
 template <bool COH>
 __device__ __forceinline__ void correct_slots64(const Dev &d, long long T, int k_lo, int k_hi, int w0, int ws,
-                                                long long &mymin, int &bad)
+                                                long long &mymin, int &bad, int S, int nact)
 {
     const int n = d.n;
     const int lane = threadIdx.x & 31;
@@ -949,7 +1021,8 @@ __device__ __forceinline__ void correct_slots64(const Dev &d, long long T, int k
         const double h2 = 0.5 * dt2, h3 = dt3 * (1.0 / 6.0), h4 = dt4 * (1.0 / 24.0), h5 = dt5 * (1.0 / 120.0);
         const double x0 = ldx<COH>(&d.x[c * n + i]), v0 = ldx<COH>(&d.v[c * n + i]),
                      a0 = ldx<COH>(&d.a[c * n + i]), j0 = ldx<COH>(&d.jk[c * n + i]);
-        const double a1 = ldc(&d.fsum[(long long)c * n + kk]), j1 = ldc(&d.fsum[(long long)(3 + c) * n + kk]);
+        const double a1 = S > 0 ? part_sum<double>(d, nact, S, c, kk) : ldc(&d.fsum[(long long)c * n + kk]);
+        const double j1 = S > 0 ? part_sum<double>(d, nact, S, 3 + c, kk) : ldc(&d.fsum[(long long)(3 + c) * n + kk]);
         // prediction of this component (Sec. 2.4 step 7a)
         const double xp = fma(j0, h3, fma(a0, h2, fma(v0, dt, x0)));
         const double vp = fma(j0, h2, fma(a0, dt, v0));
@@ -1003,12 +1076,12 @@ __device__ __forceinline__ void correct_slots64(const Dev &d, long long T, int k
 
 template <bool MIXED, bool COH>
 __device__ __forceinline__ void correct_slots(const Dev &d, long long T, int k_lo, int k_hi, int w0, int ws,
-                                              long long &mymin, int &bad)
+                                              long long &mymin, int &bad, int S = 0, int nact = 0)
 {
     if (MIXED)
-        correct_slots_ds<COH>(d, T, k_lo, k_hi, w0, ws, mymin, bad);
+        correct_slots_ds<COH>(d, T, k_lo, k_hi, w0, ws, mymin, bad, S, nact);
     else
-        correct_slots64<COH>(d, T, k_lo, k_hi, w0, ws, mymin, bad);
+        correct_slots64<COH>(d, T, k_lo, k_hi, w0, ws, mymin, bad, S, nact);
 }
 
 // ---------------------------------------------------------------- j-split reduction
@@ -1019,51 +1092,6 @@ __device__ __forceinline__ void store_partial(const Dev &d, int nact, int s, int
     P *p = (P *)d.part + (long long)s * 6 * nact + k;
 #pragma unroll
     for (int c = 0; c < 6; c++) p[(long long)c * nact] = f[c];
-}
-
-template <class P>
-struct Acc;
-template <>
-struct Acc<float> {
-    DS v;
-    __device__ void zero() { v.zero(); }
-    __device__ void add(float f) { v.add(f); }
-    __device__ void add(const Acc &o)
-    {
-        v.add(o.v.h);
-        v.add(o.v.l);
-    }
-    __device__ double value() const { return v.as_double(); }
-    __device__ float result() const { return __fadd_rn(v.h, v.l); }
-};
-template <>
-struct Acc<double> {
-    double v;
-    __device__ void zero() { v = 0.0; }
-    __device__ void add(double f) { v += f; }
-    __device__ void add(const Acc &o) { v += o.v; }
-    __device__ double value() const { return v; }
-    __device__ double result() const { return v; }
-};
-
-// Every (component, slot) sum of the S j-split partials is taken in one canonical
-// order, whatever the tile's occupancy and whichever reduction routine runs: eight
-// interleaved running sums q_r over s = r, r + 8, r + 16, ... (ascending), then
-// ((q0 + q1) + (q2 + q3)) + ((q4 + q5) + (q6 + q7)).  A particle's force therefore
-// does not depend on its slot in the active list, nor on which tile it shares.
-constexpr int RED_R = 8;
-
-template <class P>
-__device__ __forceinline__ P combine8(Acc<P> q[RED_R])
-{
-    q[0].add(q[1]);
-    q[2].add(q[3]);
-    q[4].add(q[5]);
-    q[6].add(q[7]);
-    q[0].add(q[2]);
-    q[4].add(q[6]);
-    q[0].add(q[4]);
-    return q[0].result();
 }
 
 // The summed force of slot k, component c: FP64 on the FP64 path, FP32 on the
@@ -1081,24 +1109,10 @@ __device__ __forceinline__ void store_fsum(const Dev &d, int c, int k, P v)
 template <class P>
 __device__ void tile_reduce(const Dev &d, int nact, int S, int k0, int nvalid)
 {
-    const P *part = (const P *)d.part;
     const int npairs = nvalid * 6;
     for (int pidx = threadIdx.x; pidx < npairs; pidx += FT) {
         const int c = pidx / nvalid, k = k0 + pidx % nvalid;
-        const P *p = part + (long long)c * nact + k;
-        const long long stride = 6LL * nact;
-        Acc<P> q[RED_R];
-#pragma unroll
-        for (int r = 0; r < RED_R; r++) q[r].zero();
-        for (int s0 = 0; s0 < S; s0 += RED_R) {
-            P v[RED_R];
-#pragma unroll
-            for (int r = 0; r < RED_R; r++) v[r] = s0 + r < S ? __ldcg(p + (long long)(s0 + r) * stride) : P(0);
-#pragma unroll
-            for (int r = 0; r < RED_R; r++)
-                if (s0 + r < S) q[r].add(v[r]);
-        }
-        store_fsum<P>(d, c, k, combine8<P>(q));
+        store_fsum<P>(d, c, k, part_sum<P>(d, nact, S, c, k));
     }
 }
 
@@ -1139,14 +1153,20 @@ __device__ void tile_reduce_small(const Dev &d, int nact, int S, int k0, int nva
 // that tile sums them (the counter returns to zero for the next launch) and, with
 // `tail`, corrects the tile's particles right away, adding their new next times
 // to *Tacc.
+//
+// With `defer` an i-parallel plan (mode 0) stops after the partial stores: its
+// tiles hold up to ITILE_A_MIX slots and S partials each, which one CTA would sum
+// as a long chain of L2 round trips, while k_correct sums them spread over the GPU
+// (part_sum, the same canonical order).
 template <class P, bool COH>
 __device__ __forceinline__ void finish_item(const Dev &d, int nact, const Plan &pl, int it, bool tail, long long T,
-                                            unsigned long long *Tacc)
+                                            unsigned long long *Tacc, bool defer = false)
 {
     __shared__ int s_last;
     // the barrier gathers this CTA's partial stores; thread 0's fence releases them
     // before the arrival is counted
     __syncthreads();
+    if (defer && pl.mode == 0) return;
     if (threadIdx.x == 0) {
         __threadfence();
         const unsigned prev = atomicAdd(&d.tilecnt[it], 1u);
@@ -1183,7 +1203,7 @@ constexpr int BJB = 256;  // warp mode j-tile (2 records per thread)
 
 template <bool SOFT, bool COH>
 __device__ void phase_force_mixed(const Dev &d, int nact, const Plan &pl, bool tail, long long T,
-                                  unsigned long long *Tacc)
+                                  unsigned long long *Tacc, bool defer = false)
 {
     const float eps2 = d.eps2f;
     __shared__ float4 sA[BJB], sB[BJB];
@@ -1325,7 +1345,7 @@ __device__ void phase_force_mixed(const Dev &d, int nact, const Plan &pl, bool t
                 }
             }
         }
-        finish_item<float, COH>(d, nact, pl, it, tail, T, Tacc);
+        finish_item<float, COH>(d, nact, pl, it, tail, T, Tacc, defer);
     }
 }
 
@@ -1370,10 +1390,10 @@ __global__ void __launch_bounds__(FT, 4) k_force_mixed(FArgs fa)
     const Plan pl = make_plan(nact, d.npad, fa.grid, fa.tn, true, d.cap);
     if (TAIL && pl.mode == 1) {
         const long long T = d.ctrl->T_cur;
-        phase_force_mixed<SOFT, false>(d, nact, pl, true, T, (unsigned long long *)&d.ctrl->T_acc);
+        phase_force_mixed<SOFT, false>(d, nact, pl, true, T, (unsigned long long *)&d.ctrl->T_acc, fa.defer != 0);
         finalize_step(d, nact, T, pl.items);
     } else {
-        phase_force_mixed<SOFT, false>(d, nact, pl, false, 0, nullptr);
+        phase_force_mixed<SOFT, false>(d, nact, pl, false, 0, nullptr, fa.defer != 0);
     }
 }
 
@@ -1439,7 +1459,7 @@ __global__ void __launch_bounds__(FT, 4) k_force_fp64(FArgs fa)
                 if (lane == 0) store_partial<double>(d, nact, s, k, g);
             }
         }
-        finish_item<double, false>(d, nact, pl, it, tail, T, (unsigned long long *)&d.ctrl->T_acc);
+        finish_item<double, false>(d, nact, pl, it, tail, T, (unsigned long long *)&d.ctrl->T_acc, fa.defer != 0);
     }
     if (tail) finalize_step(d, nact, T, pl.items);
 }
@@ -1450,6 +1470,7 @@ struct CArgs {
     Tune tn;       // force kernel has already corrected and finalized the step
     int tail_ok;
     int mixed;
+    int defer;     // the force kernel ran with FArgs::defer: i-parallel plans are summed here
 };
 
 // Corrects every active particle and (last CTA) turns the running minimum into the
@@ -1463,7 +1484,9 @@ __global__ void __launch_bounds__(CT) k_correct(CArgs ca)
     Ctrl *ctrl = d.ctrl;
     const int nact = min(ctrl->nact, d.n);
     if (nact <= 0) return;
-    if (ca.tail_ok && make_plan(nact, d.npad, ca.grid, ca.tn, ca.mixed != 0, d.cap).mode == 1) return;
+    const Plan pl = make_plan(nact, d.npad, ca.grid, ca.tn, ca.mixed != 0, d.cap);
+    if (ca.tail_ok && pl.mode == 1) return;
+    const int S = ca.defer && pl.mode == 0 ? pl.S : 0;
     // only the CTAs that have particles to correct take part (eight per warp); the
     // others leave at once, so a small active set costs a few CTAs, not the grid
     constexpr int PER_CTA = (CT / 32) * 8;
@@ -1476,7 +1499,7 @@ __global__ void __launch_bounds__(CT) k_correct(CArgs ca)
     const int nwarps = (ncta * CT) >> 5;
     long long mymin = LLONG_MAX;
     int bad = 0;
-    correct_slots<MIXED, false>(d, T, 0, nact, gwarp, nwarps, mymin, bad);
+    correct_slots<MIXED, false>(d, T, 0, nact, gwarp, nwarps, mymin, bad, S, nact);
     if (bad & 2) set_err(ctrl, ST_EINVAL);
     if (bad & 1) set_err(ctrl, ST_ENONFINITE);
     mymin = warp_min_ll(mymin);
@@ -1500,6 +1523,20 @@ __global__ void __launch_bounds__(CT) k_correct(CArgs ca)
             ctrl->done = 0;
         }
     }
+}
+
+// The sums k_correct takes for a deferred i-parallel plan (slot k, components c and
+// 3 + c per thread), stored to fsum: the autotuner times a deferred plan's force
+// launch together with this kernel, so both work decompositions are compared with
+// their reductions.
+template <class P>
+__global__ void k_part_sum(Dev d, int nact, int S)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= 3 * nact) return;
+    const int c = w / nact, k = w % nact;
+    store_fsum<P>(d, c, k, part_sum<P>(d, nact, S, c, k));
+    store_fsum<P>(d, 3 + c, k, part_sum<P>(d, nact, S, 3 + c, k));
 }
 
 // Initial steps after the first full force evaluation (Sec. 2.4 steps 3-4 and the
