@@ -68,12 +68,14 @@ def _args():
     p.add_argument("--profile-force", type=int, default=0, metavar="N",
                    help="profiling hook: initialise an N-particle Plummer sphere (one full force evaluation), "
                         "evaluate all N once more, print nothing and exit")
-    p.add_argument("--sweep", choices=["force", "powerlaw", "accuracy", "ensemble"],
+    p.add_argument("--sweep", choices=["force", "powerlaw", "accuracy", "ensemble", "eta"],
                    help="extra measurements, one JSON line each (not the benchmark line): force = "
                         "full evaluations N=2^10..2^20 and N=2^20 with active sets 1..2^20; powerlaw = "
                         "N=262144 power-law masses to t=1/8 (active-set histogram, interactions/s per "
                         "set size); accuracy = N=16384 FP64 vs mixed to t=1; ensemble = 256 clusters of "
-                        "log-uniform N in [256, 8192] to t=--ens-t, one ensemble vs the clusters one by one")
+                        "log-uniform N in [256, 8192] to t=--ens-t, one ensemble vs the clusters one by one; eta = "
+                        "Plummer N=1024..16384 to t=2 for eta=0.001..0.1: s per N-body unit and |dE/E| (mixed, FP64 "
+                        "at eta=0.01, the oracle at N=1024) and the block-step distribution")
     p.add_argument("--ens-t", type=float, default=0.125)
     p.add_argument("--profile-nact", type=int, default=0, metavar="K",
                    help="profiling hook: autotune on the --n workload, then evaluate the force of K random "
@@ -680,6 +682,55 @@ def sweep_ensemble(a):
     return 0
 
 
+def sweep_eta(a):
+    """Accuracy and cost against Aarseth's eta (the paper's eta sweep, Sec. 3.2):
+    Plummer N = 1024, 4096, 16384 (seed 1, eps = 1e-4) integrated to t = 2 for
+    eta = 0.001 .. 0.1 in mixed precision; at eta = 0.01 also the FP64 form and the
+    distribution of block steps at t = 2 (the paper's step histogram); at N = 1024
+    the oracle's |dE/E| for eta = 0.01 and 0.1."""
+    import torch
+
+    import oracle
+    from paper_1702_00440_gb300 import gravidy, inputs
+
+    t_end = 2.0
+    rows = []
+    for n in (1024, 4096, 16384):
+        m, x, v = inputs.plummer(n, seed=1)
+        for eta in (0.001, 0.003, 0.01, 0.03, 0.1):
+            for prec in (("mixed", "fp64") if eta == 0.01 else ("mixed",)):
+                g = gravidy.Integrator(m, x, v, EPS, eta, precision=prec, autotune=True)
+                K0, U0 = g.energy()
+                s0 = g.stats()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                g.evolve(t_end)
+                wall = time.perf_counter() - t0
+                K1, U1 = g.energy()
+                s1 = g.stats()
+                row = {"n": n, "eta": eta, "precision": prec, "s_per_nbu": wall / t_end,
+                       "dE_E": abs((K1 + U1 - K0 - U0) / (K0 + U0)),
+                       "block_steps": s1["block_steps"] - s0["block_steps"],
+                       "particle_steps": s1["particle_steps"] - s0["particle_steps"]}
+                if eta == 0.01 and prec == "mixed":
+                    lg = np.log2(g.state()["dtau"] * 2.0 ** -22).astype(int)
+                    row["log2_dt_histogram"] = {int(b): int((lg == b).sum()) for b in np.unique(lg)}
+                g.close()
+                rows.append(row)
+    oracle.build()
+    m, x, v = inputs.plummer(1024, seed=1)
+    orc = []
+    for eta in (0.01, 0.1):
+        sim = oracle.Sim(m, x, v, EPS, eta)
+        E0 = sum(sim.energy())
+        t0 = time.perf_counter()
+        sim.evolve(t_end)
+        orc.append({"n": 1024, "eta": eta, "dE_E": abs((sum(sim.energy()) - E0) / E0),
+                    "wall_s": time.perf_counter() - t0, "block_steps": sim.stats()["nblock"]})
+    print(json.dumps({"sweep": "eta", "t_end": t_end, "eps": EPS, "rows": rows, "oracle": orc}))
+    return 0
+
+
 def profile_force(a):
     from paper_1702_00440_gb300 import gravidy, inputs
 
@@ -738,7 +789,7 @@ def main():
         return profile_steps(a)
     if a.sweep:
         return {"force": sweep_force, "powerlaw": sweep_powerlaw, "accuracy": sweep_accuracy,
-                "ensemble": sweep_ensemble}[a.sweep](a)
+                "ensemble": sweep_ensemble, "eta": sweep_eta}[a.sweep](a)
     if a.impl == "reference":
         return run_reference(a)
     return run_gravidy(a)

@@ -151,8 +151,27 @@ void launch_force_with(gd_ctx *c, const FArgs &fa)
     }
 }
 
-// force only (no correction): hooks, initial forces, autotuner
-void launch_force(gd_ctx *c) { launch_force_with(c, fargs(c, 0)); }
+// Sums a deferred i-parallel plan's j-split partials into fsum (what k_correct
+// does inside a block step), so the hooks and the initial forces see summed forces.
+void launch_part_sum(gd_ctx *c, int nact, const Tune &tn)
+{
+    const Plan pl = make_plan(nact, c->d.npad, c->grid_force, tn, c->mixed, c->d.cap);
+    if (!DEFER_SUMS || pl.mode != 0) return;
+    const int g = (3 * nact + 255) / 256;
+    if (c->mixed)
+        k_part_sum<float><<<g, 256, 0, c->stream>>>(c->d, nact, pl.S);
+    else
+        k_part_sum<double><<<g, 256, 0, c->stream>>>(c->d, nact, pl.S);
+    c->launches += 1;
+}
+
+// force only (no correction) of nact active slots, summed into fsum: hooks and
+// initial forces, with the same work decomposition as the block steps
+void launch_force(gd_ctx *c, int nact)
+{
+    launch_force_with(c, fargs(c, 0, DEFER_SUMS));
+    launch_part_sum(c, nact, effective_tune(c));
+}
 
 void launch_predict_all(gd_ctx *c, long long tick, bool mixed_records)
 {
@@ -407,7 +426,7 @@ int first_forces(gd_ctx *c)
     launch_predict_all(c, 0, c->mixed);
     k_iota<<<(n + 255) / 256, 256, 0, c->stream>>>(d.act, n);
     k_set_step<<<1, 1, 0, c->stream>>>(d.ctrl, 0, n);
-    launch_force(c);
+    launch_force(c, n);
     if (c->mixed)
         k_init_steps<true><<<(n + 255) / 256, 256, 0, c->stream>>>(d);
     else
@@ -510,18 +529,9 @@ int autotune(gd_ctx *c, int reps)
                 t.s_fixed[b] = (short)std::min(S, 32767);
                 const FArgs fa{d, c->grid_force, t, 0, DEFER_SUMS};
                 // a deferred i-parallel plan is timed with the sums k_correct will take
-                const Plan pl = make_plan(nact, d.npad, c->grid_force, t, c->mixed, d.cap);
-                const bool sums = DEFER_SUMS && pl.mode == 0;
                 auto launch_timed = [&]() {
                     launch_force_with(c, fa);
-                    if (sums) {
-                        const int g = (3 * nact + 255) / 256;
-                        if (c->mixed)
-                            k_part_sum<float><<<g, 256, 0, c->stream>>>(d, nact, pl.S);
-                        else
-                            k_part_sum<double><<<g, 256, 0, c->stream>>>(d, nact, pl.S);
-                        c->launches += 1;
-                    }
+                    launch_part_sum(c, nact, t);
                 };
                 k_set_step<<<1, 1, 0, c->stream>>>(d.ctrl, c->h_ctrl->T_cur, nact);
                 c->launches += 1;
@@ -1080,7 +1090,7 @@ int gd_force(gd_ctx *c, int64_t tick, const int32_t *idx, int64_t nact, double *
     k_set_step<<<1, 1, 0, c->stream>>>(d.ctrl, Tsave, (int)nact);
     c->launches += 1;
     if (c->opt.time_force) CK(cudaEventRecord(c->ev[0], c->stream));
-    launch_force(c);
+    launch_force(c, (int)nact);
     if (c->opt.time_force) CK(cudaEventRecord(c->ev[1], c->stream));
     CK(cudaGetLastError());
     // fsum planes (stride n) -> staging, first nact rows (the mixed path's FP32
