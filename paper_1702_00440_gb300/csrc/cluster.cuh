@@ -21,7 +21,13 @@
 //      write their corrected particles through to global memory.
 // The loop stops, with the same decision in every CTA, when a step has more than
 // `ns` active particles (then the full-GPU kernels take that step), when the block
-// time passes tick_end, after max_steps steps, or on a fault.  All cluster
+// time passes tick_end, after max_steps steps, or on a fault.  With `handoff` the
+// step the cluster leaves to the full GPU is handed over already selected: every
+// CTA writes its predicted j-records and its active particles' places in the
+// (ascending) active list to global memory and starts the running minimum of the
+// next block time with its inactive particles, i.e. the work of k_select_predict,
+// so that the force kernel runs next; a launch that ends at tick_end hands over an
+// empty step.  All cluster
 // barriers are unconditional in the loop body, so every CTA passes the same
 // sequence of them; a last barrier keeps every CTA's shared memory alive until no
 // CTA can still read it.
@@ -83,6 +89,8 @@ struct ClArgs {
     int P;          // particles per CTA
     int ns;         // largest active count taken here (<= CL_NS)
     int max_steps;  // block steps per launch
+    int handoff;    // 1: hand the next step over selected (see above); 0: leave it to k_select_predict
+    int slot;       // handoff: >= 0 records the handed-over N_act in nact_hist[slot]
 };
 
 // Mailbox a CTA posts for the others (read through distributed shared memory).
@@ -148,12 +156,13 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
     long long T_last = 0, psteps = 0;
     int last_n = 0, steps = 0;
     unsigned long long ph[3] = {0ull, 0ull, 0ull};  // CTA 0's clock: predict, force, correct
+    bool handed = false;  // the next step was handed over selected
     const float eps2 = d.eps2f;
     __syncthreads();
 
     for (;;) {
         // the exit tests read values every CTA holds identically
-        if (T > tick_end || steps >= a.max_steps) break;
+        if (T > tick_end || (!a.handoff && steps >= a.max_steps)) break;
 
         // ---- 1. predict own particles, list own active ones (ascending local index)
         const unsigned long long t0 = global_ns();
@@ -252,7 +261,29 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
         const int nact = s_off[C];
         const unsigned long long t1 = global_ns();
         ph[0] += t1 - t0;
-        if (nact > a.ns) break;  // a large step: the full-GPU kernels take it
+        if (nact > a.ns || (a.handoff && steps >= a.max_steps)) {
+            // a large step (or the last of this launch): the full-GPU kernels take it
+            if (a.handoff) {
+                for (int p = t; p < Pr; p += CL_T) {
+                    d.jA[p0 + p] = jA[p];
+                    d.jB[p0 + p] = jB[p];
+                    d.jC[p0 + p] = jC[p];
+                }
+#pragma unroll
+                for (int rd = 0; rd < CL_ROUNDS; rd++)
+                    if ((bal[rd] >> lane) & 1u)
+                        d.act[s_off[r] + s_wc[rd * CL_W + warp] + __popc(bal[rd] & ((1u << lane) - 1u))] =
+                            p0 + rd * CL_T + t;
+                const long long m = warp_min_ll(mn);  // the inactive particles' next times
+                if (lane == 0 && m != LLONG_MAX) atomicMin((unsigned long long *)&ctrl->T_acc, (unsigned long long)m);
+                if (r == 0 && t == 0) {
+                    ctrl->nact = nact;
+                    if (a.slot >= 0) d.nact_hist[a.slot] = nact;
+                }
+                handed = true;
+            }
+            break;
+        }
         // gather the active particles' j-records (i-records of this step)
         for (int k = t; k < nact; k += CL_T) {
             const int q = aown[k], kl = aloc[k];
@@ -438,6 +469,10 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
     cl.sync();  // no CTA leaves while another may still read its shared memory
     if (r == 0 && t == 0) {
         ctrl->T_cur = T;
+        if (a.handoff && !handed) {  // tick_end passed, or a fault: nothing to hand over
+            ctrl->nact = 0;
+            if (a.slot >= 0) d.nact_hist[a.slot] = 0;
+        }
         ctrl->ph_ns[0] += ph[0];
         ctrl->ph_ns[1] += ph[1];
         ctrl->ph_ns[2] += ph[2];

@@ -223,7 +223,7 @@ void launch_step(gd_ctx *c, int slot, cudaEvent_t e0, cudaEvent_t e1, bool captu
 constexpr int CL_STEPS = 4096;
 constexpr int CL_EV = 2 * 64;  // first timing event of the cluster launches (after the force pairs)
 
-void launch_cluster(gd_ctx *c)
+void launch_cluster(gd_ctx *c, int handoff, int slot)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(c->cl_C);
@@ -237,7 +237,7 @@ void launch_cluster(gd_ctx *c)
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    const ClArgs a{c->d, c->cl_P, c->cl_ns, CL_STEPS};
+    const ClArgs a{c->d, c->cl_P, c->cl_ns, CL_STEPS, handoff, slot};
     c->launches += 1;
     if (c->soft)
         cudaLaunchKernelEx(&cfg, k_cluster_steps<true>, a);
@@ -246,14 +246,20 @@ void launch_cluster(gd_ctx *c)
 }
 
 // One cycle of gd_evolve: small steps in the cluster (when enabled) until a large
-// one, which the three step kernels then take.
+// one, which the cluster hands over selected and the force and correction kernels
+// then take; without the cluster, one three-kernel block step.
 void launch_cycle(gd_ctx *c, int slot, cudaEvent_t e0, cudaEvent_t e1, bool capturing)
 {
     if (c->cl_C) {
         const unsigned fl = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
         if (c->opt.time_force) cudaEventRecordWithFlags(c->ev[CL_EV + 2 * slot], c->stream, fl);
-        launch_cluster(c);
+        launch_cluster(c, 1, slot);
         if (c->opt.time_force) cudaEventRecordWithFlags(c->ev[CL_EV + 2 * slot + 1], c->stream, fl);
+        if (e0) cudaEventRecordWithFlags(e0, c->stream, fl);
+        launch_force_step(c);
+        if (e1) cudaEventRecordWithFlags(e1, c->stream, fl);
+        launch_correct(c);
+        return;
     }
     launch_step(c, slot, e0, e1, capturing);
 }
@@ -580,7 +586,7 @@ int fused_chunk(gd_ctx *c)
 {
     if (!c->cl_C) return launch_fused(c, FUSED_STEPS);
     for (int s = 0; s < c->graph_steps; s++) {
-        launch_cluster(c);
+        launch_cluster(c, 0, -1);
         int rc = launch_fused(c, 1);
         if (rc) return rc;
     }
@@ -865,7 +871,7 @@ int gd_evolve(gd_ctx *c, double t_end)
     auto chunk = [&]() -> int {
         if (c->opt.use_graph) {
             CK(cudaGraphLaunch(c->graph, c->stream));
-            c->launches += (c->cl_C ? 4LL : 3LL) * G;
+            c->launches += 3LL * G;  // (cluster or select) + force + correct per cycle
         } else {
             for (int s = 0; s < G; s++) {
                 cudaEvent_t e0 = c->opt.time_force ? c->ev[2 * s] : nullptr;
