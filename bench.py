@@ -68,14 +68,15 @@ def _args():
     p.add_argument("--profile-force", type=int, default=0, metavar="N",
                    help="profiling hook: initialise an N-particle Plummer sphere (one full force evaluation), "
                         "evaluate all N once more, print nothing and exit")
-    p.add_argument("--sweep", choices=["force", "powerlaw", "accuracy", "ensemble", "eta"],
+    p.add_argument("--sweep", choices=["force", "powerlaw", "accuracy", "ensemble", "eta", "soft", "lagrange"],
                    help="extra measurements, one JSON line each (not the benchmark line): force = "
                         "full evaluations N=2^10..2^20 and N=2^20 with active sets 1..2^20; powerlaw = "
                         "N=262144 power-law masses to t=1/8 (active-set histogram, interactions/s per "
                         "set size); accuracy = N=16384 FP64 vs mixed to t=1; ensemble = 256 clusters of "
                         "log-uniform N in [256, 8192] to t=--ens-t, one ensemble vs the clusters one by one; eta = "
                         "Plummer N=1024..16384 to t=2 for eta=0.001..0.1: s per N-body unit and |dE/E| (mixed, FP64 "
-                        "at eta=0.01, the oracle at N=1024) and the block-step distribution")
+                        "at eta=0.01, the oracle at N=1024) and the block-step distribution; soft = the same for "
+                        "eps=1e-5..1e-2 at eta=0.01; lagrange = Lagrange radii of N=16384 every 1/2 unit to t=8")
     p.add_argument("--ens-t", type=float, default=0.125)
     p.add_argument("--profile-nact", type=int, default=0, metavar="K",
                    help="profiling hook: autotune on the --n workload, then evaluate the force of K random "
@@ -731,6 +732,78 @@ def sweep_eta(a):
     return 0
 
 
+def sweep_soft(a):
+    """Accuracy and cost against the Plummer softening (the paper's softening sweep,
+    Sec. 4.1): N = 1024, 4096, 16384 (seed 1) to t = 2 at eta = 0.01 for eps = 1e-5,
+    1e-4, 1e-3, 1e-2, mixed precision; the oracle at N = 1024."""
+    import torch
+
+    import oracle
+    from paper_1702_00440_gb300 import gravidy, inputs
+
+    t_end = 2.0
+    rows = []
+    for n in (1024, 4096, 16384):
+        m, x, v = inputs.plummer(n, seed=1)
+        for eps in (1e-5, 1e-4, 1e-3, 1e-2):
+            g = gravidy.Integrator(m, x, v, eps, ETA, precision="mixed", autotune=True)
+            K0, U0 = g.energy()
+            s0 = g.stats()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g.evolve(t_end)
+            wall = time.perf_counter() - t0
+            K1, U1 = g.energy()
+            s1 = g.stats()
+            g.close()
+            rows.append({"n": n, "eps": eps, "s_per_nbu": wall / t_end, "dE_E": abs((K1 + U1 - K0 - U0) / (K0 + U0)),
+                         "block_steps": s1["block_steps"] - s0["block_steps"],
+                         "particle_steps": s1["particle_steps"] - s0["particle_steps"]})
+    oracle.build()
+    m, x, v = inputs.plummer(1024, seed=1)
+    orc = []
+    for eps in (1e-5, 1e-2):
+        sim = oracle.Sim(m, x, v, eps, ETA)
+        E0 = sum(sim.energy())
+        t0 = time.perf_counter()
+        sim.evolve(t_end)
+        orc.append({"n": 1024, "eps": eps, "dE_E": abs((sum(sim.energy()) - E0) / E0),
+                    "wall_s": time.perf_counter() - t0, "block_steps": sim.stats()["nblock"]})
+    print(json.dumps({"sweep": "soft", "t_end": t_end, "eta": ETA, "rows": rows, "oracle": orc}))
+    return 0
+
+
+def sweep_lagrange(a):
+    """Lagrange radii (radii enclosing 1, 5, 10, 25, 50, 75, 90 % of the mass about
+    the centre of mass) of the N = 16384 benchmark sphere every 1/2 N-body unit to
+    t = 8, with |dE/E| (the paper's Lagrange-radius diagnostic, Sec. 4.2, over a
+    short stretch)."""
+    from paper_1702_00440_gb300 import gravidy, inputs
+
+    n = 16384
+    m, x, v = inputs.plummer(n, seed=1)
+    fr = np.array([0.01, 0.05, 0.1, 0.25, 0.5, 0.75, 0.9])
+
+    def radii(xx):
+        c = (m[:, None] * xx).sum(0) / m.sum()
+        r = np.linalg.norm(xx - c, axis=1)
+        o = np.argsort(r)
+        cm = np.cumsum(m[o]) / m.sum()
+        return [float(r[o][np.searchsorted(cm, f)]) for f in fr]
+
+    g = gravidy.Integrator(m, x, v, EPS, ETA, precision="mixed", autotune=True)
+    E0 = sum(g.energy())
+    rows = [{"t": 0.0, "radii": radii(x), "dE_E": 0.0}]
+    t0 = time.perf_counter()
+    for k in range(1, 17):
+        g.evolve(0.5 * k)
+        rows.append({"t": 0.5 * k, "radii": radii(g.state()["x"]), "dE_E": abs((sum(g.energy()) - E0) / E0)})
+    wall = time.perf_counter() - t0
+    g.close()
+    print(json.dumps({"sweep": "lagrange", "n": n, "fractions": fr.tolist(), "rows": rows, "wall_s": wall}))
+    return 0
+
+
 def profile_force(a):
     from paper_1702_00440_gb300 import gravidy, inputs
 
@@ -789,7 +862,8 @@ def main():
         return profile_steps(a)
     if a.sweep:
         return {"force": sweep_force, "powerlaw": sweep_powerlaw, "accuracy": sweep_accuracy,
-                "ensemble": sweep_ensemble, "eta": sweep_eta}[a.sweep](a)
+                "ensemble": sweep_ensemble, "eta": sweep_eta, "soft": sweep_soft,
+                "lagrange": sweep_lagrange}[a.sweep](a)
     if a.impl == "reference":
         return run_reference(a)
     return run_gravidy(a)
