@@ -311,6 +311,30 @@ def test_free_running_energy_within_2x_of_oracle(prec):
     assert 0.8 < stats["block_steps"] / so["nblock"] < 1.25
 
 
+def test_fp64_free_run_follows_the_oracle_schedule_n1024_to_t2():
+    """The FP64 GPU path free-running from the benchmark's N = 1024 sphere to
+    t = 2 (eta = 0.01) takes the oracle's block schedule: the same block and
+    particle step counts (a quantisation decision could flip only for a step
+    estimate within rounding of a power of two; allowed: 0.2 %) and the same
+    energy error to within 5 %."""
+    m, x, v = inputs.plummer(1024, seed=1)
+    sim = oracle.Sim(m, x, v, EPS, ETA)
+    E0 = sum(sim.energy())
+    sim.evolve(2.0)
+    de_or = abs((sum(sim.energy()) - E0) / E0)
+    so = sim.stats()
+    with gravidy.Integrator(m, x, v, EPS, ETA, precision="fp64") as g:
+        G0 = sum(g.energy())
+        g.evolve(2.0)
+        de = abs((sum(g.energy()) - G0) / G0)
+        st = g.stats()
+    print("fp64 n=1024 t=2: blocks %d/%d psteps %d/%d |dE/E| %.4e/%.4e"
+          % (st["block_steps"], so["nblock"], st["particle_steps"], so["nsteps"], de, de_or))
+    assert abs(st["block_steps"] - so["nblock"]) <= 0.002 * so["nblock"]
+    assert abs(st["particle_steps"] - so["nsteps"]) <= 0.002 * so["nsteps"]
+    assert abs(de - de_or) <= 0.05 * de_or
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("n", [1000, 20000])
 def test_graph_eager_and_fused_paths_identical(prec, n):
