@@ -513,6 +513,47 @@ def _timed_force(g, idx, reps=3):
     return sorted(ts)[len(ts) // 2]
 
 
+# ------------------------------------------------------------------ oracle on all host cores
+
+def _host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _pool(workers):
+    """A process pool started with spawn (the parent holds a CUDA context)."""
+    import multiprocessing as mp
+
+    return mp.get_context("spawn").Pool(workers)
+
+
+def _oracle_cluster_job(job):
+    """One cluster of the ensemble through the oracle to t_end: (interactions, s)."""
+    q, n, seed, t_end = job
+    import oracle
+    from paper_1702_00440_gb300 import inputs
+
+    m, x, v = inputs.plummer(int(n), seed=int(seed))
+    t0 = time.perf_counter()
+    sim = oracle.Sim(m, x, v, EPS, ETA)
+    sim.evolve(t_end)
+    return sim.stats()["interactions"], time.perf_counter() - t0
+
+
+def _oracle_force_job(job):
+    """Oracle force of a slice of active particles against all n: (count, s)."""
+    n, idx = job
+    import oracle
+    from paper_1702_00440_gb300 import inputs
+
+    m, x, v = inputs.plummer(int(n), seed=1)
+    t0 = time.perf_counter()
+    oracle.force(m, x, v, EPS, np.asarray(idx, dtype=np.int32))
+    return len(idx), time.perf_counter() - t0
+
+
 def sweep_force(a):
     """Full evaluations N = 2^10..2^20 (mixed), and N = 2^20 with random active
     sets of 1, 32, 1024, 32768, 2^20 (mixed and FP64, FP64 up to 32768), with the
@@ -548,8 +589,20 @@ def sweep_force(a):
     t0 = time.perf_counter()
     oracle.force(m, x, v, EPS, sub)
     dt = time.perf_counter() - t0
+    # the 4096-particle i-subsample against all 2^20 j, spread over the host cores
+    cores = _host_cores()
+    sub4k = inputs.random_subset(n, 4096, seed=4096)
+    jobs = [(n, part.tolist()) for part in np.array_split(sub4k, cores)]
+    t0 = time.perf_counter()
+    with _pool(cores) as pool:
+        done = pool.map(_oracle_force_job, jobs)
+    dt4k = time.perf_counter() - t0
     out = {"sweep": "force", "metric": "acc+jerk interactions/s", "rows": rows,
            "oracle": {"interactions_per_s": 64.0 * n / dt, "sample": "64 i x 2^20 j", "cores": 1},
+           "oracle_all_cores": {"interactions_per_s": 4096.0 * n / dt4k, "wall_s": dt4k, "cores": cores,
+                                "sample": "4096 i x 2^20 j (wall time includes each worker's start and its "
+                                          "regeneration of the 2^20 inputs)",
+                                "worker_s": [round(w, 2) for _, w in done]},
            "peak_tflops": FP32_PEAK_TFLOPS}
     print(json.dumps(out))
     return 0
@@ -626,7 +679,31 @@ def sweep_accuracy(a):
         g.close()
         res[prec] = {"s_per_nbu": wall, "dE_E": abs((K1 + U1 - K0 - U0) / (K0 + U0)),
                      "block_steps": st["block_steps"], "particle_steps": st["particle_steps"]}
-    print(json.dumps({"sweep": "accuracy", "n": n, "t_end": 1.0, **res}))
+    # the N = 512 sphere of the first configuration to t = 1: both GPU forms and the oracle
+    import oracle
+
+    oracle.build()
+    m, x, v = inputs.plummer(512, seed=1)
+    small = {}
+    for prec in ("mixed", "fp64"):
+        g = gravidy.Integrator(m, x, v, EPS, ETA, precision=prec)
+        E0 = sum(g.energy())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.evolve(1.0)
+        wall = time.perf_counter() - t0
+        st = g.stats()
+        small[prec] = {"s_per_nbu": wall, "dE_E": abs((sum(g.energy()) - E0) / E0),
+                       "block_steps": st["block_steps"], "particle_steps": st["particle_steps"]}
+        g.close()
+    sim = oracle.Sim(m, x, v, EPS, ETA)
+    E0 = sum(sim.energy())
+    t0 = time.perf_counter()
+    sim.evolve(1.0)
+    so = sim.stats()
+    small["oracle"] = {"s_per_nbu": time.perf_counter() - t0, "dE_E": abs((sum(sim.energy()) - E0) / E0),
+                       "block_steps": so["nblock"], "particle_steps": so["nsteps"], "cores": 1}
+    print(json.dumps({"sweep": "accuracy", "n": n, "t_end": 1.0, **res, "n512": small}))
     return 0
 
 
@@ -679,6 +756,25 @@ def sweep_ensemble(a):
            "one_by_one": {"wall_s": wall_seq, "block_steps": steps_seq, "interactions_per_s": inter_seq / wall_seq},
            "speedup": wall_seq / wall_ens,
            "dE_E": {"median": float(np.median(de)), "max": float(de.max())}}
+    # the oracle on the host: every cluster to a short t_cpu, all host cores (one
+    # cluster per worker at a time), and every 8th cluster on one core
+    t_cpu = 1.0 / 64
+    cores = _host_cores()
+    jobs = [(q, int(nq), 1000 + q, t_cpu) for q, nq in enumerate(sizes)]
+    jobs_sorted = sorted(jobs, key=lambda j: -j[1])  # large clusters first
+    t0 = time.perf_counter()
+    with _pool(cores) as pool:
+        res = pool.map(_oracle_cluster_job, jobs_sorted, chunksize=1)
+    wall_all = time.perf_counter() - t0
+    inter_all = sum(r[0] for r in res)
+    t0 = time.perf_counter()
+    one = [_oracle_cluster_job(j) for j in jobs[::8]]
+    wall_one = time.perf_counter() - t0
+    out["oracle"] = {"t_end": t_cpu, "all_cores": {"cores": cores, "clusters": len(jobs), "wall_s": wall_all,
+                                                   "interactions_per_s": inter_all / wall_all},
+                     "one_core": {"clusters": len(jobs[::8]), "wall_s": wall_one,
+                                  "interactions_per_s": sum(r[0] for r in one) / wall_one},
+                     "sample": "each cluster from t = 0 (its initial O(N_c^2) force included) to t = 1/64"}
     print(json.dumps(out))
     return 0
 
