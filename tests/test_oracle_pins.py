@@ -12,6 +12,8 @@ import os
 import numpy as np
 import pytest
 
+from kepler import kepler_at as _kepler_at
+from kepler import kepler_ic as _kepler_ic
 from paper_1702_00440_gb300 import inputs
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -226,29 +228,6 @@ def test_block_quantisation_rules(oracle_mod):
 
 
 # ---------------------------------------------------------------- integrator
-
-def _kepler_ic(e=0.5, a=1.0):
-    m = np.array([0.5, 0.5])
-    rp = a * (1 - e)
-    vp = math.sqrt((1 + e) / (a * (1 - e)))
-    x = np.array([[-rp / 2, 0, 0], [rp / 2, 0, 0]])
-    v = np.array([[0, -vp / 2, 0], [0, vp / 2, 0]])
-    return m, x, v
-
-
-def _kepler_at(t, e=0.5, a=1.0):
-    """Relative position and velocity of a Kepler orbit (M = 1) that is at
-    pericentre at t = 0, from Kepler's equation."""
-    n = math.sqrt(1.0 / a ** 3)
-    M = n * t
-    E = M
-    for _ in range(60):
-        E -= (E - e * math.sin(E) - M) / (1 - e * math.cos(E))
-    den = 1 - e * math.cos(E)
-    r = np.array([a * (math.cos(E) - e), a * math.sqrt(1 - e * e) * math.sin(E), 0.0])
-    v = np.array([-a * n * math.sin(E) / den, a * n * math.sqrt(1 - e * e) * math.cos(E) / den, 0.0])
-    return r, v
-
 
 def test_kepler_orbit_block_steps(oracle_mod):
     e = 0.5
