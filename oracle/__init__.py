@@ -1,12 +1,12 @@
-"""FP64 CPU oracle of the Hermite-4 block-step integrator -- TEST INFRASTRUCTURE.
+"""FP64 CPU oracle of the Hermite-4 (and Hermite-6) block-step integrators -- TEST INFRASTRUCTURE.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
 legs of ``bench.py`` may import this package.  The product path (the CUDA
 library behind ``include/gravidy.h`` and its Python binding) never calls it.
 
-The arithmetic lives in ``hermite_oracle.c`` (plain single-threaded C,
-compiled without FMA contraction); this module compiles it on first use with
-gcc and wraps it with ctypes.  Every function cites the part of GraviDy
+The arithmetic lives in ``hermite_oracle.c`` and ``hermite6_oracle.c`` (plain
+single-threaded C, compiled without FMA contraction); this module compiles them
+on first use with gcc and wraps them with ctypes.  Every function cites the part of GraviDy
 (arXiv 1702.00440) it follows in the C source.
 
 Conventions: positions/velocities/accelerations/jerks are ``float64`` arrays of
@@ -22,7 +22,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "hermite_oracle.c")
+_SRCS = [os.path.join(_HERE, "hermite_oracle.c"), os.path.join(_HERE, "hermite6_oracle.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 CFLAGS = ["-O2", "-fno-fast-math", "-ffp-contract=off", "-fPIC", "-shared", "-std=c99"]
@@ -32,11 +32,11 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile ``hermite_oracle.c`` into ``_build/liboracle.so`` (gcc)."""
+    """Compile the oracle sources into ``_build/liboracle.so`` (gcc)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(os.path.getmtime(q) for q in _SRCS):
         tmp = _SO + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, *_SRCS, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -72,6 +72,19 @@ def _load():
             "or_sim_energy": (None, [_P, _P, _P]),
             "or_sim_get": (None, [_P, _P, _P, _P, _P, _P, _P]),
             "or_sim_stats": (None, [_P, _P, _P, _P, _P]),
+            "or6_force": (None, [_I64, _P, _P, _P, _P, _D, _I64, _P, _P, _P, _P]),
+            "or6_predict_one": (None, [_P, _P, _P, _P, _P, _P, _D, _P, _P, _P]),
+            "or6_correct_one": (None, [_P, _P, _P, _P, _P, _P, _P, _P, _D, _P, _P]),
+            "or6_derivs": (None, [_P, _P, _P, _P, _P, _P, _D, _P, _P, _P]),
+            "or6_aarseth_dt": (_D, [_P, _P, _P, _P, _P, _P, _D]),
+            "or6_sim_new": (_P, [_I64, _P, _P, _P, _D, _D, _D, _D, _D, _I64]),
+            "or6_sim_free": (None, [_P]),
+            "or6_sim_step": (_I64, [_P, _P, _P]),
+            "or6_sim_replay": (None, [_P, _I64, _I64, _P]),
+            "or6_sim_evolve": (_I64, [_P, _I64]),
+            "or6_sim_energy": (None, [_P, _P, _P]),
+            "or6_sim_get": (None, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
+            "or6_sim_stats": (None, [_P, _P, _P, _P, _P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -253,4 +266,103 @@ class Sim:
         ns = ctypes.c_int64()
         it = ctypes.c_double()
         self._lib.or_sim_stats(self._h, ctypes.byref(t), ctypes.byref(nb), ctypes.byref(ns), ctypes.byref(it))
+        return dict(tick=t.value, nblock=nb.value, nsteps=ns.value, interactions=it.value)
+
+
+# ---------------------------------------------------------------- sixth order
+
+def force6(m, x, v, a, eps, idx=None):
+    """Softened acceleration, jerk and snap of particles ``idx`` (default: all)
+    from positions, velocities and accelerations of all particles."""
+    lib = _load()
+    m = _f64(m)
+    n = m.shape[0]
+    x, v, a = (_f64(q, (n, 3)) for q in (x, v, a))
+    idx = np.arange(n, dtype=np.int32) if idx is None else np.ascontiguousarray(idx, np.int32)
+    k = idx.shape[0]
+    acc, jrk, snp = np.zeros((k, 3)), np.zeros((k, 3)), np.zeros((k, 3))
+    lib.or6_force(n, _ptr(m), _ptr(x), _ptr(v), _ptr(a), float(eps) ** 2, k, _ptr(idx), _ptr(acc), _ptr(jrk),
+                  _ptr(snp))
+    return acc, jrk, snp
+
+
+def predict6_one(x, v, a, j, s, c, dt):
+    lib = _load()
+    xp, vp, ap = np.zeros(3), np.zeros(3), np.zeros(3)
+    lib.or6_predict_one(*(_ptr(_f64(q)) for q in (x, v, a, j, s, c)), float(dt), _ptr(xp), _ptr(vp), _ptr(ap))
+    return xp, vp, ap
+
+
+def correct6_one(x0, v0, a0, j0, s0, a1, j1, s1, dt):
+    lib = _load()
+    x1, v1 = np.zeros(3), np.zeros(3)
+    lib.or6_correct_one(*(_ptr(_f64(q)) for q in (x0, v0, a0, j0, s0, a1, j1, s1)), float(dt), _ptr(x1), _ptr(v1))
+    return x1, v1
+
+
+def derivs6(a0, j0, s0, a1, j1, s1, dt):
+    """(crackle, pop, 5th derivative) of a at the end of the step."""
+    lib = _load()
+    c, p, q = np.zeros(3), np.zeros(3), np.zeros(3)
+    lib.or6_derivs(*(_ptr(_f64(w)) for w in (a0, j0, s0, a1, j1, s1)), float(dt), _ptr(c), _ptr(p), _ptr(q))
+    return c, p, q
+
+
+def aarseth6_dt(a, j, s, c, p, q, eta):
+    return _load().or6_aarseth_dt(*(_ptr(_f64(w)) for w in (a, j, s, c, p, q)), float(eta))
+
+
+class Sim6:
+    """The sixth-order oracle integrator (same block-step scheme, one more derivative)."""
+
+    def __init__(self, m, x, v, eps, eta, eta_init=0.01, dt_min=2.0 ** -22, dt_max=0.125, fixed_dtau=0):
+        self._lib = _load()
+        m = _f64(m)
+        self.n = n = m.shape[0]
+        self.dt_min = float(dt_min)
+        x = _f64(x, (n, 3))
+        v = _f64(v, (n, 3))
+        h = self._lib.or6_sim_new(n, _ptr(m), _ptr(x), _ptr(v), float(eps), float(eta), float(eta_init),
+                                  self.dt_min, float(dt_max), int(fixed_dtau))
+        if not h:
+            raise ValueError("oracle rejected the arguments")
+        self._h = ctypes.c_void_p(h)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.or6_sim_free(h)
+            self._h = None
+
+    def step(self):
+        idx = np.zeros(self.n, np.int32)
+        t = ctypes.c_int64()
+        c = self._lib.or6_sim_step(self._h, ctypes.byref(t), _ptr(idx))
+        return t.value, idx[:c].copy()
+
+    def replay(self, tick, idx):
+        idx = np.ascontiguousarray(idx, np.int32)
+        self._lib.or6_sim_replay(self._h, int(tick), idx.shape[0], _ptr(idx))
+
+    def evolve(self, t_end):
+        return self._lib.or6_sim_evolve(self._h, int(round(t_end / self.dt_min)))
+
+    def energy(self):
+        K = ctypes.c_double()
+        U = ctypes.c_double()
+        self._lib.or6_sim_energy(self._h, ctypes.byref(K), ctypes.byref(U))
+        return K.value, U.value
+
+    def state(self):
+        n = self.n
+        x, v, a, j, s, c = (np.zeros((n, 3)) for _ in range(6))
+        tau = np.zeros(n, np.int64)
+        dtau = np.zeros(n, np.int64)
+        self._lib.or6_sim_get(self._h, *(_ptr(q) for q in (x, v, a, j, s, c, tau, dtau)))
+        return dict(x=x, v=v, a=a, j=j, s=s, c=c, tau=tau, dtau=dtau)
+
+    def stats(self):
+        t, nb, ns = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        it = ctypes.c_double()
+        self._lib.or6_sim_stats(self._h, ctypes.byref(t), ctypes.byref(nb), ctypes.byref(ns), ctypes.byref(it))
         return dict(tick=t.value, nblock=nb.value, nsteps=ns.value, interactions=it.value)
