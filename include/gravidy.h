@@ -293,6 +293,58 @@ const char *gd_ens_last_error(const gd_ens *s);
 int gd_force_noalloc(int64_t n, const double *m, const double *x, const double *v, double eps,
                      const int32_t *idx, int64_t nact, double *acc, double *jerk, void *stream);
 
+/* ---- sixth-order Hermite integrator (FP64) ---------------------------------
+ *
+ * The same block-step scheme (Sec. 2.4: active set, prediction of all N, force
+ * of the active set from predicted values, correction, power-of-two steps)
+ * raised to sixth order as in the sixth-order Hermite scheme the paper cites
+ * among the higher-order Hermite integrators (Nitadori & Makino 2008): the force
+ * evaluation returns acceleration, jerk and snap (the first two time derivatives
+ * of the softened Eq. 1, which need the predicted accelerations of all
+ * particles); positions, velocities and accelerations are predicted with the
+ * crackle; the corrector is the time-symmetric sixth-order formula; the step is
+ *     dt = eta ( (|a||snap| + |jerk|^2) / (|crackle||a^(5)| + |pop|^2) )^(1/6)
+ * with crackle, pop and a^(5) from the quintic interpolant of (a, jerk, snap) at
+ * both ends of the step, quantised as in the fourth-order path.  The first steps
+ * are eta_init |a| / |jerk| (quantised); the initial crackle is zero.  All
+ * arithmetic is FP64.  Arrays and ownership as for gd_init; opt may be NULL
+ * (dt_min, dt_max, device and stream are used, the rest ignored); errors as for
+ * the other calls, gd_h6_last_error(NULL) after a failed init. */
+typedef struct gd_h6 gd_h6;
+
+int gd_h6_init(gd_h6 **out, int64_t n, const double *m, const double *x, const double *v,
+               double eps, double eta, double eta_init, const gd_opts *opt);
+
+/* Advance until no particle's next time is <= t_end (as gd_evolve). */
+int gd_h6_evolve(gd_h6 *s, double t_end);
+
+/* One block step; *t_out its time, *nact_out its number of active particles. */
+int gd_h6_step_block(gd_h6 *s, double *t_out, int64_t *nact_out);
+
+/* One block step with a given block time and active list (host int32,
+ * ascending, distinct), as gd_replay_step. */
+int gd_h6_replay_step(gd_h6 *s, int64_t tick_next, const int32_t *idx, int64_t nact);
+
+/* Acceleration, jerk and snap (nact*3 host doubles each, order of idx) of the
+ * particles idx against all n predicted to tick; state unchanged. */
+int gd_h6_force(gd_h6 *s, int64_t tick, const int32_t *idx, int64_t nact, double *acc,
+                double *jerk, double *snap);
+
+/* Kinetic and softened potential energy with every particle predicted to the
+ * time of the last block step. */
+int gd_h6_energy(gd_h6 *s, double *K, double *U);
+
+/* State at each particle's own time (n*3 AoS doubles; tau, dtau n int64);
+ * any pointer may be NULL. */
+int gd_h6_get_state(gd_h6 *s, double *x, double *v, double *a, double *jerk, double *snap,
+                    double *crackle, int64_t *tau, int64_t *dtau);
+
+/* Counters (as gd_get_stats; phase_ms zero). */
+int gd_h6_get_stats(gd_h6 *s, gd_stats *st);
+
+void gd_h6_free(gd_h6 *s);
+const char *gd_h6_last_error(const gd_h6 *s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -7,7 +7,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = [os.path.join(HERE, "csrc", "gravidy.cu")]
+SRC = [os.path.join(HERE, "csrc", "gravidy.cu"), os.path.join(HERE, "csrc", "hermite6.cu")]
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libgravidy_gb300.so")

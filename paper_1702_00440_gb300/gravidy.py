@@ -30,6 +30,8 @@ EXPORTS = (
     "gd_cluster_info", "gd_cluster_time",
     "gd_ens_init", "gd_ens_evolve", "gd_ens_step_block", "gd_ens_energy", "gd_ens_get_state",
     "gd_ens_get_stats", "gd_ens_free", "gd_ens_last_error",
+    "gd_h6_init", "gd_h6_evolve", "gd_h6_step_block", "gd_h6_replay_step", "gd_h6_force", "gd_h6_energy",
+    "gd_h6_get_state", "gd_h6_get_stats", "gd_h6_free", "gd_h6_last_error",
 )
 
 
@@ -121,6 +123,16 @@ def load(build_if_missing: bool = True):
             "gd_ens_get_stats": (ctypes.c_int, [P, P]),
             "gd_ens_free": (None, [P]),
             "gd_ens_last_error": (ctypes.c_char_p, [P]),
+            "gd_h6_init": (ctypes.c_int, [P, I64, P, P, P, D, D, D, P]),
+            "gd_h6_evolve": (ctypes.c_int, [P, D]),
+            "gd_h6_step_block": (ctypes.c_int, [P, P, P]),
+            "gd_h6_replay_step": (ctypes.c_int, [P, I64, P, I64]),
+            "gd_h6_force": (ctypes.c_int, [P, I64, P, I64, P, P, P]),
+            "gd_h6_energy": (ctypes.c_int, [P, P, P]),
+            "gd_h6_get_state": (ctypes.c_int, [P, P, P, P, P, P, P, P, P]),
+            "gd_h6_get_stats": (ctypes.c_int, [P, P]),
+            "gd_h6_free": (None, [P]),
+            "gd_h6_last_error": (ctypes.c_char_p, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -454,3 +466,82 @@ class Ensemble:
         _check_ens(load().gd_ens_get_stats(self._h, ctypes.byref(s)), self._h)
         return dict(tick=s.tick, block_steps=s.block_steps, particle_steps=s.particle_steps,
                     interactions=s.interactions, last_nact=s.last_nact, kernel_launches=s.kernel_launches)
+
+
+def _check_h6(rc, h=None):
+    if rc != GD_OK:
+        msg = load().gd_h6_last_error(h)
+        raise GravidyError(rc, msg.decode() if msg else "error")
+
+
+class Integrator6:
+    """gd_h6: the sixth-order Hermite block-step integrator (FP64)."""
+
+    def __init__(self, m, x, v, eps, eta, eta_init=0.01, **opts):
+        lib = load()
+        m = np.ascontiguousarray(np.asarray(m, dtype=np.float64))
+        self.n = n = m.shape[0]
+        x = _f64(x, (n, 3))
+        v = _f64(v, (n, 3))
+        opts.setdefault("precision", "fp64")
+        o = make_opts(**opts)
+        self.dt_min = o.dt_min
+        h = ctypes.c_void_p()
+        _check_h6(lib.gd_h6_init(ctypes.byref(h), n, _p(m), _p(x), _p(v), float(eps), float(eta), float(eta_init),
+                                 ctypes.byref(o)))
+        self._h = h
+
+    def close(self):
+        h, self._h = getattr(self, "_h", None), None
+        if h is not None:
+            load().gd_h6_free(h)
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def evolve(self, t_end):
+        _check_h6(load().gd_h6_evolve(self._h, float(t_end)), self._h)
+
+    def step_block(self):
+        t = ctypes.c_double()
+        k = ctypes.c_int64()
+        _check_h6(load().gd_h6_step_block(self._h, ctypes.byref(t), ctypes.byref(k)), self._h)
+        return t.value, k.value
+
+    def replay_step(self, tick, idx):
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        _check_h6(load().gd_h6_replay_step(self._h, int(tick), _p(idx), idx.shape[0]), self._h)
+
+    def force(self, tick, idx):
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        k = idx.shape[0]
+        acc, jrk, snp = np.empty((k, 3)), np.empty((k, 3)), np.empty((k, 3))
+        _check_h6(load().gd_h6_force(self._h, int(tick), _p(idx), k, _p(acc), _p(jrk), _p(snp)), self._h)
+        return acc, jrk, snp
+
+    def energy(self):
+        K = ctypes.c_double()
+        U = ctypes.c_double()
+        _check_h6(load().gd_h6_energy(self._h, ctypes.byref(K), ctypes.byref(U)), self._h)
+        return K.value, U.value
+
+    def state(self):
+        n = self.n
+        o = {k: np.empty((n, 3)) for k in ("x", "v", "a", "j", "s", "c")}
+        o["tau"] = np.empty(n, np.int64)
+        o["dtau"] = np.empty(n, np.int64)
+        _check_h6(load().gd_h6_get_state(self._h, *(_p(o[k]) for k in ("x", "v", "a", "j", "s", "c", "tau", "dtau"))),
+                  self._h)
+        return o
+
+    def stats(self):
+        st = gd_stats()
+        _check_h6(load().gd_h6_get_stats(self._h, ctypes.byref(st)), self._h)
+        return dict(tick=st.tick, block_steps=st.block_steps, particle_steps=st.particle_steps,
+                    interactions=st.interactions, last_nact=st.last_nact, kernel_launches=st.kernel_launches)

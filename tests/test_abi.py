@@ -1,6 +1,6 @@
 """The C ABI without a GPU: the library builds, loads, and exports every
-function include/gravidy.h declares; host-side argument checks of gd_init
-reject bad input before any device work."""
+function include/gravidy.h declares; host-side argument checks of gd_init and
+gd_h6_init reject bad input before any device work."""
 import ctypes
 import os
 import re
@@ -33,17 +33,21 @@ def test_library_exports_every_declared_function():
     assert sorted(gravidy.EXPORTS) == _declared()
 
 
-def _init(n, m, x, v, eps=1e-4, eta=0.01, **kw):
+def _init(n, m, x, v, eps=1e-4, eta=0.01, order=4, **kw):
     lib = gravidy.load()
     o = gravidy.make_opts(**kw)
     h = ctypes.c_void_p()
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    if order == 6:
+        rc = lib.gd_h6_init(ctypes.byref(h), n, p(m), p(x), p(v), eps, eta, 0.01, ctypes.byref(o))
+        return rc, lib.gd_h6_last_error(None).decode()
     rc = lib.gd_init(ctypes.byref(h), n, p(m), p(x), p(v), eps, eta, ctypes.byref(o))
     return rc, lib.gd_last_error(None).decode()
 
 
+@pytest.mark.parametrize("order", [4, 6])
 @pytest.mark.parametrize("case", ["n0", "eps", "eta", "dtmin", "dtorder", "mass", "nan"])
-def test_gd_init_rejects_bad_arguments_on_the_host(case):
+def test_gd_init_rejects_bad_arguments_on_the_host(case, order):
     n = 4
     m = np.full(n, 0.25)
     x = np.arange(12, dtype=float).reshape(4, 3)
@@ -64,7 +68,7 @@ def test_gd_init_rejects_bad_arguments_on_the_host(case):
         m[1] = -1.0
     elif case == "nan":
         x[2, 1] = np.nan
-    rc, msg = _init(n, m, x, v, eps, eta, **kw)
+    rc, msg = _init(n, m, x, v, eps, eta, order, **kw)
     assert rc == gravidy.GD_EINVAL
     assert msg
 
