@@ -68,7 +68,7 @@ def _args():
     p.add_argument("--profile-force", type=int, default=0, metavar="N",
                    help="profiling hook: initialise an N-particle Plummer sphere (one full force evaluation), "
                         "evaluate all N once more, print nothing and exit")
-    p.add_argument("--sweep", choices=["force", "powerlaw", "accuracy", "ensemble", "eta", "soft", "lagrange"],
+    p.add_argument("--sweep", choices=["force", "powerlaw", "accuracy", "ensemble", "eta", "soft", "lagrange", "h6"],
                    help="extra measurements, one JSON line each (not the benchmark line): force = "
                         "full evaluations N=2^10..2^20 and N=2^20 with active sets 1..2^20; powerlaw = "
                         "N=262144 power-law masses to t=1/8 (active-set histogram, interactions/s per "
@@ -76,7 +76,8 @@ def _args():
                         "log-uniform N in [256, 8192] to t=--ens-t, one ensemble vs the clusters one by one; eta = "
                         "Plummer N=1024..16384 to t=2 for eta=0.001..0.1: s per N-body unit and |dE/E| (mixed, FP64 "
                         "at eta=0.01, the oracle at N=1024) and the block-step distribution; soft = the same for "
-                        "eps=1e-5..1e-2 at eta=0.01; lagrange = Lagrange radii of N=16384 every 1/2 unit to t=8")
+                        "eps=1e-5..1e-2 at eta=0.01; lagrange = Lagrange radii of N=16384 every 1/2 unit to t=8; "
+                        "h6 = sixth- vs fourth-order Hermite: cost and |dE/E| to t=1, and the snap kernel's rate")
     p.add_argument("--ens-t", type=float, default=0.125)
     p.add_argument("--profile-nact", type=int, default=0, metavar="K",
                    help="profiling hook: autotune on the --n workload, then evaluate the force of K random "
@@ -900,6 +901,53 @@ def sweep_lagrange(a):
     return 0
 
 
+def sweep_h6(a):
+    """Sixth- against fourth-order Hermite on Plummer N = 1024 and 4096 (seed 1,
+    eps = 1e-4) to t = 1: wall time per N-body unit and |dE/E| for the FP64
+    fourth-order path at eta = 0.003, 0.01, 0.03, the FP64 sixth-order path at
+    eta = 0.1, 0.2, 0.4 and the mixed fourth-order path at eta = 0.003, 0.01;
+    and full force/jerk/snap evaluations (N = 16384, 65536) of the sixth-order
+    kernel."""
+    import torch
+
+    from paper_1702_00440_gb300 import gravidy, inputs
+
+    rows = []
+    for n in (1024, 4096):
+        m, x, v = inputs.plummer(n, seed=1)
+        runs = [("h4", "fp64", e) for e in (0.003, 0.01, 0.03)] + [("h6", "fp64", e) for e in (0.1, 0.2, 0.4)] + \
+               [("h4", "mixed", e) for e in (0.003, 0.01)]
+        for order, prec, eta in runs:
+            if order == "h6":
+                g = gravidy.Integrator6(m, x, v, EPS, eta)
+            else:
+                g = gravidy.Integrator(m, x, v, EPS, eta, precision=prec, autotune=prec == "mixed")
+            E0 = sum(g.energy())
+            s0 = g.stats()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g.evolve(1.0)
+            wall = time.perf_counter() - t0
+            E1 = sum(g.energy())
+            s1 = g.stats()
+            g.close()
+            rows.append({"n": n, "order": order, "precision": prec, "eta": eta, "s_per_nbu": wall,
+                         "dE_E": abs((E1 - E0) / E0), "block_steps": s1["block_steps"] - s0["block_steps"],
+                         "particle_steps": s1["particle_steps"] - s0["particle_steps"]})
+    force = []
+    for n in (16384, 65536):
+        m, x, v = inputs.plummer(n, seed=1)
+        with gravidy.Integrator6(m, x, v, EPS, 0.2) as g:
+            idx = np.arange(n, dtype=np.int32)
+            g.force(0, idx)
+            t0 = time.perf_counter()
+            g.force(0, idx)
+            dt = time.perf_counter() - t0
+        force.append({"n": n, "s": dt, "interactions_per_s": float(n) * n / dt})
+    print(json.dumps({"sweep": "h6", "t_end": 1.0, "eps": EPS, "rows": rows, "force": force}))
+    return 0
+
+
 def profile_force(a):
     from paper_1702_00440_gb300 import gravidy, inputs
 
@@ -959,7 +1007,7 @@ def main():
     if a.sweep:
         return {"force": sweep_force, "powerlaw": sweep_powerlaw, "accuracy": sweep_accuracy,
                 "ensemble": sweep_ensemble, "eta": sweep_eta, "soft": sweep_soft,
-                "lagrange": sweep_lagrange}[a.sweep](a)
+                "lagrange": sweep_lagrange, "h6": sweep_h6}[a.sweep](a)
     if a.impl == "reference":
         return run_reference(a)
     return run_gravidy(a)

@@ -315,7 +315,7 @@ def aarseth6_dt(a, j, s, c, p, q, eta):
 class Sim6:
     """The sixth-order oracle integrator (same block-step scheme, one more derivative)."""
 
-    def __init__(self, m, x, v, eps, eta, eta_init=0.01, dt_min=2.0 ** -22, dt_max=0.125, fixed_dtau=0):
+    def __init__(self, m, x, v, eps, eta, eta_init=0.001, dt_min=2.0 ** -22, dt_max=0.125, fixed_dtau=0):
         self._lib = _load()
         m = _f64(m)
         self.n = n = m.shape[0]

@@ -25,6 +25,9 @@
  *     oracle.
  * Readings where the sources are silent (listed in the design notes):
  *   - the initial step is eta_init |a| / |jerk| (quantised), crackle = 0 at t = 0;
+ *     the first step's predictions miss the crackle term, so eta_init must be
+ *     small (the wrappers default to 1e-3; 1e-2 leaves an energy error of about
+ *     4e-9 at N = 1024 that no later step removes);
  *   - the initial snap uses the exact initial accelerations of all particles.
  *
  * Build: together with hermite_oracle.c, gcc -O2 -fno-fast-math -ffp-contract=off.

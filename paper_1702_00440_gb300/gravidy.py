@@ -477,7 +477,7 @@ def _check_h6(rc, h=None):
 class Integrator6:
     """gd_h6: the sixth-order Hermite block-step integrator (FP64)."""
 
-    def __init__(self, m, x, v, eps, eta, eta_init=0.01, **opts):
+    def __init__(self, m, x, v, eps, eta, eta_init=0.001, **opts):
         lib = load()
         m = np.ascontiguousarray(np.asarray(m, dtype=np.float64))
         self.n = n = m.shape[0]
