@@ -267,12 +267,17 @@ def run_reference(a):
 
 # ------------------------------------------------------------------ main arm
 
+# the sources the fourth-order step kernels are built from (the sixth-order path,
+# hermite6.cu, has kernels of its own)
+STEP_SOURCES = ("cluster.cuh", "ensemble.cuh", "gravidy.cu", "kernels.cuh")
+
+
 def _csrc_hash():
-    """SHA-256 over the CUDA sources (file names and contents, sorted by name)."""
+    """SHA-256 over the step kernels' CUDA sources (file names and contents)."""
     d = os.path.join(ROOT, "paper_1702_00440_gb300", "csrc")
     h = hashlib.sha256()
     for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh", ".h")):
+        if name in STEP_SOURCES:
             h.update(name.encode())
             with open(os.path.join(d, name), "rb") as f:
                 h.update(f.read())
