@@ -79,6 +79,9 @@ def _args():
                         "eps=1e-5..1e-2 at eta=0.01; lagrange = Lagrange radii of N=16384 every 1/2 unit to t=8; "
                         "h6 = sixth- vs fourth-order Hermite: cost and |dE/E| to t=1, and the snap kernel's rate")
     p.add_argument("--ens-t", type=float, default=0.125)
+    p.add_argument("--profile-force-h6", type=int, default=0, metavar="N",
+                   help="profiling hook: initialise an N-particle Plummer sphere on the sixth-order path (two "
+                        "force/jerk/snap evaluations), evaluate all N once more, print nothing and exit")
     p.add_argument("--profile-nact", type=int, default=0, metavar="K",
                    help="profiling hook: autotune on the --n workload, then evaluate the force of K random "
                         "particles (gd_force) once, and twice more between cudaProfilerStart/Stop; print the "
@@ -962,6 +965,15 @@ def profile_force(a):
     return 0
 
 
+def profile_force_h6(a):
+    from paper_1702_00440_gb300 import gravidy, inputs
+
+    m, x, v = inputs.plummer(a.profile_force_h6, seed=1)
+    with gravidy.Integrator6(m, x, v, EPS, 0.2) as g:
+        g.force(0, np.arange(a.profile_force_h6, dtype=np.int32))
+    return 0
+
+
 def profile_steps(a):
     """Integrates to t = 0.375 (the start of the timed window), then runs the next
     1/64 N-body time unit between cudaProfilerStart/Stop, so that
@@ -1007,6 +1019,8 @@ def main():
         return profile_nact(a)
     if a.profile_force:
         return profile_force(a)
+    if a.profile_force_h6:
+        return profile_force_h6(a)
     if a.profile_steps:
         return profile_steps(a)
     if a.sweep:
