@@ -77,7 +77,8 @@ def _load():
             "or6_correct_one": (None, [_P, _P, _P, _P, _P, _P, _P, _P, _D, _P, _P]),
             "or6_derivs": (None, [_P, _P, _P, _P, _P, _P, _D, _P, _P, _P]),
             "or6_aarseth_dt": (_D, [_P, _P, _P, _P, _P, _P, _D]),
-            "or6_sim_new": (_P, [_I64, _P, _P, _P, _D, _D, _D, _D, _D, _I64]),
+            "or4s_correct_one": (None, [_P, _P, _P, _P, _P, _P, _D, _P, _P]),
+            "or6_sim_new": (_P, [_I64, _P, _P, _P, _D, _D, _D, _D, _D, _I64, ctypes.c_int, ctypes.c_int]),
             "or6_sim_free": (None, [_P]),
             "or6_sim_step": (_I64, [_P, _P, _P]),
             "or6_sim_replay": (None, [_P, _I64, _I64, _P]),
@@ -300,6 +301,14 @@ def correct6_one(x0, v0, a0, j0, s0, a1, j1, s1, dt):
     return x1, v1
 
 
+def correct4s_one(x0, v0, a0, j0, a1, j1, dt):
+    """Time-symmetric fourth-order corrector (Hut, Makino & McMillan 1995)."""
+    lib = _load()
+    x1, v1 = np.zeros(3), np.zeros(3)
+    lib.or4s_correct_one(*(_ptr(_f64(q)) for q in (x0, v0, a0, j0, a1, j1)), float(dt), _ptr(x1), _ptr(v1))
+    return x1, v1
+
+
 def derivs6(a0, j0, s0, a1, j1, s1, dt):
     """(crackle, pop, 5th derivative) of a at the end of the step."""
     lib = _load()
@@ -313,9 +322,13 @@ def aarseth6_dt(a, j, s, c, p, q, eta):
 
 
 class Sim6:
-    """The sixth-order oracle integrator (same block-step scheme, one more derivative)."""
+    """The time-symmetric Hermite oracle integrator: order 6 (one more
+    derivative than GraviDy's scheme) or order 4 (GraviDy's scheme with the
+    time-symmetric corrector), n_iter evaluation-correction passes per block
+    step."""
 
-    def __init__(self, m, x, v, eps, eta, eta_init=0.001, dt_min=2.0 ** -22, dt_max=0.125, fixed_dtau=0):
+    def __init__(self, m, x, v, eps, eta, eta_init=0.001, dt_min=2.0 ** -22, dt_max=0.125, fixed_dtau=0,
+                 order=6, n_iter=1):
         self._lib = _load()
         m = _f64(m)
         self.n = n = m.shape[0]
@@ -323,7 +336,7 @@ class Sim6:
         x = _f64(x, (n, 3))
         v = _f64(v, (n, 3))
         h = self._lib.or6_sim_new(n, _ptr(m), _ptr(x), _ptr(v), float(eps), float(eta), float(eta_init),
-                                  self.dt_min, float(dt_max), int(fixed_dtau))
+                                  self.dt_min, float(dt_max), int(fixed_dtau), int(order), int(n_iter))
         if not h:
             raise ValueError("oracle rejected the arguments")
         self._h = ctypes.c_void_p(h)

@@ -23,6 +23,21 @@
  *       dt = eta ( (|a||snap| + |jerk|^2) / (|crackle||a^(5)| + |pop|^2) )^(1/6),
  *     quantised to the power-of-two block steps exactly as in the 4th-order
  *     oracle.
+ *
+ * The same driver also runs the fourth-order scheme in its time-symmetric form
+ * (order 4): the corrector of Hut, Makino & McMillan (1995), which is the
+ * fourth-order member of the nm08 family,
+ *     v1 = v0 + h (a1 + a0) - (h^2 / 3) (j1 - j0)
+ *     x1 = x0 + h (v1 + v0) - (h^2 / 3) (a1 - a0),      h = dt / 2,
+ * with GraviDy's cubic predictor, force and jerk, Aarseth step and block
+ * quantisation (Sec. 2.1, 2.4); snap and crackle stay zero.  Either order may
+ * iterate the evaluation and correction n_iter times per block step (P(EC)^n,
+ * Kokubo, Yoshinaga & Makino 1998): after every pass but the last, the
+ * corrected position and velocity and the new acceleration of each active
+ * particle replace its prediction, and the next pass evaluates the active
+ * particles against those values.  With shared constant steps and converged
+ * passes the map is time-reversible.
+ *
  * Readings where the sources are silent (listed in the design notes):
  *   - the initial step is eta_init |a| / |jerk| (quantised), crackle = 0 at t = 0;
  *     the first step's predictions miss the crackle term, so eta_init must be
@@ -38,6 +53,10 @@
 #include <string.h>
 
 /* from hermite_oracle.c */
+void or_hermite_derivs(const double a0[3], const double j0[3], const double a1[3],
+                       const double j1[3], double dt, double a2[3], double a3[3]);
+double or_aarseth_dt(const double a1[3], const double j1[3], const double a2e[3],
+                     const double a3e[3], double eta);
 void or_force(int64_t n, const double *m, const double *x, const double *v, double eps2,
               int64_t nact, const int32_t *idx, double *acc, double *jrk);
 void or_energy(int64_t n, const double *m, const double *x, const double *v, double eps2,
@@ -141,6 +160,23 @@ void or6_correct_one(const double x0[3], const double v0[3], const double a0[3],
     }
 }
 
+/* Time-symmetric fourth-order corrector (Hut, Makino & McMillan 1995): with
+ * h = dt / 2,
+ *   v1 = v0 + h (a1 + a0) - (1/3) h^2 (j1 - j0)
+ *   x1 = x0 + h (v1 + v0) - (1/3) h^2 (a1 - a0).
+ * The velocity formula integrates the cubic Hermite interpolant of (a, jerk)
+ * at both ends; the position formula is the same quadrature of the velocity. */
+void or4s_correct_one(const double x0[3], const double v0[3], const double a0[3],
+                      const double j0[3], const double a1[3], const double j1[3], double dt,
+                      double x1[3], double v1[3])
+{
+    double h = dt / 2.0, h2 = h * h;
+    for (int k = 0; k < 3; k++) {
+        v1[k] = v0[k] + h * (a1[k] + a0[k]) - h2 * (j1[k] - j0[k]) / 3.0;
+        x1[k] = x0[k] + h * (v1[k] + v0[k]) - h2 * (a1[k] - a0[k]) / 3.0;
+    }
+}
+
 /* The quintic a(tau) = sum_k c_k tau^k on tau in [-h, h] (h = dt / 2, tau = 0 at
  * the middle of the step) that matches a, jerk, snap at both ends.  With
  * plus/minus halves P = (q1 + q0)/2, M = (q1 - q0)/2 of each quantity:
@@ -186,6 +222,7 @@ typedef struct or6_sim {
     int64_t n;
     double eps2, eta, dt_min;
     int64_t dtau_max, fixed_dtau;
+    int order, n_iter;                 /* 4 (time-symmetric) or 6; evaluations per step */
     double *m, *x, *v, *a, *j, *s, *c; /* state at each particle's own time */
     double *xp, *vp, *ap;              /* predicted state of all particles */
     double *a1, *j1, *s1;              /* new force, jerk, snap of the active set */
@@ -205,13 +242,15 @@ void or6_sim_free(or6_sim *q)
     free(q);
 }
 
-/* Initial force, jerk (4th-order oracle) and snap (from the exact initial
- * accelerations), crackle 0, first steps eta_init |a| / |jerk| (or fixed_dtau). */
+/* Initial force, jerk (4th-order oracle) and, for order 6, snap (from the
+ * exact initial accelerations); crackle 0; first steps eta_init |a| / |jerk|
+ * (or fixed_dtau). */
 or6_sim *or6_sim_new(int64_t n, const double *m, const double *x, const double *v, double eps,
-                     double eta, double eta_init, double dt_min, double dt_max, int64_t fixed_dtau)
+                     double eta, double eta_init, double dt_min, double dt_max, int64_t fixed_dtau,
+                     int order, int n_iter)
 {
     if (n < 1 || !(eps >= 0) || !(eta > 0) || !(eta_init > 0) || !(dt_min > 0) ||
-        !(dt_max >= dt_min))
+        !(dt_max >= dt_min) || (order != 4 && order != 6) || n_iter < 1)
         return NULL;
     or6_sim *q = (or6_sim *)calloc(1, sizeof(or6_sim));
     if (!q)
@@ -222,10 +261,12 @@ or6_sim *or6_sim_new(int64_t n, const double *m, const double *x, const double *
     q->dt_min = dt_min;
     q->dtau_max = (int64_t)(dt_max / dt_min);
     q->fixed_dtau = fixed_dtau;
+    q->order = order;
+    q->n_iter = n_iter;
     size_t v3 = (size_t)n * 3 * sizeof(double);
     q->m = malloc((size_t)n * sizeof(double));
     q->x = malloc(v3); q->v = malloc(v3); q->a = malloc(v3); q->j = malloc(v3);
-    q->s = malloc(v3); q->c = calloc((size_t)n * 3, sizeof(double));
+    q->s = calloc((size_t)n * 3, sizeof(double)); q->c = calloc((size_t)n * 3, sizeof(double));
     q->xp = malloc(v3); q->vp = malloc(v3); q->ap = malloc(v3);
     q->a1 = malloc(v3); q->j1 = malloc(v3); q->s1 = malloc(v3);
     q->tau = calloc((size_t)n, sizeof(int64_t));
@@ -243,8 +284,11 @@ or6_sim *or6_sim_new(int64_t n, const double *m, const double *x, const double *
     for (int64_t i = 0; i < n; i++)
         q->act[i] = (int32_t)i;
     or_force(n, q->m, q->x, q->v, q->eps2, n, q->act, q->a, q->j);
-    or6_force(n, q->m, q->x, q->v, q->a, q->eps2, n, q->act, q->a1, q->j1, q->s);
-    q->interactions += 2.0 * (double)n * (double)n;
+    q->interactions += (double)n * (double)n;
+    if (order == 6) {
+        or6_force(n, q->m, q->x, q->v, q->a, q->eps2, n, q->act, q->a1, q->j1, q->s);
+        q->interactions += (double)n * (double)n;
+    }
     for (int64_t i = 0; i < n; i++) {
         if (fixed_dtau > 0) {
             q->dtau[i] = fixed_dtau;
@@ -257,6 +301,31 @@ or6_sim *or6_sim_new(int64_t n, const double *m, const double *x, const double *
     return q;
 }
 
+/* New force, jerk and (order 6) snap of the active set into a1, j1, s1. */
+static void evaluate6(or6_sim *q, int64_t nact, const int32_t *idx)
+{
+    if (q->order == 6) {
+        or6_force(q->n, q->m, q->xp, q->vp, q->ap, q->eps2, nact, idx, q->a1, q->j1, q->s1);
+    } else {
+        or_force(q->n, q->m, q->xp, q->vp, q->eps2, nact, idx, q->a1, q->j1);
+        memset(q->s1, 0, (size_t)nact * 3 * sizeof(double));
+    }
+    q->interactions += (double)nact * (double)q->n;
+}
+
+/* Corrected x1, v1 of active slot k (particle i) from its state at its own time
+ * and the slot's new force, jerk, snap. */
+static void correct_slot6(const or6_sim *q, int64_t k, int64_t i, double dt, double x1[3],
+                          double v1[3])
+{
+    if (q->order == 6)
+        or6_correct_one(q->x + 3 * i, q->v + 3 * i, q->a + 3 * i, q->j + 3 * i, q->s + 3 * i,
+                        q->a1 + 3 * k, q->j1 + 3 * k, q->s1 + 3 * k, dt, x1, v1);
+    else
+        or4s_correct_one(q->x + 3 * i, q->v + 3 * i, q->a + 3 * i, q->j + 3 * i, q->a1 + 3 * k,
+                         q->j1 + 3 * k, dt, x1, v1);
+}
+
 static void block_step6(or6_sim *q, int64_t tick_next, int64_t nact, const int32_t *idx)
 {
     int64_t n = q->n;
@@ -265,22 +334,42 @@ static void block_step6(or6_sim *q, int64_t tick_next, int64_t nact, const int32
         or6_predict_one(q->x + 3 * i, q->v + 3 * i, q->a + 3 * i, q->j + 3 * i, q->s + 3 * i,
                         q->c + 3 * i, dt, q->xp + 3 * i, q->vp + 3 * i, q->ap + 3 * i);
     }
-    or6_force(n, q->m, q->xp, q->vp, q->ap, q->eps2, nact, idx, q->a1, q->j1, q->s1);
-    q->interactions += (double)nact * (double)n;
+    /* P(EC)^n: every pass but the last puts the active particles' corrected
+     * values in place of their predictions before the next evaluation */
+    for (int pass = 1; pass < q->n_iter; pass++) {
+        evaluate6(q, nact, idx);
+        for (int64_t k = 0; k < nact; k++) {
+            int64_t i = idx[k];
+            double dt = (double)(tick_next - q->tau[i]) * q->dt_min;
+            correct_slot6(q, k, i, dt, q->xp + 3 * i, q->vp + 3 * i);
+            for (int c = 0; c < 3; c++)
+                q->ap[3 * i + c] = q->a1[3 * k + c];
+        }
+    }
+    evaluate6(q, nact, idx);
     for (int64_t k = 0; k < nact; k++) {
         int64_t i = idx[k];
         double dt = (double)(tick_next - q->tau[i]) * q->dt_min;
-        double crk[3], pop[3], a5[3];
+        double crk[3] = {0, 0, 0}, pop[3], a5[3], a2[3], a3[3], a2e[3];
         double *a1 = q->a1 + 3 * k, *j1 = q->j1 + 3 * k, *s1 = q->s1 + 3 * k;
-        or6_derivs(q->a + 3 * i, q->j + 3 * i, q->s + 3 * i, a1, j1, s1, dt, crk, pop, a5);
         double x1[3], v1[3];
-        or6_correct_one(q->x + 3 * i, q->v + 3 * i, q->a + 3 * i, q->j + 3 * i, q->s + 3 * i, a1,
-                        j1, s1, dt, x1, v1);
+        correct_slot6(q, k, i, dt, x1, v1);
+        if (q->order == 6)
+            or6_derivs(q->a + 3 * i, q->j + 3 * i, q->s + 3 * i, a1, j1, s1, dt, crk, pop, a5);
+        else
+            or_hermite_derivs(q->a + 3 * i, q->j + 3 * i, a1, j1, dt, a2, a3);
         int64_t dtau;
         if (q->fixed_dtau > 0) {
             dtau = q->fixed_dtau;
         } else {
-            double dtn = or6_aarseth_dt(a1, j1, s1, crk, pop, a5, q->eta);
+            double dtn;
+            if (q->order == 6) {
+                dtn = or6_aarseth_dt(a1, j1, s1, crk, pop, a5, q->eta);
+            } else {
+                for (int c = 0; c < 3; c++)
+                    a2e[c] = a2[c] + dt * a3[c];
+                dtn = or_aarseth_dt(a1, j1, a2e, a3, q->eta);
+            }
             dtau = or_quantise(dtn, q->dtau[i], tick_next, q->dt_min, q->dtau_max);
         }
         for (int c = 0; c < 3; c++) {
