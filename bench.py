@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -68,7 +69,8 @@ def _args():
     p.add_argument("--profile-force", type=int, default=0, metavar="N",
                    help="profiling hook: initialise an N-particle Plummer sphere (one full force evaluation), "
                         "evaluate all N once more, print nothing and exit")
-    p.add_argument("--sweep", choices=["force", "powerlaw", "accuracy", "ensemble", "eta", "soft", "lagrange", "h6"],
+    p.add_argument("--sweep", choices=["force", "powerlaw", "accuracy", "ensemble", "eta", "soft", "lagrange", "h6",
+                                          "timesym"],
                    help="extra measurements, one JSON line each (not the benchmark line): force = "
                         "full evaluations N=2^10..2^20 and N=2^20 with active sets 1..2^20; powerlaw = "
                         "N=262144 power-law masses to t=1/8 (active-set histogram, interactions/s per "
@@ -77,7 +79,9 @@ def _args():
                         "Plummer N=1024..16384 to t=2 for eta=0.001..0.1: s per N-body unit and |dE/E| (mixed, FP64 "
                         "at eta=0.01, the oracle at N=1024) and the block-step distribution; soft = the same for "
                         "eps=1e-5..1e-2 at eta=0.01; lagrange = Lagrange radii of N=16384 every 1/2 unit to t=8; "
-                        "h6 = sixth- vs fourth-order Hermite: cost and |dE/E| to t=1, and the snap kernel's rate")
+                        "h6 = sixth- vs fourth-order Hermite: cost and |dE/E| to t=1, and the snap kernel's rate; "
+                        "timesym = the time-symmetric schemes (order 4 and 6, one and two passes): cost and |dE/E| "
+                        "to t=1, energy drift and reversibility on a Kepler orbit with shared constant steps")
     p.add_argument("--ens-t", type=float, default=0.125)
     p.add_argument("--profile-force-h6", type=int, default=0, metavar="N",
                    help="profiling hook: initialise an N-particle Plummer sphere on the sixth-order path (two "
@@ -956,6 +960,78 @@ def sweep_h6(a):
     return 0
 
 
+def sweep_timesym(a):
+    """The time-symmetric schemes of the gd_h6 engine.  (1) Plummer N = 1024 and
+    4096 (seed 1, eps = 1e-4) to t = 1: wall time per N-body unit, |dE/E| and
+    step counts of GraviDy's FP64 fourth-order path (eta = 0.01), the
+    time-symmetric fourth-order corrector with one and two passes (eta = 0.01)
+    and the sixth-order scheme with one and two passes (eta = 0.2).  (2) The
+    e = 0.5 Kepler orbit with shared constant steps (dt_min = dt_max): the mean
+    energy error of each of 8 orbits, its linear drift over the run relative to
+    its mean, and the distance from the start after one orbit forward and back
+    with reversed velocities."""
+    import torch
+
+    from paper_1702_00440_gb300 import gravidy, inputs
+
+    rows = []
+    for n in (1024, 4096):
+        m, x, v = inputs.plummer(n, seed=1)
+        runs = [("h4 standard", 4, 0, 0.01), ("h4 time-symmetric", 4, 1, 0.01), ("h4 time-symmetric", 4, 2, 0.01),
+                ("h6", 6, 1, 0.2), ("h6", 6, 2, 0.2)]
+        for name, order, n_iter, eta in runs:
+            if n_iter == 0:
+                g = gravidy.Integrator(m, x, v, EPS, eta, precision="fp64")
+            else:
+                g = gravidy.Integrator6(m, x, v, EPS, eta, eta_init=eta if order == 4 else 0.001, order=order,
+                                        n_iter=n_iter)
+            E0 = sum(g.energy())
+            s0 = g.stats()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g.evolve(1.0)
+            wall = time.perf_counter() - t0
+            E1 = sum(g.energy())
+            s1 = g.stats()
+            g.close()
+            rows.append({"n": n, "scheme": name, "n_iter": max(n_iter, 1), "eta": eta, "s_per_nbu": wall,
+                         "dE_E": abs((E1 - E0) / E0), "block_steps": s1["block_steps"] - s0["block_steps"],
+                         "particle_steps": s1["particle_steps"] - s0["particle_steps"],
+                         "interactions": s1["interactions"] - s0["interactions"]})
+    # Kepler binary, G = M = 1, semi-major axis 1, e = 0.5, at pericentre at t = 0
+    e = 0.5
+    rp = 1.0 - e
+    vp = math.sqrt((1 + e) / rp)
+    mk = np.array([0.5, 0.5])
+    xk = np.array([[-rp / 2, 0, 0], [rp / 2, 0, 0]])
+    vk = np.array([[0, -vp / 2, 0], [0, vp / 2, 0]])
+    kepler = []
+    for order, dt in ((4, 2.0 ** -8), (6, 2.0 ** -7)):
+        nper = int(round(2 * math.pi / dt))
+        for n_iter in (1, 2):
+            with gravidy.Integrator6(mk, xk, vk, 0.0, 0.2, order=order, n_iter=n_iter, dt_min=dt, dt_max=dt) as g:
+                E0 = sum(g.energy())
+                err = []
+                for _ in range(8 * nper):
+                    g.step_block()
+                    err.append(sum(g.energy()) / E0 - 1)
+            means = np.array(err).reshape(8, nper).mean(axis=1)
+            drift = abs(np.polyfit(np.arange(8), means, 1)[0]) * 7 / abs(means.mean())
+            t1 = nper * dt
+            with gravidy.Integrator6(mk, xk, vk, 0.0, 0.2, order=order, n_iter=n_iter, dt_min=dt, dt_max=dt) as g:
+                g.evolve(t1)
+                fw = g.state()
+            with gravidy.Integrator6(mk, fw["x"], -fw["v"], 0.0, 0.2, order=order, n_iter=n_iter, dt_min=dt,
+                                     dt_max=dt) as g:
+                g.evolve(t1)
+                bk = g.state()
+            back = max(np.abs(bk["x"] - xk).max(), np.abs(bk["v"] + vk).max())
+            kepler.append({"order": order, "n_iter": n_iter, "dt": dt, "orbit_mean_dE_E": [float(q) for q in means],
+                           "drift_over_8_orbits_rel_to_mean": float(drift), "round_trip_one_orbit": float(back)})
+    print(json.dumps({"sweep": "timesym", "t_end": 1.0, "eps": EPS, "rows": rows, "kepler": kepler}))
+    return 0
+
+
 def profile_force(a):
     from paper_1702_00440_gb300 import gravidy, inputs
 
@@ -1026,7 +1102,8 @@ def main():
     if a.sweep:
         return {"force": sweep_force, "powerlaw": sweep_powerlaw, "accuracy": sweep_accuracy,
                 "ensemble": sweep_ensemble, "eta": sweep_eta, "soft": sweep_soft,
-                "lagrange": sweep_lagrange, "h6": sweep_h6}[a.sweep](a)
+                "lagrange": sweep_lagrange, "h6": sweep_h6,
+            "timesym": sweep_timesym}[a.sweep](a)
     if a.impl == "reference":
         return run_reference(a)
     return run_gravidy(a)

@@ -315,6 +315,25 @@ typedef struct gd_h6 gd_h6;
 int gd_h6_init(gd_h6 **out, int64_t n, const double *m, const double *x, const double *v,
                double eps, double eta, double eta_init, const gd_opts *opt);
 
+/* The same engine with a choice of scheme.  order 6 is the scheme above;
+ * order 4 is GraviDy's fourth-order scheme (Sec. 2.1: cubic predictor, force
+ * and jerk, Aarseth's step from the cubic interpolant) with the time-symmetric
+ * corrector of Hut, Makino & McMillan (1995), the fourth-order member of the
+ * nm08 family: with h = dt / 2,
+ *     v1 = v0 + h (a1 + a0) - (h^2 / 3) (j1 - j0),
+ *     x1 = x0 + h (v1 + v0) - (h^2 / 3) (a1 - a0);
+ * snap and crackle stay zero (gd_h6_force returns a zero snap).  n_iter in
+ * [1, 16] is the number of evaluation-correction passes per block step
+ * (P(EC)^n, Kokubo, Yoshinaga & Makino 1998): every pass but the last puts the
+ * corrected position and velocity and the new acceleration of each active
+ * particle in place of its prediction before the next evaluation.  With shared
+ * constant steps and n_iter >= 2 the map is time-reversible to round-off.
+ * gd_h6_init(...) is gd_h6_init_scheme(..., 6, 1, opt).  An order other than 4
+ * or 6, or n_iter outside [1, 16], is GD_EINVAL. */
+int gd_h6_init_scheme(gd_h6 **out, int64_t n, const double *m, const double *x, const double *v,
+                      double eps, double eta, double eta_init, int32_t order, int32_t n_iter,
+                      const gd_opts *opt);
+
 /* Advance until no particle's next time is <= t_end (as gd_evolve). */
 int gd_h6_evolve(gd_h6 *s, double t_end);
 

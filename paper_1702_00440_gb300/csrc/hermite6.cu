@@ -17,7 +17,17 @@
 // once per 78 cycles per scheduler, so this path is about 70x slower per pair
 // than the mixed fourth-order one; it is the accuracy-first form).
 //
-// Kernels per block step (three, captured as a CUDA graph of G steps):
+// The same engine runs the fourth-order scheme in its time-symmetric form
+// (order 4: the corrector of Hut, Makino & McMillan 1995,
+//     v1 = v0 + h (a1 + a0) - h^2 (j1 - j0) / 3,  x1 = x0 + h (v1 + v0) - h^2 (a1 - a0) / 3,
+// h = dt / 2, with the cubic predictor, force and jerk only, and Aarseth's
+// fourth-order step; snap and crackle stay zero), and either order can iterate
+// evaluation and correction n_iter times per block step (P(EC)^n, Kokubo,
+// Yoshinaga & Makino 1998): every pass but the last writes the corrected x, v
+// and the new a of each active particle over its prediction, so the next pass
+// sees them; with shared constant steps and n_iter >= 2 the map is reversible.
+//
+// Kernels per block step (1 + 2 n_iter, captured as a CUDA graph of G steps):
 //   k6_select_predict  predict every particle to T_cur, append the active ones
 //                      to the list (arrival order) and start the next-time
 //                      minimum over the inactive ones;
@@ -62,6 +72,8 @@ struct Ctrl6 {
 
 struct Dev6 {
     int n;
+    int order;                       // 4 (time-symmetric fourth order) or 6
+    int n_iter;                      // evaluation-correction passes per block step
     double dt_min, eps2, eta;
     long long dtau_max;
     double *m;
@@ -150,8 +162,11 @@ __global__ void k6_predict_all(Dev6 d, long long tick)
 // The pair term with r = x_j - x_i, u = v_j - v_i, w = a_j - a_i, s^2 = r^2 + eps^2:
 //   A0 = m r / s^3,  alpha = (r.u) / s^2,  A1 = m u / s^3 - 3 alpha A0,
 //   beta = (u.u + r.w) / s^2 + alpha^2,  A2 = m w / s^3 - 6 alpha A1 - 3 beta A0.
+// SNAP = false (order 4) evaluates A0 and A1 only and leaves the snap partials zero.
+template <bool SNAP>
 __global__ void __launch_bounds__(T6) k6_force(Dev6 d, int grid)
 {
+    constexpr int NQ = SNAP ? NC : 6;   // components reduced
     const int nact = min(d.ctrl->nact, d.n);
     if (nact <= 0) return;
     const Plan6 pl = plan6(nact, d.n, grid, d.cap);
@@ -162,7 +177,12 @@ __global__ void __launch_bounds__(T6) k6_force(Dev6 d, int grid)
         const int i = d.act[k];
         const double xi = d.xp[i], yi = d.xp[n + i], zi = d.xp[2 * n + i];
         const double ui = d.vp[i], vi = d.vp[n + i], wi = d.vp[2 * n + i];
-        const double pi = d.ap[i], qi = d.ap[n + i], ri = d.ap[2 * n + i];
+        double pi = 0.0, qi = 0.0, ri = 0.0;
+        if (SNAP) {
+            pi = d.ap[i];
+            qi = d.ap[n + i];
+            ri = d.ap[2 * n + i];
+        }
         double f[NC];
 #pragma unroll
         for (int q = 0; q < NC; q++) f[q] = 0.0;
@@ -171,13 +191,11 @@ __global__ void __launch_bounds__(T6) k6_force(Dev6 d, int grid)
             if (jj == i) continue;
             const double rx = d.xp[jj] - xi, ry = d.xp[n + jj] - yi, rz = d.xp[2 * n + jj] - zi;
             const double ux = d.vp[jj] - ui, uy = d.vp[n + jj] - vi, uz = d.vp[2 * n + jj] - wi;
-            const double wx = d.ap[jj] - pi, wy = d.ap[n + jj] - qi, wz = d.ap[2 * n + jj] - ri;
             const double ss = rx * rx + ry * ry + rz * rz + d.eps2;
             const double rinv = rsqrt(ss);
             const double rinv2 = rinv * rinv;
             const double mi3 = d.m[jj] * rinv * rinv2;
             const double alpha = (rx * ux + ry * uy + rz * uz) * rinv2;
-            const double beta = (ux * ux + uy * uy + uz * uz + rx * wx + ry * wy + rz * wz) * rinv2 + alpha * alpha;
             const double a0x = mi3 * rx, a0y = mi3 * ry, a0z = mi3 * rz;
             const double a1x = mi3 * ux - 3.0 * alpha * a0x, a1y = mi3 * uy - 3.0 * alpha * a0y,
                          a1z = mi3 * uz - 3.0 * alpha * a0z;
@@ -187,22 +205,27 @@ __global__ void __launch_bounds__(T6) k6_force(Dev6 d, int grid)
             f[3] += a1x;
             f[4] += a1y;
             f[5] += a1z;
-            f[6] += mi3 * wx - 6.0 * alpha * a1x - 3.0 * beta * a0x;
-            f[7] += mi3 * wy - 6.0 * alpha * a1y - 3.0 * beta * a0y;
-            f[8] += mi3 * wz - 6.0 * alpha * a1z - 3.0 * beta * a0z;
+            if (SNAP) {
+                const double wx = d.ap[jj] - pi, wy = d.ap[n + jj] - qi, wz = d.ap[2 * n + jj] - ri;
+                const double beta =
+                    (ux * ux + uy * uy + uz * uz + rx * wx + ry * wy + rz * wz) * rinv2 + alpha * alpha;
+                f[6] += mi3 * wx - 6.0 * alpha * a1x - 3.0 * beta * a0x;
+                f[7] += mi3 * wy - 6.0 * alpha * a1y - 3.0 * beta * a0y;
+                f[8] += mi3 * wz - 6.0 * alpha * a1z - 3.0 * beta * a0z;
+            }
         }
         // fixed pairwise tree over the CTA's threads
         __syncthreads();  // red[] of the previous item has been read
 #pragma unroll
-        for (int q = 0; q < NC; q++) red[q][t] = f[q];
+        for (int q = 0; q < NQ; q++) red[q][t] = f[q];
         __syncthreads();
         for (int h = T6 / 2; h >= 1; h >>= 1) {
             if (t < h)
 #pragma unroll
-                for (int q = 0; q < NC; q++) red[q][t] += red[q][t + h];
+                for (int q = 0; q < NQ; q++) red[q][t] += red[q][t + h];
             __syncthreads();
         }
-        if (t < NC) d.part[((long long)sidx * NC + t) * nact + k] = red[t][0];
+        if (t < NC) d.part[((long long)sidx * NC + t) * nact + k] = t < NQ ? red[t][0] : 0.0;
     }
 }
 
@@ -246,7 +269,44 @@ __device__ __forceinline__ long long quantise6(const Dev6 &d, double dt_new, lon
 
 __device__ __forceinline__ double norm3(double x, double y, double z) { return sqrt(x * x + y * y + z * z); }
 
-// Correct active slot k at block time T with its new force a1, jerk j1, snap s1.
+// Corrected position x1 and velocity v1 (component q) of particle i over dt
+// from its state at its own time and the new a1, j1 (and s1 at order 6).
+__device__ __forceinline__ void corrected(const Dev6 &d, int o, double dt, double a1, double j1, double s1,
+                                          double &x1, double &v1)
+{
+    const double h = 0.5 * dt, h2 = h * h;
+    const double x0 = d.x[o], v0 = d.v[o], a0 = d.a[o], j0 = d.j[o];
+    if (d.order == 6) {
+        const double h3 = h2 * h, s0 = d.s[o];
+        v1 = v0 + h * (a1 + a0) - 0.4 * h2 * (j1 - j0) + h3 * (s1 + s0) / 15.0;
+        x1 = x0 + h * (v1 + v0) - 0.4 * h2 * (a1 - a0) + h3 * (j1 + j0) / 15.0;
+    } else {
+        v1 = v0 + h * (a1 + a0) - h2 * (j1 - j0) / 3.0;
+        x1 = x0 + h * (v1 + v0) - h2 * (a1 - a0) / 3.0;
+    }
+}
+
+// A pass that is not the last: the corrected x, v and the new a of active slot k
+// replace the particle's prediction (the next pass evaluates against them).
+__device__ void trial6(const Dev6 &d, int k, long long T, const double a1[3], const double j1[3],
+                       const double s1[3], int &bad)
+{
+    const int n = d.n;
+    const int i = d.act[k];
+    const double dt = (double)(T - d.tau[i]) * d.dt_min;
+    for (int q = 0; q < 3; q++) {
+        const int o = q * n + i;
+        double x1, v1;
+        corrected(d, o, dt, a1[q], j1[q], s1[q], x1, v1);
+        if (!isfinite(x1) || !isfinite(v1)) bad = 1;
+        d.xp[o] = x1;
+        d.vp[o] = v1;
+        d.ap[o] = a1[q];
+    }
+}
+
+// Correct active slot k at block time T with its new force a1, jerk j1, snap s1
+// (zero at order 4), take its new step and commit the state.
 __device__ void correct6(const Dev6 &d, int k, long long T, const double a1[3], const double j1[3],
                          const double s1[3], long long &tn_out, int &bad)
 {
@@ -254,35 +314,53 @@ __device__ void correct6(const Dev6 &d, int k, long long T, const double a1[3], 
     const int i = d.act[k];
     const long long dtick = T - d.tau[i];
     const double dt = (double)dtick * d.dt_min;
-    const double h = 0.5 * dt, h2 = h * h, h3 = h2 * h, h5 = h3 * h2;
-    double crk[3], pop[3], a5[3];
-    for (int q = 0; q < 3; q++) {
-        const int o = q * n + i;
-        const double a0 = d.a[o], j0 = d.j[o], s0 = d.s[o];
-        // the quintic interpolant on [-h, h] and its derivatives at +h
-        const double Am = 0.5 * (a1[q] - a0), Jp = 0.5 * (j1[q] + j0), Jm = 0.5 * (j1[q] - j0);
-        const double Sp = 0.5 * (s1[q] + s0), Sm = 0.5 * (s1[q] - s0);
-        const double c4 = (Sp * h - Jm) / (8.0 * h3);
-        const double c5 = (Sm * h2 - 3.0 * Jp * h + 3.0 * Am) / (8.0 * h5);
-        const double c3 = (0.5 * (Jp * h - Am) - 2.0 * c5 * h5) / h3;
-        crk[q] = 6.0 * c3 + 24.0 * c4 * h + 60.0 * c5 * h2;
-        pop[q] = 24.0 * c4 + 120.0 * c5 * h;
-        a5[q] = 120.0 * c5;
-        // time-symmetric sixth-order correction
-        const double x0 = d.x[o], v0 = d.v[o];
-        const double v1 = v0 + h * (a1[q] + a0) - 0.4 * h2 * (j1[q] - j0) + h3 * (s1[q] + s0) / 15.0;
-        const double x1 = x0 + h * (v1 + v0) - 0.4 * h2 * (a1[q] - a0) + h3 * (j1[q] + j0) / 15.0;
-        if (!isfinite(x1) || !isfinite(v1)) bad = 1;
-        d.x[o] = x1;
-        d.v[o] = v1;
+    double crk[3] = {0.0, 0.0, 0.0}, x1[3], v1[3];
+    double dt_new;
+    if (d.order == 6) {
+        const double h = 0.5 * dt, h2 = h * h, h3 = h2 * h, h5 = h3 * h2;
+        double pop[3], a5[3];
+        for (int q = 0; q < 3; q++) {
+            const int o = q * n + i;
+            const double a0 = d.a[o], j0 = d.j[o], s0 = d.s[o];
+            // the quintic interpolant on [-h, h] and its derivatives at +h
+            const double Am = 0.5 * (a1[q] - a0), Jp = 0.5 * (j1[q] + j0), Jm = 0.5 * (j1[q] - j0);
+            const double Sp = 0.5 * (s1[q] + s0), Sm = 0.5 * (s1[q] - s0);
+            const double c4 = (Sp * h - Jm) / (8.0 * h3);
+            const double c5 = (Sm * h2 - 3.0 * Jp * h + 3.0 * Am) / (8.0 * h5);
+            const double c3 = (0.5 * (Jp * h - Am) - 2.0 * c5 * h5) / h3;
+            crk[q] = 6.0 * c3 + 24.0 * c4 * h + 60.0 * c5 * h2;
+            pop[q] = 24.0 * c4 + 120.0 * c5 * h;
+            a5[q] = 120.0 * c5;
+            corrected(d, o, dt, a1[q], j1[q], s1[q], x1[q], v1[q]);
+        }
+        const double na = norm3(a1[0], a1[1], a1[2]), nj = norm3(j1[0], j1[1], j1[2]);
+        const double ns = norm3(s1[0], s1[1], s1[2]), nc = norm3(crk[0], crk[1], crk[2]);
+        const double np = norm3(pop[0], pop[1], pop[2]), nq = norm3(a5[0], a5[1], a5[2]);
+        dt_new = d.eta * pow((na * ns + nj * nj) / (nc * nq + np * np), 1.0 / 6.0);
+    } else {
+        // second and third derivative of the cubic interpolant of (a, jerk) at
+        // both ends, taken to the end of the step for Aarseth's criterion
+        const double dt2 = dt * dt, dt3 = dt2 * dt;
+        double a2e[3], a3[3];
+        for (int q = 0; q < 3; q++) {
+            const int o = q * n + i;
+            const double a0 = d.a[o], j0 = d.j[o];
+            const double da = a0 - a1[q];
+            const double a2 = (-6.0 * da - dt * (4.0 * j0 + 2.0 * j1[q])) / dt2;
+            a3[q] = (12.0 * da + 6.0 * dt * (j0 + j1[q])) / dt3;
+            a2e[q] = a2 + dt * a3[q];
+            corrected(d, o, dt, a1[q], j1[q], 0.0, x1[q], v1[q]);
+        }
+        const double na = norm3(a1[0], a1[1], a1[2]), nj = norm3(j1[0], j1[1], j1[2]);
+        const double n2 = norm3(a2e[0], a2e[1], a2e[2]), n3 = norm3(a3[0], a3[1], a3[2]);
+        dt_new = sqrt(d.eta * (na * n2 + nj * nj) / (nj * n3 + n2 * n2));
     }
-    const double na = norm3(a1[0], a1[1], a1[2]), nj = norm3(j1[0], j1[1], j1[2]);
-    const double ns = norm3(s1[0], s1[1], s1[2]), nc = norm3(crk[0], crk[1], crk[2]);
-    const double np = norm3(pop[0], pop[1], pop[2]), nq = norm3(a5[0], a5[1], a5[2]);
-    const double dt_new = d.eta * pow((na * ns + nj * nj) / (nc * nq + np * np), 1.0 / 6.0);
     const long long dtau = quantise6(d, dt_new, d.dtau[i], T);
     for (int q = 0; q < 3; q++) {
         const int o = q * n + i;
+        if (!isfinite(x1[q]) || !isfinite(v1[q])) bad = 1;
+        d.x[o] = x1[q];
+        d.v[o] = v1[q];
         d.a[o] = a1[q];
         d.j[o] = j1[q];
         d.s[o] = s1[q];
@@ -294,7 +372,10 @@ __device__ void correct6(const Dev6 &d, int k, long long T, const double a1[3], 
     tn_out = T + dtau;
 }
 
-__global__ void __launch_bounds__(T6) k6_correct(Dev6 d, int grid)
+// commit = 0: a pass that is not the last (trial6 per slot, no bookkeeping);
+// commit = 1: correction, new steps, and the last CTA turns the minimum into
+// the next block time.
+__global__ void __launch_bounds__(T6) k6_correct(Dev6 d, int grid, int commit)
 {
     Ctrl6 *ctrl = d.ctrl;
     const int nact = min(ctrl->nact, d.n);
@@ -308,15 +389,20 @@ __global__ void __launch_bounds__(T6) k6_correct(Dev6 d, int grid)
     for (int k = blockIdx.x * T6 + threadIdx.x; k < nact; k += ncta * T6) {
         double f[NC];
         for (int q = 0; q < NC; q++) f[q] = part_sum6(d, nact, pl.S, q, k);
+        if (!commit) {
+            trial6(d, k, T, f, f + 3, f + 6, bad);
+            continue;
+        }
         long long tn;
         correct6(d, k, T, f, f + 3, f + 6, tn, bad);
         mn = tn < mn ? tn : mn;
     }
+    if (bad) set_err6(ctrl, GD_ENONFINITE);
+    if (!commit) return;
     for (int o = 16; o > 0; o >>= 1) {
         const long long w = __shfl_xor_sync(0xffffffffu, mn, o);
         mn = w < mn ? w : mn;
     }
-    if (bad) set_err6(ctrl, GD_ENONFINITE);
     if ((threadIdx.x & 31) == 0 && mn != LLONG_MAX) atomicMin((unsigned long long *)&ctrl->T_acc, (unsigned long long)mn);
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -331,7 +417,7 @@ __global__ void __launch_bounds__(T6) k6_correct(Dev6 d, int grid)
             ctrl->T_acc = LLONG_MAX;
             ctrl->nblock += 1;
             ctrl->nsteps += nact;
-            ctrl->interactions += (double)nact * (double)d.n;
+            ctrl->interactions += (double)d.n_iter * (double)nact * (double)d.n;
             ctrl->nact = 0;
             ctrl->done = 0;
         }
@@ -500,21 +586,42 @@ int usable6(gd_h6 *s)
     return GD_OK;
 }
 
+// kernel launches per block step
+long long per_step6(const gd_h6 *s) { return 1 + 2LL * s->d.n_iter; }
+
+void launch_force6(gd_h6 *s)
+{
+    if (s->d.order == 6)
+        k6_force<true><<<s->grid, T6, 0, s->stream>>>(s->d, s->grid);
+    else
+        k6_force<false><<<s->grid, T6, 0, s->stream>>>(s->d, s->grid);
+    s->launches += 1;
+}
+
+// the n_iter evaluation-correction passes of the current list; the last commits
+void passes6(gd_h6 *s)
+{
+    for (int pass = 1; pass <= s->d.n_iter; pass++) {
+        launch_force6(s);
+        k6_correct<<<s->grid, T6, 0, s->stream>>>(s->d, s->grid, pass == s->d.n_iter ? 1 : 0);
+        s->launches += 1;
+    }
+}
+
 void step6(gd_h6 *s)
 {
     const int gsel = (s->d.n + T6 - 1) / T6;
     k6_select_predict<<<gsel, T6, 0, s->stream>>>(s->d);
-    k6_force<<<s->grid, T6, 0, s->stream>>>(s->d, s->grid);
-    k6_correct<<<s->grid, T6, 0, s->stream>>>(s->d, s->grid);
-    s->launches += 3;
+    s->launches += 1;
+    passes6(s);
 }
 
 // force of the listed slots into fsum (plan of the current list)
 void force_sum6(gd_h6 *s, int nact)
 {
-    k6_force<<<s->grid, T6, 0, s->stream>>>(s->d, s->grid);
+    launch_force6(s);
     k6_sum<<<(nact * NC + 255) / 256, 256, 0, s->stream>>>(s->d, s->grid);
-    s->launches += 2;
+    s->launches += 1;
 }
 
 // AoS host (n x 3) -> device planes, through the pinned stage
@@ -585,11 +692,13 @@ void gd_h6_free(gd_h6 *s)
 
 const char *gd_h6_last_error(const gd_h6 *s) { return s ? s->err.c_str() : g_h6_err.c_str(); }
 
-int gd_h6_init(gd_h6 **out, int64_t n, const double *m, const double *x, const double *v, double eps, double eta,
-               double eta_init, const gd_opts *opt)
+int gd_h6_init_scheme(gd_h6 **out, int64_t n, const double *m, const double *x, const double *v, double eps,
+                      double eta, double eta_init, int32_t order, int32_t n_iter, const gd_opts *opt)
 {
     if (!out) return fail6(nullptr, GD_EINVAL, "out is required");
     *out = nullptr;
+    if (order != 4 && order != 6) return fail6(nullptr, GD_EINVAL, "order must be 4 or 6");
+    if (n_iter < 1 || n_iter > 16) return fail6(nullptr, GD_EINVAL, "n_iter must be in [1, 16]");
     gd_opts o;
     gd_opts_default(&o);
     if (opt) o = *opt;
@@ -624,10 +733,12 @@ int gd_h6_init(gd_h6 **out, int64_t n, const double *m, const double *x, const d
     }
     int sms = 0, occ = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k6_force, T6, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k6_force<true>, T6, 0);
     s->grid = std::max(1, sms * std::max(1, occ));
     Dev6 &d = s->d;
     d.n = (int)n;
+    d.order = order;
+    d.n_iter = n_iter;
     d.dt_min = o.dt_min;
     d.eps2 = eps * eps;
     d.eta = eta;
@@ -664,9 +775,10 @@ int gd_h6_init(gd_h6 **out, int64_t n, const double *m, const double *x, const d
     if (e != cudaSuccess) return bail(fail6(s, GD_ECUDA, "upload"));
     int rc;
     if ((rc = upload6(s, d.x, x)) || (rc = upload6(s, d.v, v))) return bail(rc);
-    // pass 1: force and jerk (predicted accelerations zero), pass 2: snap
+    // pass 1: force and jerk (predicted accelerations zero), pass 2 (order 6): snap
     const int gi = (int)((n + 255) / 256);
-    for (int pass = 1; pass <= 2; pass++) {
+    const int npass = order == 6 ? 2 : 1;
+    for (int pass = 1; pass <= npass; pass++) {
         k6_predict_all<<<gi, 256, 0, s->stream>>>(d, 0);
         k6_iota<<<gi, 256, 0, s->stream>>>(d.act, (int)n);
         k6_set_list<<<1, 1, 0, s->stream>>>(d, 0, (int)n);
@@ -682,11 +794,17 @@ int gd_h6_init(gd_h6 **out, int64_t n, const double *m, const double *x, const d
     // the bookkeeping of the two passes is not a block step
     s->h_ctrl->nblock = 0;
     s->h_ctrl->nsteps = 0;
-    s->h_ctrl->interactions = 2.0 * (double)n * (double)n;
+    s->h_ctrl->interactions = (double)npass * (double)n * (double)n;
     CK6(cudaMemcpyAsync(d.ctrl, s->h_ctrl, sizeof(Ctrl6), cudaMemcpyHostToDevice, s->stream));
     if ((rc = sync6(s))) return bail(rc);
     *out = s;
     return GD_OK;
+}
+
+int gd_h6_init(gd_h6 **out, int64_t n, const double *m, const double *x, const double *v, double eps, double eta,
+               double eta_init, const gd_opts *opt)
+{
+    return gd_h6_init_scheme(out, n, m, x, v, eps, eta, eta_init, 6, 1, opt);
 }
 
 int gd_h6_step_block(gd_h6 *s, double *t_out, int64_t *nact_out)
@@ -715,7 +833,7 @@ int gd_h6_evolve(gd_h6 *s, double t_end)
     s->launches += 1;
     for (;;) {
         CK6(cudaGraphLaunch(s->graph, s->stream));
-        s->launches += 3LL * G6;
+        s->launches += per_step6(s) * G6;
         if ((rc = sync6(s))) return rc;
         if (s->h_ctrl->T_cur > tick_end) break;
     }
@@ -738,10 +856,10 @@ int gd_h6_replay_step(gd_h6 *s, int64_t tick_next, const int32_t *idx, int64_t n
     const int gi = (d.n + 255) / 256;
     k6_predict_all<<<gi, 256, 0, s->stream>>>(d, tick_next);
     k6_set_list<<<1, 1, 0, s->stream>>>(d, tick_next, (int)nact);
-    k6_force<<<s->grid, T6, 0, s->stream>>>(d, s->grid);
-    k6_correct<<<s->grid, T6, 0, s->stream>>>(d, s->grid);
+    s->launches += 2;
+    passes6(s);
     k6_resync<<<1, 1024, 0, s->stream>>>(d);
-    s->launches += 5;
+    s->launches += 1;
     CK6(cudaGetLastError());
     return sync6(s);
 }

@@ -30,7 +30,7 @@ EXPORTS = (
     "gd_cluster_info", "gd_cluster_time",
     "gd_ens_init", "gd_ens_evolve", "gd_ens_step_block", "gd_ens_energy", "gd_ens_get_state",
     "gd_ens_get_stats", "gd_ens_free", "gd_ens_last_error",
-    "gd_h6_init", "gd_h6_evolve", "gd_h6_step_block", "gd_h6_replay_step", "gd_h6_force", "gd_h6_energy",
+    "gd_h6_init", "gd_h6_init_scheme", "gd_h6_evolve", "gd_h6_step_block", "gd_h6_replay_step", "gd_h6_force", "gd_h6_energy",
     "gd_h6_get_state", "gd_h6_get_stats", "gd_h6_free", "gd_h6_last_error",
 )
 
@@ -124,6 +124,7 @@ def load(build_if_missing: bool = True):
             "gd_ens_free": (None, [P]),
             "gd_ens_last_error": (ctypes.c_char_p, [P]),
             "gd_h6_init": (ctypes.c_int, [P, I64, P, P, P, D, D, D, P]),
+            "gd_h6_init_scheme": (ctypes.c_int, [P, I64, P, P, P, D, D, D, I32, I32, P]),
             "gd_h6_evolve": (ctypes.c_int, [P, D]),
             "gd_h6_step_block": (ctypes.c_int, [P, P, P]),
             "gd_h6_replay_step": (ctypes.c_int, [P, I64, P, I64]),
@@ -475,9 +476,11 @@ def _check_h6(rc, h=None):
 
 
 class Integrator6:
-    """gd_h6: the sixth-order Hermite block-step integrator (FP64)."""
+    """gd_h6: the time-symmetric Hermite block-step integrators (FP64): order 6
+    (sixth-order Hermite) or order 4 (the fourth-order scheme with the
+    time-symmetric corrector), n_iter evaluation-correction passes per step."""
 
-    def __init__(self, m, x, v, eps, eta, eta_init=0.001, **opts):
+    def __init__(self, m, x, v, eps, eta, eta_init=0.001, order=6, n_iter=1, **opts):
         lib = load()
         m = np.ascontiguousarray(np.asarray(m, dtype=np.float64))
         self.n = n = m.shape[0]
@@ -487,8 +490,8 @@ class Integrator6:
         o = make_opts(**opts)
         self.dt_min = o.dt_min
         h = ctypes.c_void_p()
-        _check_h6(lib.gd_h6_init(ctypes.byref(h), n, _p(m), _p(x), _p(v), float(eps), float(eta), float(eta_init),
-                                 ctypes.byref(o)))
+        _check_h6(lib.gd_h6_init_scheme(ctypes.byref(h), n, _p(m), _p(x), _p(v), float(eps), float(eta),
+                                        float(eta_init), int(order), int(n_iter), ctypes.byref(o)))
         self._h = h
 
     def close(self):

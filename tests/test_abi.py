@@ -73,6 +73,21 @@ def test_gd_init_rejects_bad_arguments_on_the_host(case, order):
     assert msg
 
 
+@pytest.mark.parametrize("order,n_iter", [(5, 1), (2, 1), (4, 0), (6, 17), (6, -1)])
+def test_h6_scheme_rejects_bad_order_and_passes_on_the_host(order, n_iter):
+    lib = gravidy.load()
+    n = 4
+    m = np.full(n, 0.25)
+    x = np.arange(12, dtype=float).reshape(4, 3)
+    v = np.zeros((4, 3))
+    h = ctypes.c_void_p()
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    rc = lib.gd_h6_init_scheme(ctypes.byref(h), n, p(m), p(x), p(v), 1e-4, 0.01, 0.01, order, n_iter, None)
+    assert rc == gravidy.GD_EINVAL
+    assert not h.value
+    assert lib.gd_h6_last_error(None).decode()
+
+
 def test_opts_defaults():
     o = gravidy.make_opts()
     assert o.dt_min == 2.0 ** -22 and o.dt_max == 0.125 and o.precision == gravidy.GD_MIXED

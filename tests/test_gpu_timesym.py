@@ -1,0 +1,123 @@
+"""The time-symmetric schemes of the gd_h6 engine on the GPU (order 4 with the
+time-symmetric corrector, and P(EC)^n passes of either order) against the
+oracle, through the C ABI: force and jerk of the order-4 kernel, replayed and
+free-running block schedules, and reversibility of the two-pass map on a Kepler
+orbit with shared constant steps."""
+import numpy as np
+import pytest
+
+import oracle
+from kepler import kepler_ic
+from paper_1702_00440_gb300 import gravidy, inputs
+
+pytestmark = pytest.mark.gpu
+
+EPS = 1e-4
+ETA4 = 0.01
+DT_MIN = 2.0 ** -22
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    gravidy.load()
+    oracle.build()
+
+
+@pytest.mark.parametrize("nact", [1, 300, 2000])
+def test_order4_force_and_jerk_zero_snap(nact):
+    n = 2000
+    m, x, v = inputs.plummer(n, seed=41, masses=inputs.power_law_masses(n, seed=41))
+    idx = inputs.random_subset(n, nact, seed=nact) if nact < n else np.arange(n, dtype=np.int32)
+    with gravidy.Integrator6(m, x, v, EPS, ETA4, eta_init=ETA4, order=4) as g:
+        acc, jerk, snap = g.force(0, idx)
+        st = g.state()
+    a, j = oracle.force(m, x, v, EPS, idx)
+    for got, want in ((acc, a), (jerk, j)):
+        assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
+    assert np.all(snap == 0.0)
+    assert np.all(st["s"] == 0.0) and np.all(st["c"] == 0.0)
+    a_all, _ = oracle.force(m, x, v, EPS)
+    assert np.abs(st["a"] - a_all).max() <= 1e-11 * np.abs(a_all).max()
+
+
+@pytest.mark.parametrize("order,n_iter", [(4, 1), (4, 2), (6, 2), (4, 3)])
+def test_replayed_schedule(order, n_iter):
+    """The oracle's free-running schedule replayed on the GPU: same block times
+    and lists, states equal to round-off growth."""
+    m, x, v = inputs.plummer(256, seed=3)
+    eta, eta_init = (ETA4, ETA4) if order == 4 else (0.2, 0.001)
+    sim = oracle.Sim6(m, x, v, EPS, eta, eta_init=eta_init, order=order, n_iter=n_iter)
+    rec = []
+    while True:
+        tick, idx = sim.step()
+        rec.append((tick, idx))
+        if tick >= int(0.25 / DT_MIN):
+            break
+    so = sim.state()
+    sto = sim.stats()
+    with gravidy.Integrator6(m, x, v, EPS, eta, eta_init=eta_init, order=order, n_iter=n_iter) as g:
+        for tick, idx in rec:
+            g.replay_step(tick, idx)
+        st = g.state()
+        stats = g.stats()
+    dx = np.abs(st["x"] - so["x"]).max()
+    dv = np.abs(st["v"] - so["v"]).max()
+    print("order %d n_iter %d replay n=256: %d steps, max|dx| %.2e max|dv| %.2e, dtau agree %.4f"
+          % (order, n_iter, len(rec), dx, dv, np.mean(st["dtau"] == so["dtau"])))
+    assert stats["block_steps"] == len(rec)
+    assert stats["interactions"] == sto["interactions"]
+    assert (st["tau"] == so["tau"]).all()
+    assert dx < 1e-9 and dv < 1e-9
+    assert np.mean(st["dtau"] == so["dtau"]) > 0.99
+
+
+@pytest.mark.parametrize("n_iter", [1, 2])
+def test_order4_free_run_n512_to_t1(n_iter):
+    m, x, v = inputs.plummer(512, seed=1)
+    sim = oracle.Sim6(m, x, v, EPS, ETA4, eta_init=ETA4, order=4, n_iter=n_iter)
+    E0 = sum(sim.energy())
+    sim.evolve(1.0)
+    de_or = abs(sum(sim.energy()) / E0 - 1)
+    so = sim.stats()
+    with gravidy.Integrator6(m, x, v, EPS, ETA4, eta_init=ETA4, order=4, n_iter=n_iter) as g:
+        G0 = sum(g.energy())
+        g.evolve(1.0)
+        de = abs(sum(g.energy()) / G0 - 1)
+        st = g.state()
+        stats = g.stats()
+    print("order 4 n_iter %d free n=512 t=1: blocks %d/%d psteps %d/%d |dE/E| %.3e/%.3e"
+          % (n_iter, stats["block_steps"], so["nblock"], stats["particle_steps"], so["nsteps"], de, de_or))
+    assert (st["tau"] == int(1.0 / DT_MIN)).all()
+    assert abs(stats["block_steps"] - so["nblock"]) <= 0.01 * so["nblock"]
+    assert de <= 2 * de_or + 1e-12
+
+
+def _kepler_round_trip(order, n_iter, dt=2.0 ** -8, t=6.0):
+    """Shared constant steps (dt_min = dt_max = dt) forward to t, velocities
+    reversed, forward to t again; returns (distance from the start, the forward
+    state, the forward oracle state)."""
+    m, x, v = kepler_ic(0.5)
+    opts = dict(dt_min=dt, dt_max=dt)
+    with gravidy.Integrator6(m, x, v, 0.0, 0.2, order=order, n_iter=n_iter, **opts) as g:
+        g.evolve(t)
+        fw = g.state()
+    with gravidy.Integrator6(m, fw["x"], -fw["v"], 0.0, 0.2, order=order, n_iter=n_iter, **opts) as g:
+        g.evolve(t)
+        bk = g.state()
+    sim = oracle.Sim6(m, x, v, 0.0, 0.2, dt_min=dt, dt_max=dt, order=order, n_iter=n_iter)
+    sim.evolve(t)
+    return max(np.abs(bk["x"] - x).max(), np.abs(bk["v"] + v).max()), fw, sim.state()
+
+
+@pytest.mark.parametrize("order", [4, 6])
+def test_two_passes_are_reversible_on_the_gpu(order):
+    one, fw1, so1 = _kepler_round_trip(order, 1)
+    two, fw2, so2 = _kepler_round_trip(order, 2)
+    print("GPU order %d round trip: one pass %.2e, two passes %.2e; forward vs oracle %.2e / %.2e"
+          % (order, one, two, np.abs(fw1["x"] - so1["x"]).max(), np.abs(fw2["x"] - so2["x"]).max()))
+    assert two < 1e-12
+    assert one > 30 * two
+    for fw, so in ((fw1, so1), (fw2, so2)):
+        assert (fw["tau"] == so["tau"]).all()
+        assert np.abs(fw["x"] - so["x"]).max() < 1e-11
+        assert np.abs(fw["v"] - so["v"]).max() < 1e-11
