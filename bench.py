@@ -70,7 +70,7 @@ def _args():
                    help="profiling hook: initialise an N-particle Plummer sphere (one full force evaluation), "
                         "evaluate all N once more, print nothing and exit")
     p.add_argument("--sweep", choices=["force", "powerlaw", "accuracy", "ensemble", "eta", "soft", "lagrange", "h6",
-                                          "timesym"],
+                                          "timesym", "collapse"],
                    help="extra measurements, one JSON line each (not the benchmark line): force = "
                         "full evaluations N=2^10..2^20 and N=2^20 with active sets 1..2^20; powerlaw = "
                         "N=262144 power-law masses to t=1/8 (active-set histogram, interactions/s per "
@@ -81,8 +81,13 @@ def _args():
                         "eps=1e-5..1e-2 at eta=0.01; lagrange = Lagrange radii of N=16384 every 1/2 unit to t=8; "
                         "h6 = sixth- vs fourth-order Hermite: cost and |dE/E| to t=1, and the snap kernel's rate; "
                         "timesym = the time-symmetric schemes (order 4 and 6, one and two passes): cost and |dE/E| "
-                        "to t=1, energy drift and reversibility on a Kepler orbit with shared constant steps")
+                        "to t=1, energy drift and reversibility on a Kepler orbit with shared constant steps; "
+                        "collapse = core collapse of an N=1024 Plummer sphere (Lagrange radii, |dE/E|)")
     p.add_argument("--ens-t", type=float, default=0.125)
+    p.add_argument("--collapse-trh", type=float, default=30.0,
+                   help="--sweep collapse: stop at this many half-mass relaxation times")
+    p.add_argument("--collapse-wall", type=float, default=240.0,
+                   help="--sweep collapse: stop after this many seconds of wall time")
     p.add_argument("--profile-force-h6", type=int, default=0, metavar="N",
                    help="profiling hook: initialise an N-particle Plummer sphere on the sixth-order path (two "
                         "force/jerk/snap evaluations), evaluate all N once more, print nothing and exit")
@@ -913,6 +918,69 @@ def sweep_lagrange(a):
     return 0
 
 
+def density_centre(m, x, k=6):
+    """Casertano & Hut (1985) density centre: positions weighted by the local
+    density estimate m_i / r_k^3 (r_k the distance to the k-th nearest neighbour)."""
+    d2 = ((x[:, None, :] - x[None, :, :]) ** 2).sum(-1)
+    rk = np.sqrt(np.partition(d2, k, axis=1)[:, k])
+    rho = m / rk ** 3
+    return (rho[:, None] * x).sum(0) / rho.sum()
+
+
+def lagrange_radii(m, x, fractions, centre):
+    r = np.linalg.norm(x - centre, axis=1)
+    o = np.argsort(r)
+    cm = np.cumsum(m[o]) / m.sum()
+    return [float(r[o][min(np.searchsorted(cm, f), len(r) - 1)]) for f in fractions]
+
+
+def half_mass_relaxation_time(m, x):
+    """t_rh = 0.138 (N r_h^3 / (G <m>))^(1/2) / ln(0.1 N), r_h the half-mass radius
+    about the centre of mass (the paper's definition, Sec. 4.2; G = 1)."""
+    n = len(m)
+    c = (m[:, None] * x).sum(0) / m.sum()
+    r_h = lagrange_radii(m, x, [0.5], c)[0]
+    return 0.138 * math.sqrt(n * r_h ** 3 / m.mean()) / math.log(0.1 * n), r_h
+
+
+COLLAPSE_FRACTIONS = [0.005, 0.01, 0.02, 0.05, 0.1, 0.25, 0.5, 0.75, 0.9]
+
+
+def sweep_collapse(a):
+    """Core collapse of an equal-mass Plummer sphere (N = 1024, seed 1, eps =
+    1e-4, eta = 0.01, mixed path; the paper's single-mass experiment, Sec. 4.2,
+    at a size one GPU finishes in minutes): Lagrange radii about the density
+    centre, |dE/E|, block steps and wall time every 4 N-body units, until
+    t = --collapse-trh half-mass relaxation times or --collapse-wall seconds of
+    wall time."""
+    from paper_1702_00440_gb300 import gravidy, inputs
+
+    n = 1024
+    m, x, v = inputs.plummer(n, seed=1)
+    trh, rh = half_mass_relaxation_time(m, x)
+    t_max = a.collapse_trh * trh
+    g = gravidy.Integrator(m, x, v, EPS, ETA, precision="mixed", autotune=True)
+    E0 = sum(g.energy())
+    rows = [{"t": 0.0, "radii": lagrange_radii(m, x, COLLAPSE_FRACTIONS, density_centre(m, x)), "dE_E": 0.0,
+             "block_steps": 0, "wall_s": 0.0}]
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        k += 1
+        t = 4.0 * k
+        if t > t_max or time.perf_counter() - t0 > a.collapse_wall:
+            break
+        g.evolve(t)
+        xs = g.state()["x"]
+        rows.append({"t": t, "radii": lagrange_radii(m, xs, COLLAPSE_FRACTIONS, density_centre(m, xs)),
+                     "dE_E": abs((sum(g.energy()) - E0) / E0), "block_steps": g.stats()["block_steps"],
+                     "wall_s": time.perf_counter() - t0})
+    g.close()
+    print(json.dumps({"sweep": "collapse", "n": n, "eps": EPS, "eta": ETA, "t_rh": trh, "r_h": rh,
+                      "fractions": COLLAPSE_FRACTIONS, "rows": rows}))
+    return 0
+
+
 def sweep_h6(a):
     """Sixth- against fourth-order Hermite on Plummer N = 1024 and 4096 (seed 1,
     eps = 1e-4) to t = 1: wall time per N-body unit and |dE/E| for the FP64
@@ -1103,7 +1171,7 @@ def main():
         return {"force": sweep_force, "powerlaw": sweep_powerlaw, "accuracy": sweep_accuracy,
                 "ensemble": sweep_ensemble, "eta": sweep_eta, "soft": sweep_soft,
                 "lagrange": sweep_lagrange, "h6": sweep_h6,
-            "timesym": sweep_timesym}[a.sweep](a)
+            "timesym": sweep_timesym, "collapse": sweep_collapse}[a.sweep](a)
     if a.impl == "reference":
         return run_reference(a)
     return run_gravidy(a)
