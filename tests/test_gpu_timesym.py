@@ -121,3 +121,45 @@ def test_two_passes_are_reversible_on_the_gpu(order):
         assert (fw["tau"] == so["tau"]).all()
         assert np.abs(fw["x"] - so["x"]).max() < 1e-11
         assert np.abs(fw["v"] - so["v"]).max() < 1e-11
+
+
+@pytest.mark.parametrize("order", [4, 6])
+def test_single_free_particle_with_the_most_passes(order):
+    """One particle (no force): every pass leaves x + v t, exactly, to t = 1/4
+    with the largest pass count."""
+    m = np.array([1.0])
+    x = np.array([[0.25, -0.5, 0.125]])
+    v = np.array([[0.5, 0.25, -1.0]])
+    with gravidy.Integrator6(m, x, v, EPS, 0.01, order=order, n_iter=16) as g:
+        g.evolve(0.25)
+        st = g.state()
+        stats = g.stats()
+    assert (st["tau"] == int(0.25 / DT_MIN)).all()
+    assert np.array_equal(st["x"], x + 0.25 * v)
+    assert np.array_equal(st["v"], v)
+    assert stats["interactions"] == (1 if order == 4 else 2) + 16 * stats["particle_steps"]
+
+
+def test_three_bodies_sixteen_passes_replay():
+    """Pythagorean-like three bodies (masses 3, 4, 5 at the corners of a 3-4-5
+    triangle, at rest), eps = 0.01, to t = 8: the oracle's schedule replayed
+    with 16 passes per step."""
+    m = np.array([3.0, 4.0, 5.0]) / 12.0
+    x = np.array([[1.0, 3.0, 0.0], [-2.0, -1.0, 0.0], [1.0, -1.0, 0.0]])
+    v = np.zeros((3, 3))
+    sim = oracle.Sim6(m, x, v, 0.01, ETA4, eta_init=ETA4, order=4, n_iter=16)
+    rec = []
+    while True:
+        tick, idx = sim.step()
+        rec.append((tick, idx))
+        if tick >= int(8.0 / DT_MIN):
+            break
+    so = sim.state()
+    with gravidy.Integrator6(m, x, v, 0.01, ETA4, eta_init=ETA4, order=4, n_iter=16) as g:
+        for tick, idx in rec:
+            g.replay_step(tick, idx)
+        st = g.state()
+    print("three bodies, 16 passes: %d steps, max|dx| %.2e" % (len(rec), np.abs(st["x"] - so["x"]).max()))
+    assert (st["tau"] == so["tau"]).all()
+    assert np.abs(st["x"] - so["x"]).max() < 1e-11
+    assert np.abs(st["v"] - so["v"]).max() < 1e-11
