@@ -87,7 +87,8 @@ def _args():
     p.add_argument("--collapse-trh", type=float, default=30.0,
                    help="--sweep collapse: stop at this many half-mass relaxation times")
     p.add_argument("--collapse-wall", type=float, default=240.0,
-                   help="--sweep collapse: stop after this many seconds of wall time")
+                   help="--sweep collapse: stop each run after this many seconds of wall time")
+    p.add_argument("--collapse-seeds", default="1", help="--sweep collapse: comma-separated Plummer seeds")
     p.add_argument("--profile-force-h6", type=int, default=0, metavar="N",
                    help="profiling hook: initialise an N-particle Plummer sphere on the sixth-order path (two "
                         "force/jerk/snap evaluations), evaluate all N once more, print nothing and exit")
@@ -947,37 +948,38 @@ COLLAPSE_FRACTIONS = [0.005, 0.01, 0.02, 0.05, 0.1, 0.25, 0.5, 0.75, 0.9]
 
 
 def sweep_collapse(a):
-    """Core collapse of an equal-mass Plummer sphere (N = 1024, seed 1, eps =
-    1e-4, eta = 0.01, mixed path; the paper's single-mass experiment, Sec. 4.2,
-    at a size one GPU finishes in minutes): Lagrange radii about the density
-    centre, |dE/E|, block steps and wall time every 4 N-body units, until
-    t = --collapse-trh half-mass relaxation times or --collapse-wall seconds of
-    wall time."""
+    """Core collapse of an equal-mass Plummer sphere (N = 1024, eps = 1e-4, eta =
+    0.01, mixed path; the paper's single-mass experiment, Sec. 4.2, at a size one
+    GPU finishes in minutes): Lagrange radii about the density centre, |dE/E|,
+    block steps and wall time every 4 N-body units, until t = --collapse-trh
+    half-mass relaxation times or --collapse-wall seconds of wall time, for each
+    seed of --collapse-seeds (one JSON line per seed)."""
     from paper_1702_00440_gb300 import gravidy, inputs
 
     n = 1024
-    m, x, v = inputs.plummer(n, seed=1)
-    trh, rh = half_mass_relaxation_time(m, x)
-    t_max = a.collapse_trh * trh
-    g = gravidy.Integrator(m, x, v, EPS, ETA, precision="mixed", autotune=True)
-    E0 = sum(g.energy())
-    rows = [{"t": 0.0, "radii": lagrange_radii(m, x, COLLAPSE_FRACTIONS, density_centre(m, x)), "dE_E": 0.0,
-             "block_steps": 0, "wall_s": 0.0}]
-    t0 = time.perf_counter()
-    k = 0
-    while True:
-        k += 1
-        t = 4.0 * k
-        if t > t_max or time.perf_counter() - t0 > a.collapse_wall:
-            break
-        g.evolve(t)
-        xs = g.state()["x"]
-        rows.append({"t": t, "radii": lagrange_radii(m, xs, COLLAPSE_FRACTIONS, density_centre(m, xs)),
-                     "dE_E": abs((sum(g.energy()) - E0) / E0), "block_steps": g.stats()["block_steps"],
-                     "wall_s": time.perf_counter() - t0})
-    g.close()
-    print(json.dumps({"sweep": "collapse", "n": n, "eps": EPS, "eta": ETA, "t_rh": trh, "r_h": rh,
-                      "fractions": COLLAPSE_FRACTIONS, "rows": rows}))
+    for seed in (int(q) for q in a.collapse_seeds.split(",")):
+        m, x, v = inputs.plummer(n, seed=seed)
+        trh, rh = half_mass_relaxation_time(m, x)
+        t_max = a.collapse_trh * trh
+        g = gravidy.Integrator(m, x, v, EPS, ETA, precision="mixed", autotune=True)
+        E0 = sum(g.energy())
+        rows = [{"t": 0.0, "radii": lagrange_radii(m, x, COLLAPSE_FRACTIONS, density_centre(m, x)), "dE_E": 0.0,
+                 "block_steps": 0, "wall_s": 0.0}]
+        t0 = time.perf_counter()
+        k = 0
+        while True:
+            k += 1
+            t = 4.0 * k
+            if t > t_max or time.perf_counter() - t0 > a.collapse_wall:
+                break
+            g.evolve(t)
+            xs = g.state()["x"]
+            rows.append({"t": t, "radii": lagrange_radii(m, xs, COLLAPSE_FRACTIONS, density_centre(m, xs)),
+                         "dE_E": abs((sum(g.energy()) - E0) / E0), "block_steps": g.stats()["block_steps"],
+                         "wall_s": time.perf_counter() - t0})
+        g.close()
+        print(json.dumps({"sweep": "collapse", "n": n, "seed": seed, "eps": EPS, "eta": ETA, "t_rh": trh, "r_h": rh,
+                          "fractions": COLLAPSE_FRACTIONS, "rows": rows}), flush=True)
     return 0
 
 
