@@ -219,6 +219,15 @@ int gd_active(gd_ctx *c, int32_t *idx, int64_t *nact, int64_t *tick_next);
  * are computed and stored as usual but the block times come from the caller. */
 int gd_replay_step(gd_ctx *c, int64_t tick_next, const int32_t *idx, int64_t nact);
 
+/* Failure-detection probe: one GPU thread waits, with the bounded wait the
+ * fused kernel's grid barrier uses, for a device counter that nothing
+ * advances; after `limit` polls (limit in [1, 2^24]) it gives up, records
+ * GD_ETIMEOUT in the device flag and ends.  Returns GD_ETIMEOUT, read back by
+ * the same synchronisation as every other call; the context then refuses
+ * further work, as after any device fault, while the CUDA context and the GPU
+ * stay usable.  GD_EINVAL for a null context or a limit out of range. */
+int gd_test_wait_timeout(gd_ctx *c, int32_t limit);
+
 /* ---- ensembles of independent clusters -------------------------------------
  *
  * nclusters independent N-body systems advanced together: every cluster follows

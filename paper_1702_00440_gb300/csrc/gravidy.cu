@@ -1078,6 +1078,17 @@ const char *gd_last_error(const gd_ctx *c)
     return c->err.c_str();
 }
 
+int gd_test_wait_timeout(gd_ctx *c, int32_t limit)
+{
+    int rc = check_usable(c);
+    if (rc) return rc;
+    if (limit < 1 || limit > (1 << 24)) return fail(c, GD_EINVAL, "limit must be in [1, 2^24]");
+    k_wait_probe<<<1, 32, 0, c->stream>>>(c->d, limit);
+    c->launches += 1;
+    CK(cudaGetLastError());
+    return sync_ctrl(c);
+}
+
 int gd_force(gd_ctx *c, int64_t tick, const int32_t *idx, int64_t nact, double *acc, double *jerk)
 {
     int rc = check_usable(c);

@@ -1747,6 +1747,16 @@ __global__ void k_set_tick_end(Ctrl *c, long long tick_end) { c->tick_end = tick
 constexpr int BAR_WORDS = 32;            // the barrier counter sits alone in a 128-byte line
 constexpr int BAR_SPIN_LIMIT = 1 << 24;  // bounded wait
 
+// Polls *ctr until it reaches target, at most `limit` times; false if it gave up.
+// The bounded wait of the grid barrier (and of the failure-detection probe).
+__device__ __forceinline__ bool wait_counter_ge(const unsigned long long *ctr, unsigned long long target, int limit)
+{
+    int spins = 0;
+    while (*(volatile const unsigned long long *)ctr < target)
+        if (++spins > limit) return false;
+    return true;
+}
+
 // Grid-wide barrier for a co-resident (cooperative) grid of nb CTAs: one 64-bit
 // counter that only grows; the k-th barrier is passed when the counter reaches
 // nb * k, so each CTA waits for the multiple of nb above the value its own arrival
@@ -1763,16 +1773,22 @@ __device__ __forceinline__ void grid_sync(unsigned int *bar, Ctrl *ctrl)
         __threadfence();
         const unsigned long long old = atomicAdd(ctr, 1ull);
         const unsigned long long target = (old / nb + 1) * nb;
-        int spins = 0;
-        while (*(volatile unsigned long long *)ctr < target) {
-            if (++spins > BAR_SPIN_LIMIT) {
-                set_err(ctrl, ST_ETIMEOUT);
-                break;
-            }
-        }
+        if (!wait_counter_ge(ctr, target, BAR_SPIN_LIMIT)) set_err(ctrl, ST_ETIMEOUT);
         __threadfence();
     }
     __syncthreads();
+}
+
+// Failure-detection probe: one thread waits, with the grid barrier's bounded
+// wait, for a counter that nothing advances (the upper half of the barrier
+// array, which the barrier does not use), so the wait runs out after `limit`
+// polls and the device flag records GD_ETIMEOUT; the kernel then ends normally.
+__global__ void k_wait_probe(Dev d, int limit)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const unsigned long long *ctr = (const unsigned long long *)(d.bar + BAR_WORDS / 2);
+    const unsigned long long target = *(volatile const unsigned long long *)ctr + 1ull;
+    if (!wait_counter_ge(ctr, target, limit)) set_err(d.ctrl, ST_ETIMEOUT);
 }
 
 struct SArgs {

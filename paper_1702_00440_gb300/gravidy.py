@@ -26,7 +26,7 @@ _PRECISION = {"fp64": GD_FP64, "mixed": GD_MIXED, GD_FP64: GD_FP64, GD_MIXED: GD
 EXPORTS = (
     "gd_opts_default", "gd_init", "gd_evolve", "gd_step_block", "gd_energy", "gd_get_state",
     "gd_set_state", "gd_get_stats", "gd_kernel_time", "gd_free", "gd_last_error", "gd_force",
-    "gd_predict", "gd_active", "gd_replay_step", "gd_force_noalloc", "gd_autotune", "gd_get_tuning",
+    "gd_predict", "gd_active", "gd_replay_step", "gd_test_wait_timeout", "gd_force_noalloc", "gd_autotune", "gd_get_tuning",
     "gd_cluster_info", "gd_cluster_time",
     "gd_ens_init", "gd_ens_evolve", "gd_ens_step_block", "gd_ens_energy", "gd_ens_get_state",
     "gd_ens_get_stats", "gd_ens_free", "gd_ens_last_error",
@@ -112,6 +112,7 @@ def load(build_if_missing: bool = True):
             "gd_predict": (ctypes.c_int, [P, I64, P, P]),
             "gd_active": (ctypes.c_int, [P, P, P, P]),
             "gd_replay_step": (ctypes.c_int, [P, I64, P, I64]),
+            "gd_test_wait_timeout": (ctypes.c_int, [P, I32]),
             "gd_force_noalloc": (ctypes.c_int, [I64, P, P, P, D, P, I64, P, P, P]),
             "gd_autotune": (ctypes.c_int, [P, I32]),
             "gd_get_tuning": (ctypes.c_int, [P, P, P, P, P, I32]),

@@ -88,6 +88,12 @@ def test_h6_scheme_rejects_bad_order_and_passes_on_the_host(order, n_iter):
     assert lib.gd_h6_last_error(None).decode()
 
 
+def test_wait_probe_rejects_a_null_context_on_the_host():
+    lib = gravidy.load()
+    assert lib.gd_test_wait_timeout(None, 100) == gravidy.GD_EINVAL
+    assert lib.gd_last_error(None).decode()
+
+
 def test_opts_defaults():
     o = gravidy.make_opts()
     assert o.dt_min == 2.0 ** -22 and o.dt_max == 0.125 and o.precision == gravidy.GD_MIXED
