@@ -93,6 +93,9 @@ def _args():
     p.add_argument("--collapse-wall", type=float, default=240.0,
                    help="--sweep collapse: stop each run after this many seconds of wall time")
     p.add_argument("--collapse-seeds", default="1", help="--sweep collapse: comma-separated Plummer seeds")
+    p.add_argument("--collapse-oracle", action="store_true",
+                   help="--sweep collapse: run the FP64 oracle on the host cores (one seed per core) instead of "
+                        "the GPU")
     p.add_argument("--profile-force-h6", type=int, default=0, metavar="N",
                    help="profiling hook: initialise an N-particle Plummer sphere on the sixth-order path (two "
                         "force/jerk/snap evaluations), evaluate all N once more, print nothing and exit")
@@ -951,39 +954,70 @@ def half_mass_relaxation_time(m, x):
 COLLAPSE_FRACTIONS = [0.005, 0.01, 0.02, 0.05, 0.1, 0.25, 0.5, 0.75, 0.9]
 
 
+def _collapse_rows(m, x, t_max, wall, evolve, energy, positions, block_steps):
+    """The core-collapse diagnostics every 4 N-body units until t_max or `wall`
+    seconds: Lagrange radii about the density centre, |dE/E|, block steps."""
+    E0 = energy()
+    rows = [{"t": 0.0, "radii": lagrange_radii(m, x, COLLAPSE_FRACTIONS, density_centre(m, x)), "dE_E": 0.0,
+             "block_steps": 0, "wall_s": 0.0}]
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        k += 1
+        t = 4.0 * k
+        if t > t_max or time.perf_counter() - t0 > wall:
+            break
+        evolve(t)
+        xs = positions()
+        rows.append({"t": t, "radii": lagrange_radii(m, xs, COLLAPSE_FRACTIONS, density_centre(m, xs)),
+                     "dE_E": abs((energy() - E0) / E0), "block_steps": block_steps(),
+                     "wall_s": time.perf_counter() - t0})
+    return rows
+
+
+def _oracle_collapse_job(job):
+    """One seed of the collapse sweep through the FP64 oracle on a host core."""
+    seed, trh_factor, wall = job
+    import oracle
+    from paper_1702_00440_gb300 import inputs
+
+    n = 1024
+    m, x, v = inputs.plummer(n, seed=seed)
+    trh, rh = half_mass_relaxation_time(m, x)
+    sim = oracle.Sim(m, x, v, EPS, ETA)
+    rows = _collapse_rows(m, x, trh_factor * trh, wall, sim.evolve, lambda: sum(sim.energy()),
+                          lambda: sim.state()["x"], lambda: sim.stats()["nblock"])
+    return {"sweep": "collapse", "impl": "oracle", "n": n, "seed": seed, "eps": EPS, "eta": ETA, "t_rh": trh,
+            "r_h": rh, "fractions": COLLAPSE_FRACTIONS, "rows": rows}
+
+
 def sweep_collapse(a):
     """Core collapse of an equal-mass Plummer sphere (N = 1024, eps = 1e-4, eta =
     0.01, mixed path; the paper's single-mass experiment, Sec. 4.2, at a size one
     GPU finishes in minutes): Lagrange radii about the density centre, |dE/E|,
     block steps and wall time every 4 N-body units, until t = --collapse-trh
     half-mass relaxation times or --collapse-wall seconds of wall time, for each
-    seed of --collapse-seeds (one JSON line per seed)."""
+    seed of --collapse-seeds (one JSON line per seed).  --collapse-oracle runs
+    the same diagnostics on the FP64 oracle instead, one seed per host core."""
+    seeds = [int(q) for q in a.collapse_seeds.split(",")]
+    if a.collapse_oracle:
+        jobs = [(s, a.collapse_trh, a.collapse_wall) for s in seeds]
+        with _pool(min(len(jobs), _host_cores())) as p:
+            for res in p.imap(_oracle_collapse_job, jobs):
+                print(json.dumps(res), flush=True)
+        return 0
     from paper_1702_00440_gb300 import gravidy, inputs
 
     n = 1024
-    for seed in (int(q) for q in a.collapse_seeds.split(",")):
+    for seed in seeds:
         m, x, v = inputs.plummer(n, seed=seed)
         trh, rh = half_mass_relaxation_time(m, x)
-        t_max = a.collapse_trh * trh
         g = gravidy.Integrator(m, x, v, EPS, ETA, precision="mixed", autotune=True)
-        E0 = sum(g.energy())
-        rows = [{"t": 0.0, "radii": lagrange_radii(m, x, COLLAPSE_FRACTIONS, density_centre(m, x)), "dE_E": 0.0,
-                 "block_steps": 0, "wall_s": 0.0}]
-        t0 = time.perf_counter()
-        k = 0
-        while True:
-            k += 1
-            t = 4.0 * k
-            if t > t_max or time.perf_counter() - t0 > a.collapse_wall:
-                break
-            g.evolve(t)
-            xs = g.state()["x"]
-            rows.append({"t": t, "radii": lagrange_radii(m, xs, COLLAPSE_FRACTIONS, density_centre(m, xs)),
-                         "dE_E": abs((sum(g.energy()) - E0) / E0), "block_steps": g.stats()["block_steps"],
-                         "wall_s": time.perf_counter() - t0})
+        rows = _collapse_rows(m, x, a.collapse_trh * trh, a.collapse_wall, g.evolve, lambda: sum(g.energy()),
+                              lambda: g.state()["x"], lambda: g.stats()["block_steps"])
         g.close()
-        print(json.dumps({"sweep": "collapse", "n": n, "seed": seed, "eps": EPS, "eta": ETA, "t_rh": trh, "r_h": rh,
-                          "fractions": COLLAPSE_FRACTIONS, "rows": rows}), flush=True)
+        print(json.dumps({"sweep": "collapse", "impl": "gpu mixed", "n": n, "seed": seed, "eps": EPS, "eta": ETA,
+                          "t_rh": trh, "r_h": rh, "fractions": COLLAPSE_FRACTIONS, "rows": rows}), flush=True)
     return 0
 
 

@@ -86,3 +86,17 @@ def test_half_mass_relaxation_time_formula():
     trh, rh = bench.half_mass_relaxation_time(m, x)
     assert abs(rh - 1.0) < 1e-12
     assert abs(trh - 0.138 * math.sqrt(n * n) / math.log(0.1 * n)) < 1e-9 * trh
+
+
+def test_collapse_sweep_oracle_leg_one_row():
+    """The collapse sweep's oracle leg to 0.2 t_rh (one output at t = 4): the
+    rows carry the diagnostics, the energy error is small and the block steps
+    count up."""
+    bench = _bench()
+    res = bench._oracle_collapse_job((2, 0.2, 600.0))
+    assert res["impl"] == "oracle" and res["seed"] == 2 and abs(res["t_rh"] - 20.18) < 0.01
+    rows = res["rows"]
+    assert [r["t"] for r in rows] == [0.0, 4.0]
+    assert len(rows[1]["radii"]) == len(bench.COLLAPSE_FRACTIONS)
+    assert all(a < b for a, b in zip(rows[1]["radii"], rows[1]["radii"][1:]))
+    assert 0 < rows[1]["dE_E"] < 1e-6 and rows[1]["block_steps"] > 1000
