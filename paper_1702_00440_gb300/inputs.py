@@ -7,10 +7,13 @@ model GraviDy's tests use (Sec. 3.1: equal-mass Plummer spheres in standard
 N-body units, G = M = 1, E = -1/4, Plummer radius about 0.6).  The model is
 sampled in Plummer units (G = M = a = 1), the centre of mass is moved to the
 origin at rest, and the sample is scaled to N-body units with the analytic
-Plummer energy E = -3 pi / 64 (G M^2 / a): lengths by 16 / (3 pi) and
-velocities by sqrt(3 pi / 16).  The sample's own energy therefore differs
-from -1/4 by a sampling fluctuation of order 1/sqrt(N), as the paper's own
-run shows (its log starts from E = -0.256, Appendix A).
+Plummer energy E = -3 pi / 64 (G M^2 / a): lengths multiplied by 3 pi / 16
+and velocities by sqrt(16 / (3 pi)).  Radii beyond 10 Plummer radii are
+redrawn; the model holds 1.5 % of its mass there, so the sample is a slightly
+more bound, truncated model (K = 0.253, U = -0.513, E = -0.260 in these units)
+plus a sampling fluctuation of order 1/sqrt(N); the paper's own initial
+conditions were not exactly at -1/4 either (its log starts from E = -0.256,
+Appendix A).
 
 Power-law masses: dN/dm proportional to m^-2.35 on [0.2, 20] by inverse
 transform sampling, rescaled so the masses sum to 1.
