@@ -3,8 +3,10 @@
 
 Workload: Plummer sphere, N = 16384 equal masses in N-body units, Plummer
 softening eps = 1e-4, Aarseth eta = 0.01, power-of-two block steps in
-[2^-22, 1/8], mixed precision (FP32 pair arithmetic on double-single positions,
-FP64 prediction/correction/steps/energy).  One benchmark step advances the
+[2^-22, 1/8], mixed precision (FP32 pair arithmetic on double-single positions
+with compensated FP32 sums; prediction, correction and the Aarseth step in
+double-single / FP32 arithmetic; integer block-time bookkeeping; energy pair
+terms in FP32 with compensated sums and FP64 totals).  One benchmark step advances the
 system by dt_max = 1/8 N-body time unit -- every block step in that interval
 (active-list compaction, prediction of all N, force/jerk of the active set with
 j-split reduction, correction + Aarseth step + quantisation) -- and evaluates
@@ -337,7 +339,10 @@ def run_gravidy(a):
         g.energy()
 
     def timed_region():
-        nonlocal t
+        nonlocal t, start
+        # the state at the start of the timed steps: the roofline and e2e passes below
+        # replay exactly these block steps from it
+        start = (t, {k: q.copy() for k, q in g.state().items()})
         s0 = g.stats()
         comm.barrier()
         torch.cuda.synchronize()
@@ -370,6 +375,7 @@ def run_gravidy(a):
         s1 = g.stats()
         return total_ms, per, E, clocks, s0, s1
 
+    start = None
     total_ms, per, E, clocks, s0, s1 = timed_region()
     retried = False
     if _rejected(clocks):
@@ -382,17 +388,19 @@ def run_gravidy(a):
     value = tot_inter / (max_ms / 1e3)
     nbu = a.steps * DT_STEP
     de = abs((E - E0) / E0)
-    state_end = {k: q.copy() for k, q in g.state().items()}
+    t_w, st_w = start
+    tuning = g.tuning()
 
-    # ---- roofline of the force kernel: the same workload continued for the
-    # same number of steps with CUDA events around every force launch
-    g2 = gravidy.Integrator(m, x, v, EPS, ETA, precision=a.precision, stream=stream.cuda_stream, time_force=True,
-                            autotune=not a.no_autotune)
-    g2.set_state(state_end["x"], state_end["v"], state_end["a"], state_end["j"], state_end["tau"], state_end["dtau"])
+    # ---- roofline of the force and cluster kernels: the timed block steps replayed
+    # from their starting state, with the same tuning table (so the same block steps
+    # and arithmetic) and CUDA events around every force and cluster launch
+    g2 = gravidy.Integrator(m, x, v, EPS, ETA, precision=a.precision, stream=stream.cuda_stream, time_force=True)
+    g2.set_tuning(*tuning[:3])
+    g2.set_state(st_w["x"], st_w["v"], st_w["a"], st_w["j"], st_w["tau"], st_w["dtau"])
     g2.kernel_time()
     g2.cluster_time()
     s2a = g2.stats()
-    t2 = t
+    t2 = t_w
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     region_ms = 0.0
@@ -410,6 +418,8 @@ def run_gravidy(a):
     cl_size, _, cl_ns = g2.cluster_info()
     s2b = g2.stats()
     g2.close()
+    same_steps = (s2b["block_steps"] - s2a["block_steps"] == s1["block_steps"] - s0["block_steps"]
+                  and s2b["interactions"] - s2a["interactions"] == inter)
     # the block steps the cluster took: every interaction of the region outside
     # the full-GPU force launches
     c_inter = max(0.0, (s2b["interactions"] - s2a["interactions"]) - f_inter)
@@ -444,13 +454,14 @@ def run_gravidy(a):
     cpu = None
     e2e = None
     if not a.no_extras:
-        # ---- end to end through the public API from pinned host buffers
+        # ---- end to end through the public API from pinned host buffers: the timed
+        # block steps replayed from their starting state, every step's state uploaded
+        # from and read back to pinned host memory
         pin = {k: torch.empty(q.shape, dtype=torch.float64 if q.dtype == np.float64 else torch.int64,
-                              pin_memory=True).numpy() for k, q in state_end.items()}
-        now = g.state()
+                              pin_memory=True).numpy() for k, q in st_w.items()}
         for k in pin:
-            pin[k][...] = now[k]
-        t_e2e0 = t
+            pin[k][...] = st_w[k]
+        t_e = t_w
         bi = 4 * n * 3 * 8 + 3 * n * 8   # x, v, a, jerk + tau, dtau, next time
         bo = 4 * n * 3 * 8 + 2 * n * 8 + 16
         torch.cuda.synchronize()
@@ -459,15 +470,17 @@ def run_gravidy(a):
         for _ in range(a.steps):
             si = g.stats()["interactions"]
             g.set_state(pin["x"], pin["v"], pin["a"], pin["j"], pin["tau"], pin["dtau"])
-            t += DT_STEP
-            g.evolve(t)
+            t_e += DT_STEP
+            g.evolve(t_e)
             g.energy()
             g.state(out=pin)
             e_inter += g.stats()["interactions"] - si
         w1 = time.perf_counter()
         e_max = comm.reduce(w1 - w0, "MAX")
         e2e = {"value": comm.reduce(e_inter, "SUM") / e_max, "unit": UNIT, "h2d_bytes_per_step": bi,
-               "d2h_bytes_per_step": bo, "timing": "host wall clock, set_state + evolve(+1/8) + energy + get_state"}
+               "d2h_bytes_per_step": bo, "same_block_steps_as_value": e_inter == inter,
+               "timing": "host wall clock, set_state + evolve(+1/8) + energy + get_state, replaying the timed "
+                         "block steps from their starting state"}
 
         # ---- plain FP64 GPU form over the first 1/8 from the same ICs
         if a.precision == "mixed":
@@ -514,10 +527,10 @@ def run_gravidy(a):
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": max_ms / a.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 pair / f64 update" if a.precision == "mixed" else "f64",
+            "vs_baseline": None, "dtype": "f32 pair / ds-f32 update" if a.precision == "mixed" else "f64",
             "data": "synthetic", "config": _workload(n),
             "s_per_nbu": max_ms / 1e3 / nbu, "dE_E": de,
-            "t_timed": [(a.warmup) * DT_STEP, (a.warmup + a.steps) * DT_STEP],
+            "t_timed": [t_w, t_w + a.steps * DT_STEP], "roofline_same_block_steps": same_steps,
             "block_steps": s1["block_steps"] - s0["block_steps"],
             "particle_steps": s1["particle_steps"] - s0["particle_steps"],
             "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

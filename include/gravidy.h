@@ -115,8 +115,12 @@ void gd_opts_default(gd_opts *o);
  * initial force and jerk of all n particles (O(n^2)) and the first block step
  * of each, dt = eta |a| / |jerk| rounded down to a power of two in
  * [dt_min, dt_max].  eps is the Plummer softening length (>= 0; eps = 0 gives
- * the unsoftened Eq. 1 with the self term excluded), eta > 0.  opt may be
- * NULL for the defaults.  On success *out is a new context (time 0). */
+ * the unsoftened Eq. 1 with the self term excluded), eta > 0.  An eps whose
+ * square is below the smallest normal number of the pair arithmetic (FP32 for
+ * GD_MIXED, FP64 for GD_FP64) changes no resolvable r^2 and runs as eps = 0;
+ * an eps with max(m) / eps^3 beyond that precision's range (the self term of
+ * the softened sum would overflow) is GD_EINVAL.  opt may be NULL for the
+ * defaults.  On success *out is a new context (time 0). */
 int gd_init(gd_ctx **out, int64_t n, const double *m, const double *x, const double *v,
             double eps, double eta, const gd_opts *opt);
 
@@ -131,8 +135,10 @@ int gd_step_block(gd_ctx *c, double *t_out, int64_t *nact_out);
 
 /* Kinetic and potential energy (Sec. 2.1 Eq. 2, with the potential softened
  * like the force: -sum_{i<j} m_i m_j / sqrt(r_ij^2 + eps^2)) at the time of
- * the last block step; particles behind it are predicted to it first. The
- * pair sums run in FP64 in both precisions. */
+ * the last block step; particles behind it are predicted to it first.  GD_FP64
+ * computes every pair term in FP64; GD_MIXED computes the pair terms in FP32 on
+ * double-single positions (one Newton step on rsqrt, about 8 units of 2^-24 per
+ * term) and sums them with compensation; both return FP64 totals. */
 int gd_energy(gd_ctx *c, double *K, double *U);
 
 /* Copy the state out: x, v, a, jerk as n*3 AoS doubles (each particle at its
@@ -160,6 +166,13 @@ int gd_autotune(gd_ctx *c, int32_t reps);
  * measured).  Any pointer may be NULL. */
 int gd_get_tuning(gd_ctx *c, int32_t *mode_cut, int16_t *split, int8_t *mode, float *ms,
                   int32_t nbuckets);
+
+/* Replace the tuning table (the inverse of gd_get_tuning): mode_cut >= 1, and
+ * for buckets b < nbuckets (<= 32) split[b] >= 0 and mode[b] in {-1, 0, 1}
+ * (meanings as in gd_get_tuning; NULL leaves that column unchanged).  Two
+ * contexts with the same table and state take the same block steps with the
+ * same arithmetic.  The integration state is not changed. */
+int gd_set_tuning(gd_ctx *c, int32_t mode_cut, const int16_t *split, const int8_t *mode, int32_t nbuckets);
 
 /* Counters since gd_init. */
 int gd_get_stats(gd_ctx *c, gd_stats *s);
@@ -208,9 +221,27 @@ int gd_force(gd_ctx *c, int64_t tick, const int32_t *idx, int64_t nact, double *
  * step 7a), n*3 AoS doubles each; either pointer may be NULL. */
 int gd_predict(gd_ctx *c, int64_t tick, double *xp, double *vp);
 
+/* The next block step taken inside the small-step cluster that gd_evolve uses
+ * for steps with few active particles (gd_cluster_info), the same kernel and
+ * arithmetic, stopped after that one step.  A step with more active particles
+ * than the cluster takes is left untaken: *nact_out = 0 and *t_out = 0 (the
+ * state is unchanged; gd_step_block takes it).  Otherwise *t_out (nullable) is
+ * the step's time and *nact_out (nullable) its active count.  GD_ESTATE if the
+ * context does not use the cluster. */
+int gd_step_block_small(gd_ctx *c, double *t_out, int64_t *nact_out);
+
+/* Positions and velocities of all n particles predicted to tick exactly as the
+ * block step's predictor (Sec. 2.4 step 7a) stores them for the force kernel,
+ * n*3 AoS doubles each; either pointer may be NULL.  GD_MIXED: the double-single
+ * position of the j-record (hi + lo, an FP64 sum) and its FP32 velocity, from
+ * the double-single / FP32 Taylor series of the mixed path; GD_FP64: the same as
+ * gd_predict. */
+int gd_predict_records(gd_ctx *c, int64_t tick, double *xp, double *vp);
+
 /* The active set of the next block step (Sec. 2.4 step 5) without taking it:
- * idx (host, n int32) receives the active indices in ascending order,
- * *nact their count, *tick_next the block time. */
+ * idx (host, n int32) receives the list exactly as the block step's compaction
+ * writes it on the device (ascending particle order), *nact its length,
+ * *tick_next the block time. */
 int gd_active(gd_ctx *c, int32_t *idx, int64_t *nact, int64_t *tick_next);
 
 /* One block step with a given block time and active list (host int32,
@@ -227,6 +258,14 @@ int gd_replay_step(gd_ctx *c, int64_t tick_next, const int32_t *idx, int64_t nac
  * further work, as after any device fault, while the CUDA context and the GPU
  * stay usable.  GD_EINVAL for a null context or a limit out of range. */
 int gd_test_wait_timeout(gd_ctx *c, int32_t limit);
+
+/* Allocation-failure injection for tests: the nth allocation of `kind` (0 = host,
+ * pageable or pinned; 1 = device) that the calling thread's next context set-ups
+ * (gd_init, gd_ens_init, gd_h6_init, gd_h6_init_scheme) make fails, once, as if
+ * the allocator had run out; the set-up then frees what it holds and returns
+ * GD_ENOMEM.  nth = 0 cancels a pending injection.  GD_EINVAL for kind not 0 or 1
+ * or nth outside [0, 2^20].  Needs no GPU. */
+int gd_test_fail_alloc(int32_t kind, int32_t nth);
 
 /* ---- ensembles of independent clusters -------------------------------------
  *
@@ -275,15 +314,17 @@ const char *gd_ens_last_error(const gd_ens *s);
  *
  * gd_force_noalloc computes what gd_force computes with GD_MIXED precision --
  * the softened acceleration and jerk of the particles idx[0..nact) against all
- * n particles (Sec. 2.4, softened Eq. 1 and its time derivative) -- but from
+ * n particles, in FP32 pair arithmetic on double-single positions -- but from
  * caller-owned DEVICE arrays and without allocating anything.  Its scratch
- * (about 4.4 MiB: j-records, j-split partial sums, a control block) is a fixed
- * array compiled into the library, which every GPU that loads the library
- * holds until the process exits.
+ * (3,949,056 bytes, 3.77 MiB: j-records, j-split partial sums, summed forces,
+ * a control block) is a fixed array compiled into the library, which every GPU
+ * that loads the library holds until the process exits.
  *
  *   n      number of particles, 1 <= n <= 32768 (larger n returns GD_EINVAL)
  *   m      device, n doubles;  x, v  device, n*3 doubles (AoS xyz)
- *   eps    Plummer softening >= 0
+ *   eps    Plummer softening >= 0; eps^2 below FLT_MIN runs as eps = 0.  With
+ *          eps > 0 the row of particle i is finite only while m_i / eps^3 is
+ *          finite in FP32 (its self term); the masses are not inspected
  *   idx    device, nact int32 particle indices (duplicates allowed); an entry
  *          outside [0, n) yields NaN in its output rows
  *   nact   1 <= nact <= n

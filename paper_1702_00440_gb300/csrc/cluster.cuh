@@ -48,7 +48,7 @@ constexpr int CL_ROUNDS = 3;  // particles per thread at most (P <= CL_ROUNDS * 
 // Shared-memory layout of a CTA owning up to P particles (P a multiple of 32).
 struct ClLayout {
     int P;
-    size_t xh, xl, vh, vl, af, jf, mf, tau, dtau, jA, jB, jC, lact, iA, iB, iC, aown, oA, oB, oC, aloc, part, tp, bytes;
+    size_t xh, xl, vh, vl, af, jf, tau, dtau, jA, jB, jC, lact, iA, iB, iC, aown, oA, oB, oC, aloc, part, tp, bytes;
     __host__ __device__ ClLayout(int P_) : P(P_)
     {
         size_t o = 0;
@@ -71,7 +71,6 @@ struct ClLayout {
         vl = take(sizeof(float) * 3 * P);
         af = take(sizeof(float) * 3 * P);
         jf = take(sizeof(float) * 3 * P);
-        mf = take(sizeof(float) * P);
         lact = take(sizeof(int) * CL_NS);
         aown = take(sizeof(int) * CL_NS);
         oA = take(sizeof(float4) * CL_NS);
@@ -79,7 +78,7 @@ struct ClLayout {
         oC = take(sizeof(float2) * CL_NS);
         aloc = take(sizeof(int) * CL_NS);
         part = take(sizeof(float) * CL_NS * CL_MAXC * 6);
-        tp = take(sizeof(float) * CL_W * 6);
+        tp = take(sizeof(float) * 2 * CL_W * 6);
         bytes = o;
     }
 };
@@ -93,12 +92,6 @@ struct ClArgs {
     int slot;       // handoff: >= 0 records the handed-over N_act in nact_hist[slot]
 };
 
-// Mailbox a CTA posts for the others (read through distributed shared memory).
-struct ClBox {
-    int cnt;         // active particles of this CTA in the current step
-    int bad;         // fault bits seen by this CTA (1 non-finite)
-    long long mn;    // minimum next time over this CTA's particles after the step
-};
 
 template <bool SOFT>
 __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
@@ -113,18 +106,22 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
     extern __shared__ __align__(16) unsigned char smem[];
     float *xh = (float *)(smem + L.xh), *xl = (float *)(smem + L.xl);
     float *vh = (float *)(smem + L.vh), *vl = (float *)(smem + L.vl);
-    float *af = (float *)(smem + L.af), *jf = (float *)(smem + L.jf), *mf = (float *)(smem + L.mf);
+    float *af = (float *)(smem + L.af), *jf = (float *)(smem + L.jf);
     long long *tau = (long long *)(smem + L.tau), *dtau = (long long *)(smem + L.dtau);
-    float4 *jA = (float4 *)(smem + L.jA), *jB = (float4 *)(smem + L.jB);
-    float2 *jC = (float2 *)(smem + L.jC);
+    float4 *jA = (float4 *)(smem + L.jA), *jB = (float4 *)(smem + L.jB);  // own j-records; jA[p].w
+    float2 *jC = (float2 *)(smem + L.jC);                                 // holds the mass throughout
     int *lact = (int *)(smem + L.lact), *aown = (int *)(smem + L.aown), *aloc = (int *)(smem + L.aloc);
     float4 *oA = (float4 *)(smem + L.oA), *oB = (float4 *)(smem + L.oB);  // outbox: own active
     float2 *oC = (float2 *)(smem + L.oC);                                 // particles' j-records
     float4 *iA = (float4 *)(smem + L.iA), *iB = (float4 *)(smem + L.iB);
     float2 *iC = (float2 *)(smem + L.iC);
     float *part = (float *)(smem + L.part);  // [slot][rank][6]
-    float *tp = (float *)(smem + L.tp);      // [task][6]
-    __shared__ ClBox box;
+    float *tp = (float *)(smem + L.tp);      // [active][segment][6]
+    // inboxes the other CTAs write (distributed shared memory) before a cluster barrier:
+    // active counts of the step (before B1), minimum next time and fault bits (before B3)
+    __shared__ int s_cnt_in[CL_MAXC];
+    __shared__ long long s_mn_in[CL_MAXC];
+    __shared__ int s_bad_in[CL_MAXC];
     __shared__ int s_off[CL_MAXC + 1];
     __shared__ int s_wc[CL_ROUNDS * CL_W];
     __shared__ int s_base;
@@ -146,7 +143,7 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
             af[c * P + p] = d.af[c * n + i];
             jf[c * P + p] = d.jf[c * n + i];
         }
-        mf[p] = d.mf[i];
+        jA[p] = make_float4(0.f, 0.f, 0.f, d.mf[i]);
         tau[p] = d.tau[i];
         dtau[p] = d.dtau[i];
     }
@@ -190,7 +187,7 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
                     xp[c] = ds_pred_x(x0, v0, af[c * P + p], jf[c * P + p], dt, h2, h3);
                     vp[c] = ds_pred_v_rec(v0, af[c * P + p], jf[c * P + p], dt, h2);
                 }
-                rA[rd] = make_float4(xp[0].h, xp[1].h, xp[2].h, mf[p]);
+                rA[rd] = make_float4(xp[0].h, xp[1].h, xp[2].h, jA[p].w);
                 rB[rd] = make_float4(xp[0].l, xp[1].l, xp[2].l, vp[0]);
                 rC[rd] = make_float2(vp[1], vp[2]);
                 jA[p] = rA[rd];
@@ -236,12 +233,12 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
                 }
             }
         }
-        if (t == 0) box.cnt = s_base;
+        if (t < C) cl.map_shared_rank(s_cnt_in, t)[r] = s_base;  // this CTA's count, into every inbox
         cl.sync();  // B1: j-records, active lists and counts of every CTA are visible
 
         // ---- 2. the step's active set: counts of all CTAs, prefix offsets
-        if (warp == 0) {  // lane q reads CTA q's count; a shuffle scan gives the offsets
-            const int cq = lane < C ? cl.map_shared_rank(&box, lane)->cnt : 0;
+        if (warp == 0) {  // lane q holds CTA q's count; a shuffle scan gives the offsets
+            const int cq = lane < C ? s_cnt_in[lane] : 0;
             int inc = cq;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -292,36 +289,60 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
             iC[k] = cl.map_shared_rank(oC, q)[kl];
         }
         __syncthreads();
-        // forces over this CTA's j-range: tasks (active, j-segment); with fewer than
-        // CL_W active particles each one's j-range is cut into Sw = 2^lgS segments
+        // forces over this CTA's j-range: tasks (pair of active particles, j-segment),
+        // so every j-record loaded from shared memory serves two pair terms; with
+        // fewer than CL_W pairs each pair's j-range is cut into Sw = 2^lgS segments
+        const int npair = (nact + 1) >> 1;
         int lgS = 0;
-        if (nact < CL_W) lgS = 31 - __clz(CL_W / nact);
+        if (npair < CL_W) lgS = 31 - __clz(CL_W / npair);
         const int Sw = 1 << lgS;
         const int seg = (((Pr + Sw - 1) >> lgS) + 31) & ~31;
-        const int ntask = nact << lgS;
+        const int ntask = npair << lgS;
         for (int task = warp; task < ntask; task += CL_W) {
-            const int k = task >> lgS, sg = task & (Sw - 1);
+            const int kp = task >> lgS, sg = task & (Sw - 1);
+            const int k0 = 2 * kp;
+            const bool has1 = k0 + 1 < nact;
+            const int k1 = has1 ? k0 + 1 : k0;
             const int jb = sg * seg, je = min(jb + seg, Pr);
-            const float4 Ai = iA[k], Bi = iB[k];
-            const float2 Ci = iC[k];
-            float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            const float4 A0 = iA[k0], B0 = iB[k0], A1 = iA[k1], B1 = iB[k1];
+            const float2 C0 = iC[k0], C1 = iC[k1];
+            float f0[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, f1[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (has1) {
 #pragma unroll 4
-            for (int j = jb + lane; j < je; j += 32)
-                pair_mixed<SOFT>(jA[j], jB[j], jC[j], Ai.x, Ai.y, Ai.z, Bi.x, Bi.y, Bi.z, Bi.w, Ci.x, Ci.y, eps2, f);
+                for (int j = jb + lane; j < je; j += 32) {
+                    const float4 A = jA[j], B = jB[j];
+                    const float2 Cj = jC[j];
+                    pair_mixed<SOFT>(A, B, Cj, A0.x, A0.y, A0.z, B0.x, B0.y, B0.z, B0.w, C0.x, C0.y, eps2, f0);
+                    pair_mixed<SOFT>(A, B, Cj, A1.x, A1.y, A1.z, B1.x, B1.y, B1.z, B1.w, C1.x, C1.y, eps2, f1);
+                }
+            } else {
+#pragma unroll 4
+                for (int j = jb + lane; j < je; j += 32)
+                    pair_mixed<SOFT>(jA[j], jB[j], jC[j], A0.x, A0.y, A0.z, B0.x, B0.y, B0.z, B0.w, C0.x, C0.y, eps2,
+                                     f0);
+            }
 #pragma unroll
             for (int c = 0; c < 6; c++)
-                for (int o = 16; o > 0; o >>= 1) f[c] = __fadd_rn(f[c], __shfl_xor_sync(0xffffffffu, f[c], o));
-            // lane c < 6 stores component c (selected without indexing the array)
-            float mine_c = f[0];
-#pragma unroll
-            for (int c = 1; c < 6; c++) mine_c = lane == c ? f[c] : mine_c;
-            if (Sw == 1) {
-                if (lane < 6) {
-                    float *dst = cl.map_shared_rank(part, aown[k]);
-                    dst[(aloc[k] * CL_MAXC + r) * 6 + lane] = mine_c;
+                for (int o = 16; o > 0; o >>= 1) {
+                    f0[c] = __fadd_rn(f0[c], __shfl_xor_sync(0xffffffffu, f0[c], o));
+                    f1[c] = __fadd_rn(f1[c], __shfl_xor_sync(0xffffffffu, f1[c], o));
                 }
-            } else if (lane < 6) {
-                tp[task * 6 + lane] = mine_c;
+            // lane q < 12 stores component q % 6 of active k0 (q < 6) or k1 (selected
+            // without indexing the arrays)
+            float mine_c = f0[0];
+#pragma unroll
+            for (int c = 1; c < 6; c++) mine_c = lane == c ? f0[c] : mine_c;
+#pragma unroll
+            for (int c = 0; c < 6; c++) mine_c = lane == 6 + c ? f1[c] : mine_c;
+            const bool store = lane < 6 || (has1 && lane < 12);
+            const int k = lane < 6 ? k0 : k1, c = lane < 6 ? lane : lane - 6;
+            if (store) {
+                if (Sw == 1) {
+                    float *dst = cl.map_shared_rank(part, aown[k]);
+                    dst[(aloc[k] * CL_MAXC + r) * 6 + c] = mine_c;
+                } else {
+                    tp[((k << lgS) + sg) * 6 + c] = mine_c;
+                }
             }
         }
         if (Sw > 1) {
@@ -411,39 +432,20 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
             int b = lane < CL_W ? s_wbad[lane] : 0;
             m = warp_min_ll(m);
             b = __reduce_or_sync(0xffffffffu, b);
-            if (lane == 0) {
-                box.mn = m;
-                box.bad = b;
+            if (lane < C) {  // this CTA's post, into every inbox
+                cl.map_shared_rank(s_mn_in, lane)[r] = m;
+                cl.map_shared_rank(s_bad_in, lane)[r] = b;
             }
         }
         cl.sync();  // B3: corrected state and the posts of every CTA are visible
 
-        // write the corrected particles through to global memory; issued after the
-        // barrier, whose release would otherwise wait for these stores to reach L2
-        for (int k = t; k < mine; k += CL_T) {
-            const int p = lact[k], i = p0 + p;
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                d.xs[c * n + i] = xh[c * P + p];
-                d.xs[(3 + c) * n + i] = xl[c * P + p];
-                d.vs[c * n + i] = vh[c * P + p];
-                d.vs[(3 + c) * n + i] = vl[c * P + p];
-                d.af[c * n + i] = af[c * P + p];
-                d.jf[c * n + i] = jf[c * P + p];
-            }
-            d.tau[i] = tau[p];
-            d.dtau[i] = dtau[p];
-            d.tnext[i] = tau[p] + dtau[p];
-        }
-
         // ---- 4. next block time: minimum over the C posts
-        if (warp == 0) {  // lane q reads CTA q's post
+        if (warp == 0) {  // lane q holds CTA q's post
             long long m = LLONG_MAX;
             int b = 0;
             if (lane < C) {
-                const ClBox *bx = cl.map_shared_rank(&box, lane);
-                m = bx->mn;
-                b = bx->bad;
+                m = s_mn_in[lane];
+                b = s_bad_in[lane];
             }
             m = warp_min_ll(m);
             b = __reduce_or_sync(0xffffffffu, b);
@@ -465,6 +467,24 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
             if (t == 0 && r == 0) set_err(ctrl, ST_ENONFINITE);
             break;
         }
+    }
+    // the particles this launch corrected (their time moved on), written back to
+    // global memory once
+    for (int p = t; p < Pr; p += CL_T) {
+        const int i = p0 + p;
+        if (tau[p] == d.tau[i]) continue;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            d.xs[c * n + i] = xh[c * P + p];
+            d.xs[(3 + c) * n + i] = xl[c * P + p];
+            d.vs[c * n + i] = vh[c * P + p];
+            d.vs[(3 + c) * n + i] = vl[c * P + p];
+            d.af[c * n + i] = af[c * P + p];
+            d.jf[c * n + i] = jf[c * P + p];
+        }
+        d.tau[i] = tau[p];
+        d.dtau[i] = dtau[p];
+        d.tnext[i] = tau[p] + dtau[p];
     }
     cl.sync();  // no CTA leaves while another may still read its shared memory
     if (r == 0 && t == 0) {

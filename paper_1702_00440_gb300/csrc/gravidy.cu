@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <climits>
 #include <cmath>
 #include <cstdint>
@@ -54,6 +55,19 @@ struct gd_ctx {
 
 static thread_local std::string g_init_err;
 
+// Allocation-failure injection (gd_test_fail_alloc): the count of allocations of
+// each kind (0 host, 1 device) the calling thread may still make before one fails;
+// 0 = no injection.  Consulted by every allocation a context's set-up makes.
+static thread_local int g_alloc_left[2] = {0, 0};
+
+// True if this allocation of `kind` is the one to fail (the injection then ends).
+bool gd_alloc_fails(int kind)
+{
+    int &l = g_alloc_left[kind];
+    if (l <= 0) return false;
+    return --l == 0;
+}
+
 namespace {
 
 int fail(gd_ctx *c, int code, const std::string &msg)
@@ -75,6 +89,31 @@ int cuda_fail(gd_ctx *c, cudaError_t e, const char *what)
         cudaError_t e_ = (call);                               \
         if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
     } while (0)
+
+// Softening in the precision of the pair arithmetic (FP32 on the mixed path, FP64
+// otherwise).  An eps whose square is below the smallest normal number of that
+// precision adds nothing to any r^2 the pair arithmetic resolves, so it runs the
+// unsoftened kernel (*soft = false, *eps2 = 0), whose self term (r^2 = 0) is
+// masked.  With eps > 0 the self term (r = v = 0) contributes an exact zero only
+// while m_i / eps^3 is finite in that precision; m_max > 0 is checked against it
+// (m_max < 0: the masses are not known here, no check).  Returns false if the
+// check fails.
+bool softening(double eps, bool mixed, double m_max, bool *soft, double *eps2)
+{
+    const double e2 = eps * eps;
+    const double tiny = mixed ? (double)FLT_MIN : DBL_MIN;
+    const double e2p = mixed ? (double)(float)e2 : e2;
+    if (!(e2p >= tiny)) {
+        *soft = false;
+        *eps2 = 0.0;
+        return true;
+    }
+    *soft = true;
+    *eps2 = e2;
+    // 2^120 (FP32) / 2^1000 (FP64) leaves room for the rounding of rsqrt and the products
+    const double lim = mixed ? std::ldexp(1.0, 120) : std::ldexp(1.0, 1000);
+    return !(m_max > 0) || m_max / (eps * e2) < lim;
+}
 
 bool is_pow2(double x)
 {
@@ -223,7 +262,7 @@ void launch_step(gd_ctx *c, int slot, cudaEvent_t e0, cudaEvent_t e1, bool captu
 constexpr int CL_STEPS = 4096;
 constexpr int CL_EV = 2 * 64;  // first timing event of the cluster launches (after the force pairs)
 
-void launch_cluster(gd_ctx *c, int handoff, int slot)
+void launch_cluster(gd_ctx *c, int handoff, int slot, int max_steps = CL_STEPS)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(c->cl_C);
@@ -237,7 +276,7 @@ void launch_cluster(gd_ctx *c, int handoff, int slot)
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    const ClArgs a{c->d, c->cl_P, c->cl_ns, CL_STEPS, handoff, slot};
+    const ClArgs a{c->d, c->cl_P, c->cl_ns, max_steps, handoff, slot};
     c->launches += 1;
     if (c->soft)
         cudaLaunchKernelEx(&cfg, k_cluster_steps<true>, a);
@@ -356,7 +395,7 @@ int check_usable(gd_ctx *c)
 template <class T>
 int dalloc(gd_ctx *c, T **p, size_t count)
 {
-    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T) + 16);
+    cudaError_t e = gd_alloc_fails(1) ? cudaErrorMemoryAllocation : cudaMalloc((void **)p, count * sizeof(T) + 16);
     if (e != cudaSuccess) {
         *p = nullptr;
         return fail(c, GD_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
@@ -369,7 +408,7 @@ void free_all(gd_ctx *c)
     Dev &d = c->d;
     void *ps[] = {d.x,  d.v,   d.a,    d.jk,   d.m,       d.tau,    d.dtau, d.tnext, d.jA,        d.jB,   d.jC,
                   d.pd, d.act, d.part, d.fsum, d.tilecnt, d.status, d.eu,   d.ek,    d.nact_hist, d.bar, d.ctrl,
-                  d.xs, d.vs,  d.af,   d.jf,   d.mf};
+                  d.xs, d.vs,  d.af,   d.jf,   d.mf,      d.selstat};
     for (void *p : ps)
         if (p) cudaFree(p);
     if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
@@ -683,19 +722,29 @@ int ctx_init(gd_ctx **out, int64_t n, const double *m, const double *x, const do
     // the mixed path counts steps in FP32: tick counts up to dtau_max and dt_min^5 stay exact
     if (o.precision == GD_MIXED && (o.dt_min < std::ldexp(1.0, -24) || o.dt_max / o.dt_min > std::ldexp(1.0, 24)))
         return fail(nullptr, GD_EINVAL, "mixed precision needs dt_min >= 2^-24 and dt_max/dt_min <= 2^24");
+    double m_max = 0.0;
     for (int64_t i = 0; i < n; i++) {
         if (!std::isfinite(m[i]) || m[i] < 0) return fail(nullptr, GD_EINVAL, "masses must be finite and >= 0");
         for (int k = 0; k < 3; k++)
             if (!std::isfinite(x[3 * i + k]) || !std::isfinite(v[3 * i + k]))
                 return fail(nullptr, GD_EINVAL, "positions and velocities must be finite");
+        m_max = std::max(m_max, m[i]);
     }
+    bool soft = false;
+    double eps2 = 0.0;
+    if (!softening(eps, o.precision == GD_MIXED, m_max, &soft, &eps2))
+        return fail(nullptr, GD_EINVAL,
+                    o.precision == GD_MIXED
+                        ? "eps too small for GD_MIXED with these masses: m / eps^3 overflows FP32 (use eps = 0, a "
+                          "larger eps or GD_FP64)"
+                        : "eps too small for these masses: m / eps^3 overflows FP64 (use eps = 0 or a larger eps)");
 
-    gd_ctx *c = new (std::nothrow) gd_ctx();
+    gd_ctx *c = gd_alloc_fails(0) ? nullptr : new (std::nothrow) gd_ctx();
     if (!c) return fail(nullptr, GD_ENOMEM, "host allocation failed");
     c->opt = o;
     c->dev = o.device;
     c->mixed = o.precision == GD_MIXED;
-    c->soft = eps > 0;
+    c->soft = soft;
     c->graph_steps = o.graph_steps;
     c->tn = default_tune(c->mixed, o.mode_cut);
     int rc = GD_OK;
@@ -742,13 +791,13 @@ int ctx_init(gd_ctx **out, int64_t n, const double *m, const double *x, const do
     d.dt_min2 = o.dt_min * o.dt_min;
     d.dtau_max = (long long)(o.dt_max / o.dt_min);
     d.eta = eta;
-    d.eps2 = eps * eps;
-    d.eps2f = (float)(eps * eps);
+    d.eps2 = eps2;
+    d.eps2f = (float)eps2;
     d.dt_min_f = (float)o.dt_min;
     d.inv_dt_min_f = (float)(1.0 / o.dt_min);
     d.eta_f = (float)eta;
     c->nchunks = (d.n + ST - 1) / ST;
-    // the select kernel's chunks wait on lower chunks: keep its grid co-resident
+    // the select kernel's CTAs wait for the counts of lower CTAs: keep its grid co-resident
     c->grid_sel = std::max(1, std::min(c->nchunks, sms * std::max(1, occ_sel)));
     c->grid_corr = std::max(1, std::min((d.n + 8 * (CT / 32) - 1) / (8 * (CT / 32)), sms * 8));
     cluster_setup(c);
@@ -766,15 +815,19 @@ int ctx_init(gd_ctx **out, int64_t n, const double *m, const double *x, const do
         (rc = dalloc(c, &d.fsum, (size_t)6 * d.n)) || (rc = dalloc(c, &d.tilecnt, ntiles)) ||
         (rc = dalloc(c, &d.status, (size_t)c->nchunks)) || (rc = dalloc(c, &d.eu, (size_t)d.n)) ||
         (rc = dalloc(c, &d.ek, (size_t)d.n)) || (rc = dalloc(c, &d.nact_hist, (size_t)64)) ||
-        (rc = dalloc(c, &d.bar, (size_t)BAR_WORDS)) || (rc = dalloc(c, &d.ctrl, (size_t)1)))
+        (rc = dalloc(c, &d.bar, (size_t)BAR_WORDS)) || (rc = dalloc(c, &d.ctrl, (size_t)1)) ||
+        (rc = dalloc(c, &d.selstat, (size_t)c->grid_sel)))
         return bail(rc);
     if (c->mixed && ((rc = dalloc(c, &d.xs, 2 * n3)) || (rc = dalloc(c, &d.vs, 2 * n3)) || (rc = dalloc(c, &d.af, n3)) ||
                      (rc = dalloc(c, &d.jf, n3)) || (rc = dalloc(c, &d.mf, (size_t)d.n))))
         return bail(rc);
-    e = cudaMallocHost((void **)&c->h_ctrl, sizeof(Ctrl));
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_hist, sizeof(int) * 64);
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_snap, 2 * sizeof(Ctrl));
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_stage, (size_t)15 * d.n * sizeof(double));
+    auto hal = [&](void **p, size_t bytes) {
+        return gd_alloc_fails(0) ? cudaErrorMemoryAllocation : cudaMallocHost(p, bytes);
+    };
+    e = hal((void **)&c->h_ctrl, sizeof(Ctrl));
+    if (e == cudaSuccess) e = hal((void **)&c->h_hist, sizeof(int) * 64);
+    if (e == cudaSuccess) e = hal((void **)&c->h_snap, 2 * sizeof(Ctrl));
+    if (e == cudaSuccess) e = hal((void **)&c->h_stage, (size_t)15 * d.n * sizeof(double));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_snap[0], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_snap[1], cudaEventDisableTiming);
     if (e != cudaSuccess) return bail(fail(c, GD_ENOMEM, "pinned host allocation failed"));
@@ -795,6 +848,7 @@ int ctx_init(gd_ctx **out, int64_t n, const double *m, const double *x, const do
     h.interactions = (double)n * (double)n;  // the initial full force evaluation
     e = cudaMemcpyAsync(d.ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.status, 0, sizeof(unsigned long long) * c->nchunks, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.selstat, 0, sizeof(unsigned long long) * c->grid_sel, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.nact_hist, 0, sizeof(int) * 64, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.act, 0, sizeof(int) * d.n, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.tilecnt, 0, sizeof(unsigned int) * ntiles, c->stream);
@@ -849,6 +903,25 @@ int gd_get_tuning(gd_ctx *c, int32_t *mode_cut, int16_t *split, int8_t *mode, fl
         if (mode) mode[b] = c->tn.mode_b[b];
         if (ms) ms[b] = c->tune_ms[b];
     }
+    return GD_OK;
+}
+
+int gd_set_tuning(gd_ctx *c, int32_t mode_cut, const int16_t *split, const int8_t *mode, int32_t nbuckets)
+{
+    int rc = check_usable(c);
+    if (rc) return rc;
+    if (nbuckets < 0 || nbuckets > 32) return fail(c, GD_EINVAL, "nbuckets must be in [0, 32]");
+    if (mode_cut < 1) return fail(c, GD_EINVAL, "mode_cut must be >= 1");
+    for (int b = 0; b < nbuckets; b++) {
+        if (split && split[b] < 0) return fail(c, GD_EINVAL, "split factors must be >= 0");
+        if (mode && (mode[b] < -1 || mode[b] > 1)) return fail(c, GD_EINVAL, "modes must be -1, 0 or 1");
+    }
+    c->tn.mode_cut = mode_cut;
+    for (int b = 0; b < nbuckets; b++) {
+        if (split) c->tn.s_fixed[b] = split[b];
+        if (mode) c->tn.mode_b[b] = mode[b];
+    }
+    drop_graph(c);  // a captured graph holds the old table
     return GD_OK;
 }
 
@@ -1078,6 +1151,14 @@ const char *gd_last_error(const gd_ctx *c)
     return c->err.c_str();
 }
 
+int gd_test_fail_alloc(int32_t kind, int32_t nth)
+{
+    if ((kind != 0 && kind != 1) || nth < 0 || nth > (1 << 20))
+        return fail(nullptr, GD_EINVAL, "kind must be 0 or 1 and nth in [0, 2^20]");
+    g_alloc_left[kind] = nth;
+    return GD_OK;
+}
+
 int gd_test_wait_timeout(gd_ctx *c, int32_t limit)
 {
     int rc = check_usable(c);
@@ -1151,6 +1232,41 @@ int gd_predict(gd_ctx *c, int64_t tick, double *xp, double *vp)
     return GD_OK;
 }
 
+int gd_step_block_small(gd_ctx *c, double *t_out, int64_t *nact_out)
+{
+    int rc = check_usable(c);
+    if (rc) return rc;
+    if (!c->cl_C) return fail(c, GD_ESTATE, "this context does not use the small-step cluster");
+    if ((rc = sync_ctrl(c))) return rc;
+    const long long nb0 = c->h_ctrl->nblock;
+    launch_cluster(c, 0, -1, 1);
+    CK(cudaGetLastError());
+    if ((rc = sync_ctrl(c))) return rc;
+    const bool took = c->h_ctrl->nblock > nb0;
+    if (t_out) *t_out = took ? (double)c->h_ctrl->T_last * c->d.dt_min : 0.0;
+    if (nact_out) *nact_out = took ? c->h_ctrl->last_nact : 0;
+    return GD_OK;
+}
+
+int gd_predict_records(gd_ctx *c, int64_t tick, double *xp, double *vp)
+{
+    int rc = check_usable(c);
+    if (rc) return rc;
+    if (tick < 0) return fail(c, GD_EINVAL, "tick must be >= 0");
+    launch_predict_all(c, tick, c->mixed);
+    if (c->mixed) {
+        k_jrec_widen<<<(c->d.n + 255) / 256, 256, 0, c->stream>>>(c->d, c->d.pd);
+        c->launches += 1;
+    }
+    CK(cudaGetLastError());
+    if ((rc = download_planes(c, c->d.pd, c->d.npad, 0, c->d.n))) return rc;
+    if ((rc = download_planes(c, c->d.pd + 3 * (size_t)c->d.npad, c->d.npad, 1, c->d.n))) return rc;
+    CK(cudaStreamSynchronize(c->stream));
+    if (xp) unstage_aos(c, xp, 0, c->d.n);
+    if (vp) unstage_aos(c, vp, 1, c->d.n);
+    return GD_OK;
+}
+
 int gd_active(gd_ctx *c, int32_t *idx, int64_t *nact, int64_t *tick_next)
 {
     int rc = check_usable(c);
@@ -1166,10 +1282,7 @@ int gd_active(gd_ctx *c, int32_t *idx, int64_t *nact, int64_t *tick_next)
     CK(cudaMemcpyAsync(idx, d.act, sizeof(int) * na, cudaMemcpyDeviceToHost, c->stream));
     k_resync<<<1, 1024, 0, c->stream>>>(d);
     c->launches += 1;
-    rc = sync_ctrl(c);
-    // the device list is in the order the chunks claimed their places
-    std::sort(idx, idx + na);
-    return rc;
+    return sync_ctrl(c);
 }
 
 int gd_replay_step(gd_ctx *c, int64_t tick_next, const int32_t *idx, int64_t nact)
@@ -1294,7 +1407,7 @@ int gd_ens_init(gd_ens **out, int32_t nclusters, const int64_t *n_per, const dou
                 }
             }
     }
-    gd_ens *s = new (std::nothrow) gd_ens();
+    gd_ens *s = gd_alloc_fails(0) ? nullptr : new (std::nothrow) gd_ens();
     if (!s) return ens_fail(nullptr, GD_ENOMEM, "host allocation failed");
     s->C = nclusters;
     s->cs = cs;
@@ -1319,7 +1432,7 @@ int gd_ens_init(gd_ens **out, int32_t nclusters, const int64_t *n_per, const dou
     gd_ctx *c = s->c;
     cudaError_t e = cudaSuccess;
     auto al = [&](void **p, size_t bytes) {
-        if (e == cudaSuccess) e = cudaMalloc(p, bytes + 16);
+        if (e == cudaSuccess) e = gd_alloc_fails(1) ? cudaErrorMemoryAllocation : cudaMalloc(p, bytes + 16);
     };
     const int ntiles = (int)(total / ENS_TILE) + nclusters + 16;
     int sms = 0, occ = 0;
@@ -1534,10 +1647,15 @@ constexpr size_t NA_OFF_JA = (NA_OFF_CNT + sizeof(unsigned int) * (size_t)NOALLO
 constexpr size_t NA_OFF_JB = NA_OFF_JA + sizeof(float4) * (size_t)NOALLOC_NMAX;
 constexpr size_t NA_OFF_JC = NA_OFF_JB + sizeof(float4) * (size_t)NOALLOC_NMAX;
 constexpr size_t NA_OFF_FSUM = NA_OFF_JC + sizeof(float2) * (size_t)NOALLOC_NMAX;
-constexpr size_t NA_OFF_PART = NA_OFF_FSUM + sizeof(double) * 6 * (size_t)NOALLOC_NMAX;
-constexpr size_t NOALLOC_BYTES = NA_OFF_PART + sizeof(float) * 6 * (size_t)NOALLOC_CAP;  // about 4.6 MiB
+// summed forces: the mixed path keeps them as FP32 (store_fsum<float>)
+constexpr size_t NA_OFF_PART = NA_OFF_FSUM + sizeof(float) * 6 * (size_t)NOALLOC_NMAX;
+constexpr size_t NOALLOC_BYTES = NA_OFF_PART + sizeof(float) * 6 * (size_t)NOALLOC_CAP;  // 3,949,056 B (3.77 MiB)
+static_assert(NOALLOC_BYTES == 3949056, "the scratch size stated in gravidy.h");
 static_assert(sizeof(Ctrl) <= NA_OFF_ACT, "control block must fit its slot");
 static_assert(NOALLOC_NMAX % BJ == 0, "the j-records are padded to whole tiles");
+static_assert(NA_OFF_JA % 16 == 0 && NA_OFF_JB % 16 == 0 && NA_OFF_JC % 16 == 0 && NA_OFF_FSUM % 16 == 0 &&
+                  NA_OFF_PART % 16 == 0,
+              "vector loads of the j-records need 16-byte alignment");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
@@ -1651,8 +1769,11 @@ extern "C" int gd_force_noalloc(int64_t n, const double *m, const double *x, con
     std::memset(&d, 0, sizeof(d));
     d.n = (int)n;
     d.npad = (int)((n + BJ - 1) / BJ * BJ);
-    d.eps2f = (float)(eps * eps);
-    d.eps2 = eps * eps;
+    bool soft = false;
+    double eps2 = 0.0;
+    softening(eps, true, -1.0, &soft, &eps2);  // the masses are on the device: no overflow check
+    d.eps2f = (float)eps2;
+    d.eps2 = eps2;
     d.ctrl = (Ctrl *)s->scratch;
     d.act = (int *)(s->scratch + NA_OFF_ACT);
     d.tilecnt = (unsigned int *)(s->scratch + NA_OFF_CNT);
@@ -1667,7 +1788,7 @@ extern "C" int gd_force_noalloc(int64_t n, const double *m, const double *x, con
     const int g = std::max((d.npad + 255) / 256, (NOALLOC_TILES + 255) / 256);
     k_noalloc_pack<<<g, 256, 0, st>>>(d, m, x, v, idx, (int)nact, bad);
     const FArgs fa{d, s->grid, tn, 0};
-    if (eps > 0)
+    if (soft)
         k_force_mixed<true, false><<<s->grid, FT, 0, st>>>(fa);
     else
         k_force_mixed<false, false><<<s->grid, FT, 0, st>>>(fa);

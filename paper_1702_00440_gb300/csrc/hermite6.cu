@@ -46,6 +46,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -550,6 +551,9 @@ struct gd_h6 {
 
 static thread_local std::string g_h6_err;
 
+// allocation-failure injection of gd_test_fail_alloc (gravidy.cu)
+bool gd_alloc_fails(int kind);
+
 namespace {
 
 int fail6(gd_h6 *s, int code, const std::string &msg)
@@ -715,7 +719,8 @@ int gd_h6_init_scheme(gd_h6 **out, int64_t n, const double *m, const double *x, 
             if (!std::isfinite(x[3 * i + q]) || !std::isfinite(v[3 * i + q]))
                 return fail6(nullptr, GD_EINVAL, "positions and velocities must be finite");
     }
-    gd_h6 *s = new gd_h6();
+    gd_h6 *s = gd_alloc_fails(0) ? nullptr : new (std::nothrow) gd_h6();
+    if (!s) return fail6(nullptr, GD_ENOMEM, "host allocation failed");
     s->dev = o.device;
     auto bail = [&](int rc) {
         g_h6_err = s->err;
@@ -745,7 +750,7 @@ int gd_h6_init_scheme(gd_h6 **out, int64_t n, const double *m, const double *x, 
     d.dtau_max = (long long)(o.dt_max / o.dt_min);
     d.cap = n + 2LL * s->grid + T6;
     auto al = [&](void **p, size_t bytes) {
-        if (cudaMalloc(p, bytes) != cudaSuccess) return false;
+        if (gd_alloc_fails(1) || cudaMalloc(p, bytes) != cudaSuccess) return false;
         s->allocs.push_back(*p);
         return true;
     };
@@ -759,8 +764,8 @@ int gd_h6_init_scheme(gd_h6 **out, int64_t n, const double *m, const double *x, 
               al((void **)&d.eu, sizeof(double) * n) && al((void **)&d.ek, sizeof(double) * n) &&
               al((void **)&d.ctrl, sizeof(Ctrl6));
     if (!ok) return bail(fail6(s, GD_ENOMEM, "device allocation failed"));
-    if (cudaMallocHost((void **)&s->h_ctrl, sizeof(Ctrl6)) != cudaSuccess ||
-        cudaMallocHost((void **)&s->h_stage, sizeof(double) * 9 * n) != cudaSuccess)
+    if (gd_alloc_fails(0) || cudaMallocHost((void **)&s->h_ctrl, sizeof(Ctrl6)) != cudaSuccess ||
+        gd_alloc_fails(0) || cudaMallocHost((void **)&s->h_stage, sizeof(double) * 9 * n) != cudaSuccess)
         return bail(fail6(s, GD_ENOMEM, "pinned host allocation failed"));
     std::memset(s->h_ctrl, 0, sizeof(Ctrl6));
     s->h_ctrl->tick_end = LLONG_MAX;

@@ -17,10 +17,13 @@
 //
 // Cost model that shapes the code: on this GPU an FP64 warp instruction holds an
 // SMSP for about 78 cycles whether 1 or 32 lanes are active, while an FP32 one
-// issues every cycle.  So FP64 appears only where the method needs it (prediction,
-// correction, step selection, energy sums, the FP64 path), every FP64 instruction
-// works on as many particles or components as possible, and the mixed force path
-// keeps its sums in FP32 with compensated (two-sum) accumulation.
+// issues every cycle.  So the mixed path keeps positions and velocities as
+// double-single values and predicts, corrects and chooses steps with FP32
+// instructions (error-free transformations where the sums need more than 24
+// bits), keeps its force sums in FP32 with compensated (two-sum) accumulation, and
+// uses FP64 only for the energy totals and the host-facing conversions; the FP64
+// path does everything in FP64, with every FP64 instruction working on as many
+// particles or components as possible.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -67,7 +70,7 @@ struct Ctrl {
     unsigned int epoch;    // step counter (parity slots of the fused kernel, look-back tag of the ensemble)
     unsigned int done;     // finished-CTA counter of k_correct
     int err;               // first device-side fault (gd_status), 0 = none
-    int pad_;
+    unsigned sel_gen;      // launches of the ordered select kernel so far (mod 2^31), see k_select_predict
     unsigned long long ph_ns[3];  // fused kernel, CTA 0's clock: select, force, correct phases
     unsigned long long sel_acc;   // select: arrived chunks (high word), active count (low word); 0 between steps
 };
@@ -124,6 +127,7 @@ struct Dev {
                               // (FP64 path; the mixed path stores floats, see fsum_f)
     unsigned int *tilecnt;    // per i-tile arrival counters (zero between launches)
     unsigned long long *status;  // ensemble look-back words, one per chunk of ST particles
+    unsigned long long *selstat; // ordered select: (generation, active count) of each select CTA
     double *eu, *ek;          // per-particle energy terms
     int *nact_hist;           // nact of each step slot of a captured graph
     unsigned int *bar;        // grid-barrier counters of the fused kernel (see grid_sync)
@@ -445,15 +449,16 @@ __device__ __forceinline__ void store_jrec(const Dev &d, int i, const double xp[
 
 // ---------------------------------------------------------------- kernel: select + predict
 
-// Predicts every particle to T = ctrl->T_cur and writes the list of the particles
-// whose next time equals T (Sec. 2.4 steps 5-6).  Each chunk of ST particles claims
-// its place in the list with one 64-bit atomic add on ctrl->sel_acc: the low word
-// counts active particles (the returned value is the chunk's offset), the high word
-// counts arrived chunks, so the chunk that arrives last knows the total, publishes
-// it as ctrl->nact and clears the word for the next step.  The list is in arrival
-// order, not ascending: every later per-particle computation (force sums over j in
-// a fixed order, correction, step choice) is independent of a particle's slot, so
-// the results do not depend on it.  `slot` >= 0 records nact in nact_hist[slot].
+// The fused kernel's selection: predicts every particle to T and writes the list
+// of the particles whose next time equals T (Sec. 2.4 steps 5-6).  Each chunk of
+// ST particles claims its place in the list with one 64-bit atomic add on
+// ctrl->sel_acc: the low word counts active particles (the returned value is the
+// chunk's offset), the high word counts arrived chunks, so the chunk that arrives
+// last knows the total, publishes it as ctrl->nact and clears the word for the
+// next step.  This list is in arrival order (k_select_predict writes the ascending
+// one): every later per-particle computation (force sums over j in a fixed order,
+// correction, step choice) is independent of a particle's slot, so the results do
+// not depend on the order.  `slot` >= 0 records nact in nact_hist[slot].
 template <bool MIXED, bool COH>
 __device__ void phase_select(const Dev &d, long long T, int slot, int nchunks, unsigned long long *Tacc)
 {
@@ -522,6 +527,20 @@ __device__ void phase_select(const Dev &d, long long T, int slot, int nchunks, u
     __syncthreads();
 }
 
+// The same prediction and selection with the active list in ascending particle
+// order, as the oracle lists it (the fused kernel keeps phase_select's arrival
+// order).  The G CTAs of the grid are co-resident (G is at most the SMs times the
+// kernel's occupancy) and CTA b owns the contiguous chunks [b R, (b + 1) R), R =
+// ceil(nchunks / G):
+//   pass 1  predict the CTA's particles, count its active ones;
+//   publish the count in selstat[b], tagged with this launch's generation;
+//   sum the counts of CTAs 0 .. b-1 (each read with a bounded wait for its tag):
+//           the CTA's offset in the list;
+//   pass 2  chunk by chunk, warp ballots and a scan of the four warp counts give
+//           each active particle its place, in particle order.
+// CTA G - 1, whose wait saw every other CTA's count (so every CTA has read the
+// generation by then), publishes N_act and advances the generation.  A wait that
+// runs out records GD_ETIMEOUT and counts the missing CTA as empty.
 template <bool MIXED>
 __global__ void __launch_bounds__(ST) k_select_predict(Dev d, int slot, int nchunks)
 {
@@ -536,7 +555,107 @@ __global__ void __launch_bounds__(ST) k_select_predict(Dev d, int slot, int nchu
         }
         return;
     }
-    phase_select<MIXED, false>(d, T, slot, nchunks, (unsigned long long *)&ctrl->T_acc);
+    __shared__ unsigned s_wcnt[ST / 32];
+    __shared__ unsigned s_part[ST / 32];
+    __shared__ long long s_wmin[ST / 32];
+    __shared__ unsigned s_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned tag = (ctrl->sel_gen & 0x7FFFFFFFu) + 1u;  // never 0 (the words start at 0)
+    const int G = gridDim.x, b = blockIdx.x;
+    const int R = (nchunks + G - 1) / G;
+    const int c0 = min(b * R, nchunks), c1 = min(c0 + R, nchunks);
+    // pass 1: predict, count (lane 0 of each warp keeps its warp's running count)
+    long long mn_all = LLONG_MAX;
+    unsigned wc = 0;
+    for (int ch = c0; ch < c1; ch++) {
+        const int i = ch * ST + threadIdx.x;
+        bool act = false;
+        if (i < d.n) {
+            const long long tn = d.tnext[i];
+            act = (tn == T);
+            if (!act) mn_all = tn < mn_all ? tn : mn_all;
+            const long long dtick = T - d.tau[i];
+            if (MIXED) {
+                predict_store_ds<false>(d, i, dtick);
+            } else {
+                double xp[3], vp[3];
+                predict64<false>(d, i, (double)dtick * d.dt_min, xp, vp);
+                store_jrec<false>(d, i, xp, vp, d.m[i]);
+            }
+        }
+        wc += __popc(__ballot_sync(0xffffffffu, act));
+    }
+    if (lane == 0) s_wcnt[warp] = wc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned tot = 0;
+#pragma unroll
+        for (int w = 0; w < ST / 32; w++) tot += s_wcnt[w];
+        __threadfence();
+        atomicExch(&d.selstat[b], ((unsigned long long)tag << 32) | tot);
+    }
+    // this CTA's offset: the counts of CTAs 0 .. b-1
+    unsigned part = 0;
+    for (int q = threadIdx.x; q < b; q += ST) {
+        unsigned long long w = ld_volatile_u64(&d.selstat[q]);
+        int spins = 0;
+        while ((unsigned)(w >> 32) != tag) {
+            if (++spins > SPIN_LIMIT) {
+                set_err(ctrl, ST_ETIMEOUT);
+                w = (unsigned long long)tag << 32;
+                break;
+            }
+            __nanosleep(32);
+            w = ld_volatile_u64(&d.selstat[q]);
+        }
+        part += (unsigned)w;
+    }
+    __threadfence();
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) s_part[warp] = part;
+    __syncthreads();
+    unsigned base = 0;
+#pragma unroll
+    for (int w = 0; w < ST / 32; w++) base += s_part[w];
+    // pass 2: places in particle order
+    for (int ch = c0; ch < c1; ch++) {
+        const int i = ch * ST + threadIdx.x;
+        const bool act = i < d.n && d.tnext[i] == T;
+        const unsigned ballot = __ballot_sync(0xffffffffu, act);
+        __syncthreads();  // the previous chunk's reads of s_wcnt are done
+        if (lane == 0) s_wcnt[warp] = __popc(ballot);
+        __syncthreads();
+        unsigned off = base, tot = 0;
+#pragma unroll
+        for (int w = 0; w < ST / 32; w++) {
+            const unsigned cw = s_wcnt[w];
+            off += w < warp ? cw : 0u;
+            tot += cw;
+        }
+        if (act) {
+            const unsigned pos = off + __popc(ballot & ((1u << lane) - 1u));
+            if (pos < (unsigned)d.n) d.act[pos] = i;
+        }
+        base += tot;
+    }
+    if (b == G - 1 && threadIdx.x == 0) {
+        unsigned long long na = base;
+        if (na > (unsigned long long)d.n) {
+            set_err(ctrl, ST_ETIMEOUT);
+            na = 0;
+        }
+        ctrl->nact = (int)na;
+        if (slot >= 0) d.nact_hist[slot] = (int)na;
+        ctrl->sel_gen = tag & 0x7FFFFFFFu;
+    }
+    // minimum next time of the inactive particles -> next block time candidate
+    long long mn = warp_min_ll(mn_all);
+    if (lane == 0) s_wmin[warp] = mn;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < ST / 32; w++) mn = s_wmin[w] < mn ? s_wmin[w] : mn;
+        if (mn != LLONG_MAX) atomicMin((unsigned long long *)&ctrl->T_acc, (unsigned long long)mn);
+    }
 }
 
 // Predict all particles to `tick` (no selection): the hooks, gd_energy and the
@@ -589,6 +708,23 @@ __global__ void k_fsum_widen(Dev d, int rows, double *dst)
     for (int c = 0; c < 6; c++) dst[(long long)c * rows + k] = (double)fs[(long long)c * d.n + k];
 }
 
+// Mixed path: the predicted j-records widened to FP64 planes dst (stride npad):
+// x = hi + lo (exact), v the record's FP32 value (the predictor hook's download).
+__global__ void k_jrec_widen(Dev d, double *dst)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.n) return;
+    const int np = d.npad;
+    const float4 A = d.jA[i], B = d.jB[i];
+    const float2 C = d.jC[i];
+    dst[0 * np + i] = (double)A.x + (double)B.x;
+    dst[1 * np + i] = (double)A.y + (double)B.y;
+    dst[2 * np + i] = (double)A.z + (double)B.z;
+    dst[3 * np + i] = (double)B.w;
+    dst[4 * np + i] = (double)C.x;
+    dst[5 * np + i] = (double)C.y;
+}
+
 __global__ void k_state_from_ds(Dev d)
 {
     const int n = d.n;
@@ -626,6 +762,10 @@ __global__ void k_init_pads(Dev d)
 // on double-single positions: r = x_j - x_i from the hi and lo parts separately, so
 // the difference keeps the bits of the FP64 positions.
 //   a += m r / s^3,   jerk += m (v - 3 (r.v) r / s^2) / s^3,   s^2 = r^2 + eps^2
+// m / s^3 takes one Newton step on rsqrt.approx (y^3 (1 + 3/2 (1 - s^2 y^2)), the
+// residual from one FMA): without it the approximation's error, common to all six
+// components of a term, sets the per-particle jerk error of particles whose terms
+// cancel (measured p99 of |d jerk| / |jerk| 1.0-1.2e-6 without, 0.65-1.0e-6 with).
 template <bool SOFT>
 __device__ __forceinline__ void pair_mixed(const float4 A, const float4 B, const float2 C, const float xh,
                                            const float yh, const float zh, const float xl, const float yl,
@@ -641,7 +781,8 @@ __device__ __forceinline__ void pair_mixed(const float4 A, const float4 B, const
     float rinv = rsqrt_approx(r2);
     if (!SOFT) rinv = r2 > 0.f ? rinv : 0.f;
     const float rinv2 = rinv * rinv;
-    const float mr3 = A.w * rinv * rinv2;
+    const float e = fmaf(-r2, rinv2, 1.0f);
+    const float mr3 = fmaf(A.w * rinv * rinv2, 1.5f * e, A.w * rinv * rinv2);
     const float b = -3.f * rv * rinv2;
     f[0] = fmaf(mr3, dx, f[0]);
     f[1] = fmaf(mr3, dy, f[1]);

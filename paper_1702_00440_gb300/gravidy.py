@@ -26,7 +26,7 @@ _PRECISION = {"fp64": GD_FP64, "mixed": GD_MIXED, GD_FP64: GD_FP64, GD_MIXED: GD
 EXPORTS = (
     "gd_opts_default", "gd_init", "gd_evolve", "gd_step_block", "gd_energy", "gd_get_state",
     "gd_set_state", "gd_get_stats", "gd_kernel_time", "gd_free", "gd_last_error", "gd_force",
-    "gd_predict", "gd_active", "gd_replay_step", "gd_test_wait_timeout", "gd_force_noalloc", "gd_autotune", "gd_get_tuning",
+    "gd_predict", "gd_predict_records", "gd_step_block_small", "gd_active", "gd_replay_step", "gd_test_wait_timeout", "gd_test_fail_alloc", "gd_force_noalloc", "gd_autotune", "gd_get_tuning", "gd_set_tuning",
     "gd_cluster_info", "gd_cluster_time",
     "gd_ens_init", "gd_ens_evolve", "gd_ens_step_block", "gd_ens_energy", "gd_ens_get_state",
     "gd_ens_get_stats", "gd_ens_free", "gd_ens_last_error",
@@ -110,12 +110,16 @@ def load(build_if_missing: bool = True):
             "gd_last_error": (ctypes.c_char_p, [P]),
             "gd_force": (ctypes.c_int, [P, I64, P, I64, P, P]),
             "gd_predict": (ctypes.c_int, [P, I64, P, P]),
+            "gd_predict_records": (ctypes.c_int, [P, I64, P, P]),
+            "gd_step_block_small": (ctypes.c_int, [P, P, P]),
             "gd_active": (ctypes.c_int, [P, P, P, P]),
             "gd_replay_step": (ctypes.c_int, [P, I64, P, I64]),
             "gd_test_wait_timeout": (ctypes.c_int, [P, I32]),
+            "gd_test_fail_alloc": (ctypes.c_int, [I32, I32]),
             "gd_force_noalloc": (ctypes.c_int, [I64, P, P, P, D, P, I64, P, P, P]),
             "gd_autotune": (ctypes.c_int, [P, I32]),
             "gd_get_tuning": (ctypes.c_int, [P, P, P, P, P, I32]),
+            "gd_set_tuning": (ctypes.c_int, [P, I32, P, P, I32]),
             "gd_ens_init": (ctypes.c_int, [P, I32, P, P, P, P, D, D, P]),
             "gd_ens_evolve": (ctypes.c_int, [P, D]),
             "gd_ens_step_block": (ctypes.c_int, [P, P, P]),
@@ -209,6 +213,13 @@ def gd_step_block(ctx):
     return t.value, k.value
 
 
+def gd_step_block_small(ctx):
+    t = ctypes.c_double()
+    k = ctypes.c_int64()
+    _check(load().gd_step_block_small(ctx, ctypes.byref(t), ctypes.byref(k)), ctx)
+    return t.value, k.value
+
+
 def gd_energy(ctx):
     K = ctypes.c_double()
     U = ctypes.c_double()
@@ -285,6 +296,13 @@ def gd_get_tuning(ctx):
     return mc.value, split, mode, ms
 
 
+def gd_set_tuning(ctx, mode_cut, split, mode):
+    split = np.ascontiguousarray(split, np.int16)
+    mode = np.ascontiguousarray(mode, np.int8)
+    nb = min(split.size, mode.size, 32)
+    _check(load().gd_set_tuning(ctx, int(mode_cut), _p(split), _p(mode), nb), ctx)
+
+
 def gd_free(ctx):
     if ctx is not None and ctx.value:
         load().gd_free(ctx)
@@ -306,6 +324,13 @@ def gd_predict(ctx, n, tick):
     return xp, vp
 
 
+def gd_predict_records(ctx, n, tick):
+    xp = np.empty((n, 3))
+    vp = np.empty((n, 3))
+    _check(load().gd_predict_records(ctx, int(tick), _p(xp), _p(vp)), ctx)
+    return xp, vp
+
+
 def gd_active(ctx, n):
     idx = np.empty(n, np.int32)
     k = ctypes.c_int64()
@@ -317,6 +342,13 @@ def gd_active(ctx, n):
 def gd_replay_step(ctx, tick, idx):
     idx = np.ascontiguousarray(idx, dtype=np.int32)
     _check(load().gd_replay_step(ctx, int(tick), _p(idx), idx.shape[0]), ctx)
+
+
+def gd_test_fail_alloc(kind, nth):
+    """Make the nth host (kind 0) or device (kind 1) allocation of the calling
+    thread's next context set-ups fail once (nth = 0 cancels)."""
+    rc = load().gd_test_fail_alloc(int(kind), int(nth))
+    _check(rc)
 
 
 def gd_force_noalloc(n, m_ptr, x_ptr, v_ptr, eps, idx_ptr, nact, acc_ptr, jerk_ptr, stream=None):
@@ -384,6 +416,9 @@ class Integrator:
     def cluster_time(self):
         return gd_cluster_time(self._h)
 
+    def set_tuning(self, mode_cut, split, mode):
+        gd_set_tuning(self._h, mode_cut, split, mode)
+
     def tuning(self):
         return gd_get_tuning(self._h)
 
@@ -392,6 +427,12 @@ class Integrator:
 
     def predict(self, tick):
         return gd_predict(self._h, self.n, tick)
+
+    def step_block_small(self):
+        return gd_step_block_small(self._h)
+
+    def predict_records(self, tick):
+        return gd_predict_records(self._h, self.n, tick)
 
     def active(self):
         return gd_active(self._h, self.n)

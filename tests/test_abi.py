@@ -97,3 +97,78 @@ def test_wait_probe_rejects_a_null_context_on_the_host():
 def test_opts_defaults():
     o = gravidy.make_opts()
     assert o.dt_min == 2.0 ** -22 and o.dt_max == 0.125 and o.precision == gravidy.GD_MIXED
+
+
+def _have_gpu():
+    try:
+        import torch
+    except ImportError:
+        return False
+    return torch.cuda.is_available()
+
+
+def _small_system():
+    n = 4
+    return n, np.full(n, 0.25), np.arange(12, dtype=float).reshape(4, 3), np.zeros((4, 3))
+
+
+@pytest.mark.parametrize("entry", ["gd_init", "gd_h6_init", "gd_ens_init"])
+def test_injected_host_allocation_failure_returns_enomem(entry):
+    """A host allocation that fails during a context's set-up is reported as
+    GD_ENOMEM with a message and leaves no context behind; the injection is
+    one-shot, so the same call afterwards gets past that allocation (on a
+    machine without a GPU it then stops at the first CUDA call instead)."""
+    lib = gravidy.load()
+    n, m, x, v = _small_system()
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    o = gravidy.make_opts()
+    sizes = np.array([n], dtype=np.int64)
+
+    def call():
+        h = ctypes.c_void_p()
+        if entry == "gd_init":
+            rc = lib.gd_init(ctypes.byref(h), n, p(m), p(x), p(v), 1e-4, 0.01, ctypes.byref(o))
+            msg = lib.gd_last_error(None)
+        elif entry == "gd_h6_init":
+            rc = lib.gd_h6_init(ctypes.byref(h), n, p(m), p(x), p(v), 1e-4, 0.01, 0.001, ctypes.byref(o))
+            msg = lib.gd_h6_last_error(None)
+        else:
+            rc = lib.gd_ens_init(ctypes.byref(h), 1, p(sizes), p(m), p(x), p(v), 1e-4, 0.01, ctypes.byref(o))
+            msg = lib.gd_ens_last_error(None)
+        return rc, msg.decode(), h
+
+    gravidy.gd_test_fail_alloc(0, 1)
+    rc, msg, h = call()
+    assert rc == gravidy.GD_ENOMEM
+    assert "allocation" in msg
+    assert not h.value
+    if _have_gpu():
+        return
+    rc, msg, h = call()
+    assert rc == gravidy.GD_ECUDA and not h.value
+
+
+def test_fail_alloc_hook_rejects_bad_arguments():
+    lib = gravidy.load()
+    assert lib.gd_test_fail_alloc(2, 1) == gravidy.GD_EINVAL
+    assert lib.gd_test_fail_alloc(0, -1) == gravidy.GD_EINVAL
+    assert lib.gd_test_fail_alloc(1, 0) == gravidy.GD_OK
+
+
+def test_tiny_softening_is_checked_against_the_masses_on_the_host():
+    """The softened self term m / eps^3 must be finite in the pair arithmetic's
+    precision: eps = 1e-14 with unit masses overflows FP32 (mixed) but not FP64."""
+    lib = gravidy.load()
+    n, m, x, v = _small_system()
+    m = np.ones(n)
+    for prec, want in (("mixed", gravidy.GD_EINVAL), ("fp64", None)):
+        o = gravidy.make_opts(precision=prec)
+        h = ctypes.c_void_p()
+        p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        rc = lib.gd_init(ctypes.byref(h), n, p(m), p(x), p(v), 1e-14, 0.01, ctypes.byref(o))
+        if want is not None:
+            assert rc == want and "eps" in lib.gd_last_error(None).decode()
+        else:
+            assert rc != gravidy.GD_EINVAL
+            if h.value:
+                lib.gd_free(h)

@@ -38,3 +38,41 @@ def test_bounded_wait_runs_out_and_is_reported():
     a, j = oracle.force(m, x, v, EPS)
     assert np.abs(acc - a).max() <= 1e-12 * np.abs(a).max()
     assert abs((K1 + U1) - (K0 + U0)) <= 1e-6 * abs(K0 + U0)
+
+
+@pytest.mark.parametrize("entry", ["single", "h6", "ensemble"])
+def test_injected_device_allocation_failures_return_enomem_without_leaks(entry):
+    """Every device allocation of a context's set-up, made to fail in turn
+    (gd_test_fail_alloc), is reported as GD_ENOMEM; the set-up frees what it
+    had allocated (device memory returns to its level before), and the next
+    set-up succeeds."""
+    torch = pytest.importorskip("torch")
+    n = 100000  # planes of 2.4 MB, so a leaked allocation shows in the free memory
+    m, x, v = inputs.plummer(n, seed=3)
+
+    def make():
+        if entry == "single":
+            return gravidy.Integrator(m, x, v, EPS, ETA, precision="mixed", cluster=False)
+        if entry == "h6":
+            return gravidy.Integrator6(m, x, v, EPS, ETA)
+        return gravidy.Ensemble([n // 2, n - n // 2], m, x, v, EPS, ETA)
+
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    failures = 0
+    for k in range(1, 64):
+        gravidy.gd_test_fail_alloc(1, k)
+        try:
+            g = make()
+        except gravidy.GravidyError as e:
+            assert e.code == gravidy.GD_ENOMEM
+            failures += 1
+            continue
+        # k is beyond the set-up's allocations: it succeeded; cancel and stop
+        gravidy.gd_test_fail_alloc(1, 0)
+        g.close()
+        break
+    assert failures >= 5
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free0 - free1 <= 8 << 20, (free0, free1)

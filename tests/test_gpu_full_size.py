@@ -23,7 +23,7 @@ EPS = 1e-4
 ETA = 0.01
 DT_MIN = 2.0 ** -22
 U32 = 2.0 ** -24
-MIXED_TERM_BOUND = 160 * U32
+MIXED_TERM_BOUND = 16 * U32
 
 
 def fp64_term_bound(n):
@@ -53,6 +53,8 @@ def big_ctx(big):
 
 
 def _sampled_check(m, x, v, idx, a, j, prec, nsample, seed):
+    """Per component within the term-scaled bound on a seeded sample of the
+    active set; returns the per-particle relative errors of a and jerk."""
     rng = np.random.default_rng(seed)
     pick = rng.choice(idx.size, size=min(nsample, idx.size), replace=False)
     sub = idx[pick]
@@ -61,9 +63,14 @@ def _sampled_check(m, x, v, idx, a, j, prec, nsample, seed):
     bound = MIXED_TERM_BOUND if prec == "mixed" else fp64_term_bound(m.size)
     ra = np.abs(a[pick] - a_or).max(axis=1) / an
     rj = np.abs(j[pick] - j_or).max(axis=1) / jn
-    rel = np.linalg.norm(a[pick] - a_or, axis=1) / np.linalg.norm(a_or, axis=1)
+    rel_a = np.linalg.norm(a[pick] - a_or, axis=1) / np.linalg.norm(a_or, axis=1)
+    rel_j = np.linalg.norm(j[pick] - j_or, axis=1) / np.linalg.norm(j_or, axis=1)
+    print("%s n=%d nact=%d sample %d: max|da|/sum|a_j| %.2e max|dj|/sum|j_j| %.2e  rel a med %.2e p99 %.2e max "
+          "%.2e  rel j med %.2e p99 %.2e max %.2e"
+          % (prec, m.size, idx.size, pick.size, ra.max(), rj.max(), np.median(rel_a), np.percentile(rel_a, 99),
+             rel_a.max(), np.median(rel_j), np.percentile(rel_j, 99), rel_j.max()))
     assert ra.max() <= bound and rj.max() <= bound, (ra.max(), rj.max())
-    return np.median(rel)
+    return rel_a, rel_j
 
 
 @pytest.mark.parametrize("nact", [1, 32, 1024, 32768, 1 << 20])
@@ -72,8 +79,10 @@ def test_force_n2p20_mixed(big, big_ctx, nact):
     n = m.size
     idx = np.arange(n, dtype=np.int32) if nact == n else inputs.random_subset(n, nact, seed=nact)
     a, j = big_ctx["mixed"].force(0, idx)
-    med = _sampled_check(m, x, v, idx, a, j, "mixed", 48, nact)
-    assert med <= 1e-6
+    rel_a, rel_j = _sampled_check(m, x, v, idx, a, j, "mixed", 256, nact)
+    assert np.median(rel_a) <= 1e-6 and np.median(rel_j) <= 1e-6
+    if rel_a.size >= 200:
+        assert np.percentile(rel_a, 99) <= 1e-6 and np.percentile(rel_j, 99) <= 1e-6
 
 
 @pytest.mark.parametrize("nact", [1, 32, 1024, 32768])
@@ -81,8 +90,8 @@ def test_force_n2p20_fp64(big, big_ctx, nact):
     m, x, v = big
     idx = inputs.random_subset(m.size, nact, seed=nact)
     a, j = big_ctx["fp64"].force(0, idx)
-    med = _sampled_check(m, x, v, idx, a, j, "fp64", 48, nact)
-    assert med <= 1e-12
+    rel_a, rel_j = _sampled_check(m, x, v, idx, a, j, "fp64", 48, nact)
+    assert np.median(rel_a) <= 1e-12
 
 
 def test_force_error_on_64_snapshots_n16384():
@@ -109,18 +118,26 @@ def test_force_error_on_64_snapshots_n16384():
             for prec, ctx in (("mixed", g), ("fp64", h)):
                 a, j = ctx.force(tick, idx)
                 bound = MIXED_TERM_BOUND if prec == "mixed" else fp64_term_bound(m.size)
-                # both sides predict in FP64 but in different operation orders: positions
-                # may differ by a few ulp (~1e-15), which a term amplifies by up to
-                # 3 |x| / r with r >= eps = 1e-4, so allow 3e-11 of the term sum
+                # the FP64 context predicts in FP64 in another operation order than the
+                # oracle: positions may differ by a few ulp (~1e-15), which a term
+                # amplifies by up to 3 |x| / r with r >= eps = 1e-4, so allow 3e-11 of the
+                # term sum; the mixed context predicts in double-single (positions to
+                # about 2^-48 of |x|, the same order of difference) and rounds the
+                # predicted velocities to FP32, the rounding its j-records always carry
+                # and part of the term bound
                 assert (np.abs(a - a_or).max(axis=1) <= (bound + 3e-11) * an).all()
                 assert (np.abs(j - j_or).max(axis=1) <= (bound + 3e-11) * jn).all()
-                errs[prec].extend((np.linalg.norm(a - a_or, axis=1) / np.linalg.norm(a_or, axis=1)).tolist())
-    for prec, e in errs.items():
-        e = np.array(e)
-        print("%s: %d samples, rel |da|/|a| median %.2e p99 %.2e max %.2e"
-              % (prec, e.size, np.median(e), np.percentile(e, 99), e.max()))
-    assert np.median(errs["mixed"]) <= 1e-6
-    assert np.median(errs["fp64"]) <= 1e-12
+                errs[prec].append((np.linalg.norm(a - a_or, axis=1) / np.linalg.norm(a_or, axis=1),
+                                   np.linalg.norm(j - j_or, axis=1) / np.linalg.norm(j_or, axis=1)))
+    for prec in errs:
+        ea = np.concatenate([q[0] for q in errs[prec]])
+        ej = np.concatenate([q[1] for q in errs[prec]])
+        print("%s: %d samples, rel |da|/|a| median %.2e p99 %.2e max %.2e; |dj|/|j| median %.2e p99 %.2e max %.2e"
+              % (prec, ea.size, np.median(ea), np.percentile(ea, 99), ea.max(), np.median(ej),
+                 np.percentile(ej, 99), ej.max()))
+        tol = 1e-6 if prec == "mixed" else 1e-12
+        assert np.median(ea) <= tol and np.median(ej) <= tol
+        assert np.percentile(ea, 99) <= tol and np.percentile(ej, 99) <= tol
 
 
 def test_powerlaw_n262144_forces_and_invariants():
@@ -131,9 +148,11 @@ def test_powerlaw_n262144_forces_and_invariants():
     with gravidy.Integrator(m, x, v, EPS, ETA, precision="mixed") as g:
         idx = np.arange(n, dtype=np.int32)
         a, j = g.force(0, idx)
-        _sampled_check(m, x, v, idx, a, j, "mixed", 32, 5)
+        rel_a, rel_j = _sampled_check(m, x, v, idx, a, j, "mixed", 256, 5)
+        # power-law masses: the jerk's tail of cancelling sums is longer than for equal masses
+        assert np.percentile(rel_a, 99) <= 1e-6 and np.percentile(rel_j, 99) <= 1.5e-6
         # Newton's third law over the whole evaluation (holds at any size):
-        # |sum m a| <= sum m |error| <= 160 2^-24 sum_i m_i sum_j |term_ij|, the last sum
+        # |sum m a| <= sum m |error| <= 16 2^-24 sum_i m_i sum_j |term_ij|, the last sum
         # estimated from 256 sampled particles (times 2 for the estimate's spread)
         sample = inputs.random_subset(n, 256, seed=11)
         an_s, _ = oracle.force_absnorm(m, x, v, EPS, sample)

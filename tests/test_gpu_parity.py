@@ -3,12 +3,18 @@
 Tolerances:
   FP64 path   per-particle |a_gpu - a_oracle| / |a| <= 1e-12 (force/jerk), plus a
               round-off bound scaled by the sum of term magnitudes.
-  mixed path  FP32 pair arithmetic on double-single positions, FP32 sums over at
-              most 128 consecutive terms folded into FP64.  One term carries about
-              8 units of 2^-24 (difference, r^2, rsqrt.approx, three products); the
-              per-tile FP32 sum adds up to 128 units in the worst case, so
-              |a_gpu - a_oracle|_component <= 2^-24 * 160 * sum_j |term_j|  (~1e-5),
-              and the per-particle relative error's median is held to <= 1e-6.
+  mixed path  FP32 pair arithmetic on double-single positions (m / s^3 with one
+              Newton step on rsqrt.approx), FP32 sums over the terms of one j-tile
+              folded into compensated sums.  Per component the error stays below
+              16 units of 2^-24 times sum_j |term_j| (measured at most 8 units: a term
+              carries a few units from the difference, r^2, the refined rsqrt and the
+              products, and a tile's FP32 sum adds rounding errors that mostly
+              cancel).  Per particle, |a_gpu - a_oracle| / |a| and the same for the
+              jerk are held to <= 1e-6 at the median and, over sets of at least 200
+              particles, at the 99th percentile.  The largest per-particle errors
+              belong to particles whose terms cancel (sum_j |term_j| / |jerk| up to
+              about 700): measured up to 1.1e-6 for a and 1.1e-5 for the jerk; the
+              per-component bound above holds for them too.
 """
 import numpy as np
 import pytest
@@ -22,7 +28,10 @@ EPS = 1e-4
 ETA = 0.01
 DT_MIN = 2.0 ** -22
 U32 = 2.0 ** -24
-MIXED_TERM_BOUND = 160 * U32
+MIXED_TERM_BOUND = 16 * U32
+# the mixed path's 99th percentile of |d jerk| / |jerk| for power-law masses (dN/dm ~ m^-2.35
+# over a factor 100): measured 1.0-1.07e-6 at N = 5000, against 0.65-0.9e-6 for equal masses
+POWER_LAW_JERK_P99 = 1.5e-6
 
 
 def fp64_term_bound(n):
@@ -39,7 +48,7 @@ def _lib():
     oracle.build()
 
 
-def _check_force(prec, m, x, v, eps, idx, label="", **opts):
+def _check_force(prec, m, x, v, eps, idx, label="", jerk_p99=1e-6, **opts):
     n = m.shape[0]
     with gravidy.Integrator(m, x, v, eps, ETA, precision=prec, **opts) as g:
         a, j = g.force(0, idx)
@@ -61,6 +70,8 @@ def _check_force(prec, m, x, v, eps, idx, label="", **opts):
         assert np.percentile(rel_a, 99) <= 1e-12
     else:
         assert np.median(rel_a) <= 1e-6 and np.median(rel_j) <= 1e-6
+        if idx.size >= 200:
+            assert np.percentile(rel_a, 99) <= 1e-6 and np.percentile(rel_j, 99) <= jerk_p99
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -88,7 +99,9 @@ def test_force_subsets_split(prec, nact, mode_cut):
     n = 5000
     m, x, v = inputs.plummer(n, seed=7, masses=inputs.power_law_masses(n, seed=7))
     idx = inputs.random_subset(n, nact, seed=nact)
-    _check_force(prec, m, x, v, EPS, idx, label="subset mc=%d" % mode_cut, mode_cut=mode_cut)
+    # power-law masses: the mixed jerk's tail of cancelling sums reaches about 1.1e-6 at p99
+    _check_force(prec, m, x, v, EPS, idx, label="subset mc=%d" % mode_cut, jerk_p99=POWER_LAW_JERK_P99,
+                 mode_cut=mode_cut)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -185,6 +198,10 @@ def test_predictor_matches_oracle():
 @pytest.mark.parametrize("n", [1, 31, 128, 129, 4097, 300001])
 @pytest.mark.parametrize("pattern", ["random", "all", "first", "last", "sparse"])
 def test_active_list_bit_exact(n, pattern):
+    """The compaction's list as it sits in device memory (gd_active copies it
+    out unchanged) equals the oracle's ascending list element by element, with
+    the same block time; at n = 300001 the select grid's CTAs own several
+    chunks each and a ragged last one."""
     rng = np.random.default_rng(n)
     m, x, v = inputs.plummer(n, seed=2)
     a = np.zeros((n, 3))
