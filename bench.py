@@ -76,7 +76,7 @@ def _args():
                    help="profiling hook: initialise an N-particle Plummer sphere (one full force evaluation), "
                         "evaluate all N once more, print nothing and exit")
     p.add_argument("--sweep", choices=["force", "powerlaw", "accuracy", "ensemble", "eta", "soft", "lagrange", "h6",
-                                          "timesym", "collapse"],
+                                          "timesym", "collapse", "fp32peak", "cluster"],
                    help="extra measurements, one JSON line each (not the benchmark line): force = "
                         "full evaluations N=2^10..2^20 and N=2^20 with active sets 1..2^20; powerlaw = "
                         "N=262144 power-law masses to t=1/8 (active-set histogram, interactions/s per "
@@ -88,7 +88,10 @@ def _args():
                         "h6 = sixth- vs fourth-order Hermite: cost and |dE/E| to t=1, and the snap kernel's rate; "
                         "timesym = the time-symmetric schemes (order 4 and 6, one and two passes): cost and |dE/E| "
                         "to t=1, energy drift and reversibility on a Kepler orbit with shared constant steps; "
-                        "collapse = core collapse of an N=1024 Plummer sphere (Lagrange radii, |dE/E|)")
+                        "collapse = core collapse of an N=1024 Plummer sphere (Lagrange radii, |dE/E|); "
+                        "fp32peak = the FP32 FMA throughput probe (the force kernels' roofline denominator) with "
+                        "the SM clock sampled during it; cluster = where the small-step cluster's time goes on "
+                        "the --n workload over one N-body unit (phase cycle counters, per small step)")
     p.add_argument("--ens-t", type=float, default=0.125)
     p.add_argument("--collapse-trh", type=float, default=30.0,
                    help="--sweep collapse: stop at this many half-mass relaxation times")
@@ -581,6 +584,25 @@ def _oracle_cluster_job(job):
     return sim.stats()["interactions"], time.perf_counter() - t0
 
 
+def _oracle_compare_job(job):
+    """One ensemble cluster: the oracle's run to t and the energy errors of its
+    state and of the GPU's state at t, both by the oracle's FP64 energy function:
+    (cluster, interactions, s, |dE/E| GPU, |dE/E| oracle)."""
+    q, n, seed, t_end, xg, vg = job
+    import oracle
+    from paper_1702_00440_gb300 import inputs
+
+    m, x, v = inputs.plummer(int(n), seed=int(seed))
+    E0 = sum(oracle.energy(m, x, v, EPS))
+    Eg = sum(oracle.energy(m, xg, vg, EPS))
+    t0 = time.perf_counter()
+    sim = oracle.Sim(m, x, v, EPS, ETA)
+    sim.evolve(t_end)
+    wall = time.perf_counter() - t0
+    Eo = sum(sim.energy())
+    return q, sim.stats()["interactions"], wall, abs((Eg - E0) / E0), abs((Eo - E0) / E0)
+
+
 def _oracle_force_job(job):
     """Oracle force of a slice of active particles against all n: (count, s)."""
     n, idx = job
@@ -762,13 +784,20 @@ def sweep_ensemble(a):
         xs.append(x)
         vs.append(v)
     t_end = a.ens_t
+    t_cmp = min(DT_STEP, t_end)  # every cluster compared with the oracle here
     e = gravidy.Ensemble(sizes, np.concatenate(ms), np.concatenate(xs), np.concatenate(vs), EPS, ETA)
     K0, U0 = e.energy()
     s0 = e.stats()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    e.evolve(t_end)
+    e.evolve(t_cmp)
     wall_ens = time.perf_counter() - t0
+    st_cmp = e.state()  # every particle at t_cmp (a multiple of dt_max)
+    if t_end > t_cmp:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e.evolve(t_end)
+        wall_ens += time.perf_counter() - t0
     K1, U1 = e.energy()
     s1 = e.stats()
     e.close()
@@ -788,32 +817,77 @@ def sweep_ensemble(a):
         steps_seq += st1["block_steps"] - st0["block_steps"]
         g.close()
     inter_ens = s1["interactions"] - s0["interactions"]
+    # the cooperative form: select and force + correction of a global step in one
+    # launch with a grid barrier between them, one step or 64 steps per launch
+    fused = {}
+    for spl in (1, 64):
+        e = gravidy.Ensemble(sizes, np.concatenate(ms), np.concatenate(xs), np.concatenate(vs), EPS, ETA,
+                             fused=True, graph_steps=spl)
+        sf0 = e.stats()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e.evolve(t_end)
+        wf = time.perf_counter() - t0
+        sf1 = e.stats()
+        e.close()
+        fused["steps_per_launch_%d" % spl] = {
+            "wall_s": wf, "global_block_steps": sf1["block_steps"] - sf0["block_steps"],
+            "interactions_per_s": (sf1["interactions"] - sf0["interactions"]) / wf,
+            "same_steps_as_two_kernel": sf1["block_steps"] - sf0["block_steps"] == s1["block_steps"] - s0["block_steps"]}
     out = {"sweep": "ensemble", "clusters": int(sizes.size), "particles": int(sizes.sum()),
            "n_min": int(sizes.min()), "n_max": int(sizes.max()), "t_end": t_end,
            "ensemble": {"wall_s": wall_ens, "global_block_steps": s1["block_steps"] - s0["block_steps"],
                         "interactions_per_s": inter_ens / wall_ens},
+           "fused": fused,
            "one_by_one": {"wall_s": wall_seq, "block_steps": steps_seq, "interactions_per_s": inter_seq / wall_seq},
            "speedup": wall_seq / wall_ens,
            "dE_E": {"median": float(np.median(de)), "max": float(de.max())}}
-    # the oracle on the host: every cluster to a short t_cpu, all host cores (one
-    # cluster per worker at a time), and every 8th cluster on one core
-    t_cpu = 1.0 / 64
+    # every cluster through the oracle to t_cmp on all host cores (one cluster per
+    # worker at a time), with the energy error of the oracle's run and of the GPU
+    # ensemble's state at t_cmp, both from the oracle's FP64 energy function
     cores = _host_cores()
-    jobs = [(q, int(nq), 1000 + q, t_cpu) for q, nq in enumerate(sizes)]
-    jobs_sorted = sorted(jobs, key=lambda j: -j[1])  # large clusters first
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    cjobs = [(q, int(nq), 1000 + q, t_cmp, st_cmp["x"][offs[q]:offs[q + 1]], st_cmp["v"][offs[q]:offs[q + 1]])
+             for q, nq in enumerate(sizes)]
+    cjobs.sort(key=lambda j: -j[1])  # large clusters first
     t0 = time.perf_counter()
     with _pool(cores) as pool:
-        res = pool.map(_oracle_cluster_job, jobs_sorted, chunksize=1)
-    wall_all = time.perf_counter() - t0
-    inter_all = sum(r[0] for r in res)
+        cres = pool.map(_oracle_compare_job, cjobs, chunksize=1)
+    wall_cmp = time.perf_counter() - t0
+    cres.sort(key=lambda r: r[0])
+    de_gpu = np.array([r[3] for r in cres])
+    de_or = np.array([r[4] for r in cres])
+    ratio = de_gpu / np.maximum(de_or, 1e-300)
+    within2 = de_gpu <= 2 * de_or + 1e-12
+    big = de_or >= 1e-9  # above the floor the FP32 force arithmetic sets on a short run
+    worst = int(np.argmax(ratio))
+    out["per_cluster_vs_oracle"] = {
+        "t": t_cmp, "clusters": len(cres), "energy": "oracle FP64 energy function on both states",
+        "dE_E_gpu": {"median": float(np.median(de_gpu)), "max": float(de_gpu.max())},
+        "dE_E_oracle": {"median": float(np.median(de_or)), "max": float(de_or.max())},
+        "ratio_gpu_over_oracle": {"median": float(np.median(ratio)), "p5": float(np.percentile(ratio, 5)),
+                                  "p95": float(np.percentile(ratio, 95)), "max": float(ratio.max())},
+        "within_2x": int(within2.sum()),
+        "oracle_dE_at_least_1e-9": {"clusters": int(big.sum()), "within_2x": int((within2 & big).sum()),
+                                    "ratio_max": float(ratio[big].max()) if big.any() else None},
+        "outside_2x": [{"cluster": int(q), "n": int(sizes[q]), "dE_E_gpu": float(de_gpu[q]),
+                        "dE_E_oracle": float(de_or[q])} for q in np.nonzero(~within2)[0]],
+        "worst": {"cluster": worst, "n": int(sizes[worst]), "dE_E_gpu": float(de_gpu[worst]),
+                  "dE_E_oracle": float(de_or[worst])}}
+    # the oracle's rate: all host cores over the comparison runs, and every 8th
+    # cluster on one core to t = 1/64
+    inter_all = sum(r[1] for r in cres)
+    t_cpu = 1.0 / 64
+    jobs = [(q, int(nq), 1000 + q, t_cpu) for q, nq in enumerate(sizes)]
     t0 = time.perf_counter()
     one = [_oracle_cluster_job(j) for j in jobs[::8]]
     wall_one = time.perf_counter() - t0
-    out["oracle"] = {"t_end": t_cpu, "all_cores": {"cores": cores, "clusters": len(jobs), "wall_s": wall_all,
-                                                   "interactions_per_s": inter_all / wall_all},
-                     "one_core": {"clusters": len(jobs[::8]), "wall_s": wall_one,
-                                  "interactions_per_s": sum(r[0] for r in one) / wall_one},
-                     "sample": "each cluster from t = 0 (its initial O(N_c^2) force included) to t = 1/64"}
+    out["oracle"] = {"all_cores": {"cores": cores, "clusters": len(cres), "t_end": t_cmp, "wall_s": wall_cmp,
+                                   "interactions_per_s": inter_all / wall_cmp,
+                                   "sample": "each cluster from t = 0 (its initial O(N_c^2) force included) to "
+                                             "t = 1/8, plus two FP64 energies per cluster"},
+                     "one_core": {"clusters": len(jobs[::8]), "t_end": t_cpu, "wall_s": wall_one,
+                                  "interactions_per_s": sum(r[0] for r in one) / wall_one}}
     print(json.dumps(out))
     return 0
 
@@ -1034,6 +1108,86 @@ def sweep_collapse(a):
     return 0
 
 
+CLUSTER_PHASES = ("predict and list own active particles", "count push, barrier B1, offsets",
+                  "gather the active records (DSMEM)", "force tasks", "segment sums and partial push",
+                  "barrier B2", "correction (owners)", "minimum push, barrier B3", "next block time")
+
+
+def sweep_cluster(a):
+    """The small-step cluster's phase counters over one N-body unit of the
+    benchmark workload (t = 0.375 -> 1.375, autotuned table), per small step, with
+    the SM clock sampled meanwhile; and the CUDA-event time per cluster launch."""
+    import torch
+
+    from paper_1702_00440_gb300 import gravidy, inputs
+
+    gravidy.load()
+    n = a.n
+    m, x, v = inputs.plummer(n, seed=1)
+    g = gravidy.Integrator(m, x, v, EPS, ETA, precision="mixed", autotune=True, time_force=True)
+    g.evolve(0.375)
+    g.kernel_time()
+    g.cluster_time()
+    c0, khz = g.cluster_phases()
+    s0 = g.stats()
+    sampler = ClockSampler(0)
+    sampler.start()
+    g.evolve(1.375)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    c1, _ = g.cluster_phases()
+    s1 = g.stats()
+    cms, cl = g.cluster_time()
+    fms, fl, fi = g.kernel_time()
+    info = g.cluster_info()
+    g.close()
+    d = c1 - c0
+    steps = d[11]
+    mhz = clocks["sm_mhz"] if clocks else khz / 1e3
+    us = lambda cyc: cyc / (mhz * 1e6) * 1e6
+    per = {name: us(d[k]) / max(steps, 1) for k, name in enumerate(CLUSTER_PHASES)}
+    out = {"sweep": "cluster", "n": n, "t": [0.375, 1.375], "cluster_info": info, "small_steps": int(steps),
+           "block_steps": s1["block_steps"] - s0["block_steps"], "sm_mhz": mhz, "clocks": clocks,
+           "per_small_step_us": per, "per_small_step_total_us": sum(per.values()),
+           "per_launch_us": {"prologue": us(d[9]) / max(cl, 1), "epilogue": us(d[10]) / max(cl, 1),
+                             "cuda_events": 1e3 * cms / max(cl, 1)},
+           "cluster_launches": cl, "force_launches": fl, "force_ms_per_launch": fms / max(fl, 1)}
+    print(json.dumps(out))
+    return 0
+
+
+def sweep_fp32peak(a):
+    """FP32 FMA throughput measured by the library's probe kernel (8 independent
+    FMA chains per thread, every SM at full occupancy), repeated for about two
+    seconds with the SM clock sampled meanwhile; the unit-count formula
+    152 SMs x 128 lanes x 2 flop x f_SM is printed beside it at the sampled clock
+    and at the maximum clock."""
+    import torch
+
+    from paper_1702_00440_gb300 import gravidy
+
+    gravidy.load()
+    torch.cuda.set_device(0)
+    gravidy.gd_probe_fma(0, 1 << 12)
+    sampler = ClockSampler(0)
+    sampler.start()
+    runs = []
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < 2.0:
+        runs.append(gravidy.gd_probe_fma(0, 1 << 18))
+    clocks = sampler.stop()
+    best = max(r[0] for r in runs)
+    med = statistics.median(r[0] for r in runs)
+    mhz = clocks["sm_mhz"] if clocks else None
+    out = {"sweep": "fp32peak", "probe_tflops_best": best, "probe_tflops_median": med, "probes": len(runs),
+           "ms_per_probe": statistics.median(r[1] for r in runs), "clocks": clocks,
+           "formula_tflops_at_max_clock": FP32_PEAK_TFLOPS,
+           "formula_tflops_at_sampled_clock": (SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12) if mhz else None,
+           "probe_over_formula_at_sampled_clock": (best / (SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12)) if mhz else None}
+    print(json.dumps(out))
+    return 0
+
+
 def sweep_h6(a):
     """Sixth- against fourth-order Hermite on Plummer N = 1024 and 4096 (seed 1,
     eps = 1e-4) to t = 1: wall time per N-body unit and |dE/E| for the FP64
@@ -1224,7 +1378,8 @@ def main():
         return {"force": sweep_force, "powerlaw": sweep_powerlaw, "accuracy": sweep_accuracy,
                 "ensemble": sweep_ensemble, "eta": sweep_eta, "soft": sweep_soft,
                 "lagrange": sweep_lagrange, "h6": sweep_h6,
-            "timesym": sweep_timesym, "collapse": sweep_collapse}[a.sweep](a)
+            "timesym": sweep_timesym, "collapse": sweep_collapse, "fp32peak": sweep_fp32peak,
+            "cluster": sweep_cluster}[a.sweep](a)
     if a.impl == "reference":
         return run_reference(a)
     return run_gravidy(a)

@@ -90,7 +90,15 @@ typedef struct gd_opts {
                            16-CTA clusters) and the GPU can launch the cluster, else ignored.
                            0 = every step on the full GPU.  The two differ in the order of
                            the force sums (last bits); each is deterministic. */
+    int32_t corrector;  /* GD_CORR_HERMITE (default): the 4th-order Hermite corrector of Sec. 2.4
+                           step 7d; GD_CORR_TIMESYM: its time-symmetric form (Hut, Makino &
+                           McMillan 1995), with h = dt/2, v1 = v0 + h (a1 + a0) - h^2/3 (j1 - j0),
+                           x1 = x0 + h (v1 + v0) - h^2/3 (a1 - a0); the same force, Aarseth step
+                           and block quantisation, in every path (three kernels, small-step
+                           cluster, fused kernel, ensembles) and both precisions */
 } gd_opts;
+
+enum { GD_CORR_HERMITE = 0, GD_CORR_TIMESYM = 1 };
 
 typedef struct gd_stats {
     int64_t tick;          /* time of the last block step, in ticks */
@@ -194,6 +202,18 @@ int gd_kernel_time(gd_ctx *c, double *ms_total, int64_t *launches, double *inter
  * run on the full GPU).  Any pointer may be NULL. */
 int gd_cluster_info(gd_ctx *c, int32_t *csize, int32_t *per_cta, int32_t *max_nact);
 
+/* Where the small-step cluster's time goes: SM cycles of CTA 0 (accumulated
+ * since gd_init) in the phases of every small block step it finished --
+ * [0] predict and list the CTA's active particles, [1] publish the count,
+ * cluster barrier, offsets, [2] gather the active records, [3] force tasks,
+ * [4] segment sums and partial push, [5] cluster barrier, [6] correction,
+ * [7] publish the next-time minimum, cluster barrier, [8] next block time --
+ * then [9] the launches' prologues (state into shared memory), [10] their
+ * epilogues (write-back, hand-over) and [11] the number of small steps.  The
+ * first count (<= 12) values go to cycles; *clock_khz (nullable) receives the
+ * device's maximum SM clock. */
+int gd_cluster_phases(gd_ctx *c, double *cycles, int32_t count, int32_t *clock_khz);
+
 /* Device time of the small-step cluster launches of gd_evolve's graph or eager
  * path recorded since the last call (needs opts.time_force = 1): *ms_total
  * summed milliseconds, *launches their count (a launch takes zero or more block
@@ -258,6 +278,14 @@ int gd_replay_step(gd_ctx *c, int64_t tick_next, const int32_t *idx, int64_t nac
  * further work, as after any device fault, while the CUDA context and the GPU
  * stay usable.  GD_EINVAL for a null context or a limit out of range. */
 int gd_test_wait_timeout(gd_ctx *c, int32_t limit);
+
+/* FP32 FMA throughput of the GPU (the roofline denominator of the FP32-bound
+ * force kernels): a kernel whose threads run 8 independent FMA chains of
+ * `iters` rounds each on every SM at full occupancy, timed with CUDA events
+ * (best of three launches after a warm one).  *tflops (nullable) receives
+ * 2 flop per FMA per lane over that time, *ms (nullable) the time.  iters in
+ * [1, 2^24]; the calling thread's current device becomes `device`. */
+int gd_probe_fma(int32_t device, int32_t iters, double *tflops, double *ms);
 
 /* Allocation-failure injection for tests: the nth allocation of `kind` (0 = host,
  * pageable or pinned; 1 = device) that the calling thread's next context set-ups

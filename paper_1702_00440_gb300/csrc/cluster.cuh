@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
     const Dev &d = a.d;
     const int n = d.n, P = a.P;
     const ClLayout L(P);
+    const long long K0 = clock64();
     extern __shared__ __align__(16) unsigned char smem[];
     float *xh = (float *)(smem + L.xh), *xl = (float *)(smem + L.xl);
     float *vh = (float *)(smem + L.vh), *vl = (float *)(smem + L.vl);
@@ -153,16 +154,23 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
     long long T_last = 0, psteps = 0;
     int last_n = 0, steps = 0;
     unsigned long long ph[3] = {0ull, 0ull, 0ull};  // CTA 0's clock: predict, force, correct
+    // CTA 0's SM cycles of every finished small step's phases: predict and list, count
+    // push + B1 + offsets, gather, force tasks, segment tree + partial push, B2,
+    // correction, post + B3, next time; then the launch's prologue and epilogue and
+    // the number of finished small steps (only CTA 0's thread 0 publishes them)
+    unsigned long long cyc[12] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
     bool handed = false;  // the next step was handed over selected
     const float eps2 = d.eps2f;
     __syncthreads();
 
+    const long long L0 = clock64();
     for (;;) {
         // the exit tests read values every CTA holds identically
         if (T > tick_end || (!a.handoff && steps >= a.max_steps)) break;
 
         // ---- 1. predict own particles, list own active ones (ascending local index)
         const unsigned long long t0 = global_ns();
+        const long long P0 = clock64();
         long long mn = LLONG_MAX;
         unsigned bal[CL_ROUNDS];
         float4 rA[CL_ROUNDS], rB[CL_ROUNDS];
@@ -233,6 +241,7 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
                 }
             }
         }
+        const long long P2 = clock64();
         if (t < C) cl.map_shared_rank(s_cnt_in, t)[r] = s_base;  // this CTA's count, into every inbox
         cl.sync();  // B1: j-records, active lists and counts of every CTA are visible
 
@@ -257,6 +266,7 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
         __syncthreads();
         const int nact = s_off[C];
         const unsigned long long t1 = global_ns();
+        const long long P4 = clock64();
         ph[0] += t1 - t0;
         if (nact > a.ns || (a.handoff && steps >= a.max_steps)) {
             // a large step (or the last of this launch): the full-GPU kernels take it
@@ -289,6 +299,7 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
             iC[k] = cl.map_shared_rank(oC, q)[kl];
         }
         __syncthreads();
+        const long long P5 = clock64();
         // forces over this CTA's j-range: tasks (pair of active particles, j-segment),
         // so every j-record loaded from shared memory serves two pair terms; with
         // fewer than CL_W pairs each pair's j-range is cut into Sw = 2^lgS segments
@@ -345,6 +356,7 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
                 }
             }
         }
+        const long long P6 = clock64();
         if (Sw > 1) {
             // this CTA's partial of active k: a pairwise tree over its Sw segment sums
             for (int lh = lgS - 1; lh >= 0; lh--) {
@@ -363,8 +375,10 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
                 dst[(aloc[k] * CL_MAXC + r) * 6 + c] = tp[((k << lgS) * 6) + c];
             }
         }
+        const long long P7 = clock64();
         cl.sync();  // B2: every partial has reached its owner
         const unsigned long long t2 = global_ns();
+        const long long P8 = clock64();
         ph[1] += t2 - t1;
 
         // ---- 3. owners: sum the C partials (rank order), correct, new steps
@@ -427,6 +441,7 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
             s_wbad[warp] = bad;
         }
         __syncthreads();
+        const long long P9 = clock64();
         if (warp == 0) {
             long long m = lane < CL_W ? s_wmin[lane] : LLONG_MAX;
             int b = lane < CL_W ? s_wbad[lane] : 0;
@@ -438,6 +453,7 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
             }
         }
         cl.sync();  // B3: corrected state and the posts of every CTA are visible
+        const long long P10 = clock64();
 
         // ---- 4. next block time: minimum over the C posts
         if (warp == 0) {  // lane q holds CTA q's post
@@ -463,11 +479,19 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
         T = s_T;
         const bool stop = s_bad != 0;
         __syncthreads();  // s_T, s_bad are rewritten next step
+        {
+            const long long P11 = clock64();
+            const long long pt[12] = {P0, P2, P4, P5, P6, P7, P8, P9, P10, P11, 0, 0};
+#pragma unroll
+            for (int k = 0; k < 9; k++) cyc[k] += (unsigned long long)(pt[k + 1] - pt[k]);
+            cyc[11] += 1;
+        }
         if (stop) {
             if (t == 0 && r == 0) set_err(ctrl, ST_ENONFINITE);
             break;
         }
     }
+    const long long L1 = clock64();
     // the particles this launch corrected (their time moved on), written back to
     // global memory once
     for (int p = t; p < Pr; p += CL_T) {
@@ -488,6 +512,10 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
     }
     cl.sync();  // no CTA leaves while another may still read its shared memory
     if (r == 0 && t == 0) {
+        cyc[9] += (unsigned long long)(L0 - K0);
+        cyc[10] += (unsigned long long)(clock64() - L1);
+#pragma unroll
+        for (int k = 0; k < 12; k++) ctrl->cl_cyc[k] += cyc[k];
         ctrl->T_cur = T;
         if (a.handoff && !handed) {  // tick_end passed, or a fault: nothing to hand over
             ctrl->nact = 0;

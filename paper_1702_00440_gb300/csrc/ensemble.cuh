@@ -49,20 +49,17 @@ struct EArgs {
     int correct;        // 1: correct in the tile tails and finalize the step; 0: forces only
 };
 
-// Selection + prediction with per-cluster compaction (see k_select_predict).
-__global__ void __launch_bounds__(ST) k_ens_select(Dev d, Ens e, int nchunks)
+// Selection + prediction with per-cluster compaction (see k_select_predict) at
+// block time T with look-back tag ep.  COH: the state was written earlier in the
+// same launch (the fused kernel), so it is read through L2.
+template <bool COH>
+__device__ void ens_select_phase(const Dev &d, const Ens &e, int nchunks, long long T, unsigned ep)
 {
     Ctrl *ctrl = d.ctrl;
-    const long long T = ctrl->T_cur;
-    if (T > ctrl->tick_end) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->nact = 0;
-        return;
-    }
     __shared__ unsigned s_excl;
     __shared__ unsigned s_wcnt[ST / 32];
     __shared__ long long s_wmin[ST / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned ep = ctrl->epoch & 0x3FFFFFFFu;
     long long mn_all = LLONG_MAX;
     for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
         const int i = chunk * ST + threadIdx.x;
@@ -72,7 +69,7 @@ __global__ void __launch_bounds__(ST) k_ens_select(Dev d, Ens e, int nchunks)
         const long long tn = ldc(&d.tnext[i]);
         const bool act = (tn == T);
         if (!act) mn_all = tn < mn_all ? tn : mn_all;
-        predict_store_ds<false>(d, i, T - ldc(&d.tau[i]));
+        predict_store_ds<COH>(d, i, T - ldc(&d.tau[i]));
         const unsigned ballot = __ballot_sync(0xffffffffu, act);
         if (lane == 0) s_wcnt[warp] = __popc(ballot);
         __syncthreads();
@@ -146,6 +143,18 @@ __global__ void __launch_bounds__(ST) k_ens_select(Dev d, Ens e, int nchunks)
         for (int w = 1; w < ST / 32; w++) mn = s_wmin[w] < mn ? s_wmin[w] : mn;
         if (mn != LLONG_MAX) atomicMin((unsigned long long *)&ctrl->T_acc, (unsigned long long)mn);
     }
+    __syncthreads();  // shared memory is reused by the next phase or step
+}
+
+__global__ void __launch_bounds__(ST) k_ens_select(Dev d, Ens e, int nchunks)
+{
+    Ctrl *ctrl = d.ctrl;
+    const long long T = ctrl->T_cur;
+    if (T > ctrl->tick_end) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->nact = 0;
+        return;
+    }
+    ens_select_phase<false>(d, e, nchunks, T, ctrl->epoch & 0x3FFFFFFFu);
 }
 
 // The work plan, the same in every CTA: per cluster, tiles of ENS_TILE active
@@ -293,15 +302,16 @@ __device__ void ens_tile_reduce(const Dev &d, const Ens &e, int item0, int S, in
     __syncthreads();
 }
 
-template <bool SOFT>
-__global__ void __launch_bounds__(FT, 2) k_ens_force(EArgs a)
+// Force (and, with a.correct, correction and the step's end) of the active
+// particles of every cluster at block time T: the work plan, the (tile, j-chunk)
+// items, the tile sums by the last of a tile's items, and the last CTA turning the
+// running minimum into the next block time.  COH as for ens_select_phase.
+template <bool SOFT, bool COH>
+__device__ void ens_force_phase(const EArgs &a, long long T, EnsPlanSmem &p)
 {
     const Dev &d = a.d;
     const Ens &e = a.e;
     Ctrl *ctrl = d.ctrl;
-    const long long T = ctrl->T_cur;
-    if (a.correct && T > ctrl->tick_end) return;
-    __shared__ EnsPlanSmem p;
     __shared__ float4 sA[2 * BJ], sB[2 * BJ];
     __shared__ float2 sC[2 * BJ];
     __shared__ int s_last;
@@ -404,7 +414,7 @@ __global__ void __launch_bounds__(FT, 2) k_ens_force(EArgs a)
         if (s_last) {
             __threadfence();
             ens_tile_reduce(d, e, p.item_base[c] + tl * S, S, slot0, nvalid);
-            if (a.correct) correct_slots<true, false>(d, T, slot0, slot0 + nvalid, warp, FT / 32, mymin, bad);
+            if (a.correct) correct_slots<true, COH>(d, T, slot0, slot0 + nvalid, warp, FT / 32, mymin, bad);
         }
         __syncthreads();
     }
@@ -431,6 +441,41 @@ __global__ void __launch_bounds__(FT, 2) k_ens_force(EArgs a)
             ctrl->epoch += 1;
             ctrl->done = 0;
         }
+    }
+    __syncthreads();  // the plan in shared memory is rebuilt by the next step
+}
+
+template <bool SOFT>
+__global__ void __launch_bounds__(FT, 2) k_ens_force(EArgs a)
+{
+    Ctrl *ctrl = a.d.ctrl;
+    const long long T = ctrl->T_cur;
+    if (a.correct && T > ctrl->tick_end) return;
+    __shared__ EnsPlanSmem p;
+    ens_force_phase<SOFT, false>(a, T, p);
+}
+
+// Up to max_steps global block steps in one cooperative launch (every CTA
+// resident): select + predict, grid barrier, force + correction + the step's end,
+// grid barrier.  The block time and the look-back tag of the next step are read
+// through L2 after the barrier; every CTA sees the same values, so all leave the
+// loop together once the block time passes tick_end.  Computes what the
+// two-kernel step computes, bit for bit.
+template <bool SOFT>
+__global__ void __launch_bounds__(FT, 2) k_ens_steps(EArgs a, int nchunks, int max_steps)
+{
+    const Dev &d = a.d;
+    Ctrl *ctrl = d.ctrl;
+    __shared__ EnsPlanSmem p;
+    const long long tick_end = ldc(&ctrl->tick_end);
+    for (int s = 0; s < max_steps; s++) {
+        const long long T = ldc(&ctrl->T_cur);
+        if (T > tick_end) break;
+        const unsigned ep = ldc(&ctrl->epoch) & 0x3FFFFFFFu;
+        ens_select_phase<true>(d, a.e, nchunks, T, ep);
+        grid_sync(d.bar, ctrl);
+        ens_force_phase<SOFT, true>(a, T, p);
+        grid_sync(d.bar, ctrl);
     }
 }
 

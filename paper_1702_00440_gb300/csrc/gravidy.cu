@@ -695,6 +695,7 @@ void gd_opts_default(gd_opts *o)
     o->pdl = 0;
     o->tail_correct = 0;
     o->cluster = 1;
+    o->corrector = GD_CORR_HERMITE;
 }
 
 }  // extern "C"
@@ -719,6 +720,8 @@ int ctx_init(gd_ctx **out, int64_t n, const double *m, const double *x, const do
         return fail(nullptr, GD_EINVAL, "dt_min and dt_max must be powers of two with dt_min <= dt_max");
     if (o.dt_max / o.dt_min > std::ldexp(1.0, 40)) return fail(nullptr, GD_EINVAL, "dt_max/dt_min too large");
     if (o.precision != GD_FP64 && o.precision != GD_MIXED) return fail(nullptr, GD_EINVAL, "bad precision");
+    if (o.corrector != GD_CORR_HERMITE && o.corrector != GD_CORR_TIMESYM)
+        return fail(nullptr, GD_EINVAL, "corrector must be GD_CORR_HERMITE or GD_CORR_TIMESYM");
     // the mixed path counts steps in FP32: tick counts up to dtau_max and dt_min^5 stay exact
     if (o.precision == GD_MIXED && (o.dt_min < std::ldexp(1.0, -24) || o.dt_max / o.dt_min > std::ldexp(1.0, 24)))
         return fail(nullptr, GD_EINVAL, "mixed precision needs dt_min >= 2^-24 and dt_max/dt_min <= 2^24");
@@ -796,6 +799,7 @@ int ctx_init(gd_ctx **out, int64_t n, const double *m, const double *x, const do
     d.dt_min_f = (float)o.dt_min;
     d.inv_dt_min_f = (float)(1.0 / o.dt_min);
     d.eta_f = (float)eta;
+    d.tsym = o.corrector == GD_CORR_TIMESYM ? 1 : 0;
     c->nchunks = (d.n + ST - 1) / ST;
     // the select kernel's CTAs wait for the counts of lower CTAs: keep its grid co-resident
     c->grid_sel = std::max(1, std::min(c->nchunks, sms * std::max(1, occ_sel)));
@@ -1127,6 +1131,21 @@ int gd_cluster_time(gd_ctx *c, double *ms_total, int64_t *launches)
     return GD_OK;
 }
 
+int gd_cluster_phases(gd_ctx *c, double *cycles, int32_t count, int32_t *clock_khz)
+{
+    int rc = check_usable(c);
+    if (rc) return rc;
+    if (count < 0 || count > 12) return fail(c, GD_EINVAL, "count must be in [0, 12]");
+    if ((rc = sync_ctrl(c))) return rc;
+    for (int k = 0; k < count; k++) cycles[k] = (double)c->h_ctrl->cl_cyc[k];
+    if (clock_khz) {
+        int khz = 0;
+        cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, c->dev);
+        *clock_khz = khz;
+    }
+    return GD_OK;
+}
+
 int gd_cluster_info(gd_ctx *c, int32_t *csize, int32_t *per_cta, int32_t *max_nact)
 {
     if (!c) return fail(nullptr, GD_EINVAL, "null context");
@@ -1149,6 +1168,76 @@ const char *gd_last_error(const gd_ctx *c)
 {
     if (!c) return g_init_err.c_str();
     return c->err.c_str();
+}
+
+}  // extern "C"
+
+namespace {
+
+// FP32 FMA throughput probe: every thread runs FMA_CHAINS independent chains of
+// x = x * a + b for `iters` rounds, so each SM sub-partition always has independent
+// FMAs to issue; the result is kept live by a store that never happens for these
+// inputs (|x| stays below 2 for a = 1 - 2^-20, b = 2^-21 from x0 in [0, 1)).
+constexpr int FMA_CHAINS = 8;
+constexpr int FMA_T = 256;
+
+__global__ void __launch_bounds__(FMA_T) k_fma_probe(float *sink, int iters, float a, float b)
+{
+    float x[FMA_CHAINS];
+#pragma unroll
+    for (int k = 0; k < FMA_CHAINS; k++) x[k] = (float)((threadIdx.x + k) & 63) * (1.0f / 64.0f);
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int k = 0; k < FMA_CHAINS; k++) x[k] = fmaf(x[k], a, b);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < FMA_CHAINS; k++) s += x[k];
+    if (s > 1.0e30f) sink[blockIdx.x] = s;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gd_probe_fma(int32_t device, int32_t iters, double *tflops, double *ms)
+{
+    if (iters < 1 || iters > (1 << 24)) return fail(nullptr, GD_EINVAL, "iters must be in [1, 2^24]");
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaSetDevice");
+    int sms = 0, occ = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fma_probe, FMA_T, 0);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "device query");
+    const int grid = sms * std::max(1, occ);
+    float *sink = nullptr;
+    if (gd_alloc_fails(1) || cudaMalloc((void **)&sink, sizeof(float) * grid) != cudaSuccess)
+        return fail(nullptr, GD_ENOMEM, "cudaMalloc failed");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const float a = 1.0f - 9.5367431640625e-07f, b = 4.76837158203125e-07f;  // 1 - 2^-20, 2^-21
+    float best = 0.f;
+    if (e == cudaSuccess) {
+        k_fma_probe<<<grid, FMA_T>>>(sink, iters, a, b);  // warm
+        for (int r = 0; r < 3 && e == cudaSuccess; r++) {
+            cudaEventRecord(e0);
+            k_fma_probe<<<grid, FMA_T>>>(sink, iters, a, b);
+            cudaEventRecord(e1);
+            e = cudaEventSynchronize(e1);
+            float t = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+            if (e == cudaSuccess && (best == 0.f || t < best)) best = t;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "gd_probe_fma");
+    const double flop = 2.0 * FMA_CHAINS * (double)iters * (double)grid * FMA_T;
+    if (ms) *ms = best;
+    if (tflops) *tflops = flop / (best * 1e-3) / 1e12;
+    return GD_OK;
 }
 
 int gd_test_fail_alloc(int32_t kind, int32_t nth)
@@ -1326,6 +1415,8 @@ struct gd_ens {
     double *d_K, *d_U;
     cudaGraphExec_t graph;
     int grid_ens;
+    int grid_steps;      // fused: co-resident grid of k_ens_steps (0 = not available)
+    bool fused;          // gd_ens_evolve runs k_ens_steps, graph_steps global steps per cooperative launch
     std::string err;
 };
 
@@ -1346,6 +1437,50 @@ void ens_free_dev(gd_ens *s)
     for (void *p : ps)
         if (p) cudaFree(p);
     if (s->graph) cudaGraphExecDestroy(s->graph);
+}
+
+// One cooperative launch of up to max_steps fused global block steps.
+int ens_launch_fused(gd_ens *s, int max_steps)
+{
+    gd_ctx *c = s->c;
+    EArgs a{c->d, s->e, 1};
+    int nch = c->nchunks;
+    void *args[] = {&a, &nch, &max_steps};
+    const void *fn = c->soft ? (const void *)k_ens_steps<true> : (const void *)k_ens_steps<false>;
+    c->launches += 1;
+    const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(s->grid_steps), dim3(FT), args, 0, c->stream);
+    if (e != cudaSuccess) return ens_fail(s, GD_ECUDA, std::string("cooperative launch: ") + cudaGetErrorString(e));
+    return GD_OK;
+}
+
+// gd_ens_evolve through k_ens_steps: launches of graph_steps global steps each,
+// one kept in flight while the host reads the previous one's control-block
+// snapshot (as gd_evolve does).
+int ens_evolve_fused(gd_ens *s, long long tick_end)
+{
+    gd_ctx *c = s->c;
+    const int G = c->graph_steps;
+    int rc;
+    k_set_tick_end<<<1, 1, 0, c->stream>>>(c->d.ctrl, tick_end);
+    c->launches += 1;
+    if ((rc = ens_launch_fused(s, G))) return rc;
+    if (cudaMemcpyAsync(&c->h_snap[0], c->d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaEventRecord(c->ev_snap[0], c->stream) != cudaSuccess)
+        return ens_fail(s, GD_ECUDA, "snapshot");
+    for (long long k = 0;; k++) {
+        const int cur = (int)(k & 1), nxt = 1 - cur;
+        if ((rc = ens_launch_fused(s, G))) return rc;
+        if (cudaMemcpyAsync(&c->h_snap[nxt], c->d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream) !=
+                cudaSuccess ||
+            cudaEventRecord(c->ev_snap[nxt], c->stream) != cudaSuccess ||
+            cudaEventSynchronize(c->ev_snap[cur]) != cudaSuccess)
+            return ens_fail(s, GD_ECUDA, "snapshot");
+        if (c->h_snap[cur].err != 0 || c->h_snap[cur].T_cur > tick_end) break;
+    }
+    k_set_tick_end<<<1, 1, 0, c->stream>>>(c->d.ctrl, LLONG_MAX);
+    c->launches += 1;
+    if ((rc = sync_ctrl(c))) return ens_fail(s, rc, c->err);
+    return GD_OK;
 }
 
 void ens_launch_step(gd_ens *s)
@@ -1439,6 +1574,15 @@ int gd_ens_init(gd_ens **out, int32_t nclusters, const int64_t *n_per, const dou
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, o.device);
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->soft ? k_ens_force<true> : k_ens_force<false>, FT, 0);
     s->grid_ens = sms * std::max(1, occ);
+    if (o.fused) {
+        int coop = 0, occ_steps = 0;
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, o.device);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_steps, c->soft ? k_ens_steps<true> : k_ens_steps<false>,
+                                                          FT, 0) != cudaSuccess)
+            cudaGetLastError();
+        s->grid_steps = (coop && occ_steps > 0) ? sms * occ_steps : 0;
+        s->fused = s->grid_steps > 0;
+    }
     const int target = 2 * s->grid_ens;
     const long long part_items = (long long)target + ntiles + 16;
     al((void **)&s->d_cs, sizeof(int) * nclusters);
@@ -1509,6 +1653,7 @@ int gd_ens_evolve(gd_ens *s, double t_end)
     const long long tick_end = (long long)std::floor(t_end / c->d.dt_min);
     if (tick_end < c->h_ctrl->T_last) return ens_fail(s, GD_EINVAL, "t_end is before the current time");
     const int G = c->graph_steps;
+    if (s->fused) return ens_evolve_fused(s, tick_end);
     if (c->opt.use_graph && !s->graph) {
         cudaGraph_t g;
         cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
@@ -1523,7 +1668,7 @@ int gd_ens_evolve(gd_ens *s, double t_end)
         if (e != cudaSuccess) return ens_fail(s, GD_ECUDA, std::string("graph: ") + cudaGetErrorString(e));
     }
     k_set_tick_end<<<1, 1, 0, c->stream>>>(c->d.ctrl, tick_end);
-    for (;;) {
+    auto chunk = [&]() -> int {
         if (s->graph) {
             if (cudaGraphLaunch(s->graph, c->stream) != cudaSuccess) return ens_fail(s, GD_ECUDA, "graph launch");
             c->launches += 2LL * G;
@@ -1531,8 +1676,22 @@ int gd_ens_evolve(gd_ens *s, double t_end)
             for (int q = 0; q < G; q++) ens_launch_step(s);
         }
         if (cudaGetLastError() != cudaSuccess) return ens_fail(s, GD_ECUDA, "launch");
-        if ((rc = sync_ctrl(c))) return ens_fail(s, rc, c->err);
-        if (c->h_ctrl->T_cur > tick_end) break;
+        return GD_OK;
+    };
+    // keep one chunk in flight while the host looks at the previous one's snapshot
+    if ((rc = chunk())) return rc;
+    if (cudaMemcpyAsync(&c->h_snap[0], c->d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaEventRecord(c->ev_snap[0], c->stream) != cudaSuccess)
+        return ens_fail(s, GD_ECUDA, "snapshot");
+    for (long long k = 0;; k++) {
+        const int cur = (int)(k & 1), nxt = 1 - cur;
+        if ((rc = chunk())) return rc;
+        if (cudaMemcpyAsync(&c->h_snap[nxt], c->d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream) !=
+                cudaSuccess ||
+            cudaEventRecord(c->ev_snap[nxt], c->stream) != cudaSuccess ||
+            cudaEventSynchronize(c->ev_snap[cur]) != cudaSuccess)
+            return ens_fail(s, GD_ECUDA, "snapshot");
+        if (c->h_snap[cur].err != 0 || c->h_snap[cur].T_cur > tick_end) break;
     }
     k_set_tick_end<<<1, 1, 0, c->stream>>>(c->d.ctrl, LLONG_MAX);
     if ((rc = sync_ctrl(c))) return ens_fail(s, rc, c->err);

@@ -73,6 +73,7 @@ struct Ctrl {
     unsigned sel_gen;      // launches of the ordered select kernel so far (mod 2^31), see k_select_predict
     unsigned long long ph_ns[3];  // fused kernel, CTA 0's clock: select, force, correct phases
     unsigned long long sel_acc;   // select: arrived chunks (high word), active count (low word); 0 between steps
+    unsigned long long cl_cyc[12];  // small-step cluster, CTA 0's SM cycles per phase (see k_cluster_steps)
 };
 
 __device__ __forceinline__ void set_err(Ctrl *c, int code) { atomicCAS(&c->err, 0, code); }
@@ -105,6 +106,7 @@ struct Dev {
     double eps2;
     float eps2f;
     float dt_min_f, inv_dt_min_f, eta_f;  // FP32 copies (dt_min is a power of two: exact)
+    int tsym;                 // corrector: 0 the Hermite scheme's, 1 the time-symmetric form
     // FP64 state at each particle's own time, structure of arrays (plane c at +c*n);
     // on the mixed path these planes only stage the state in and out (k_state_to_ds,
     // k_state_from_ds)
@@ -1038,6 +1040,35 @@ __device__ __forceinline__ long long next_block_step_f(const Dev &d, float na1, 
     return dtau_old;
 }
 
+// (a.h + a.l) + (b.h + b.l), normalised
+__device__ __forceinline__ F2 ds_add(F2 a, F2 b)
+{
+    const F2 s = two_sum(a.h, b.h);
+    return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+
+// The time-symmetric fourth-order corrector (Hut, Makino & McMillan 1995) of one
+// component on the mixed path, with h = dt / 2:
+//   v1 = v0 + h (a1 + a0) - (h^2 / 3) (j1 - j0),
+//   x1 = x0 + h (v1 + v0) - (h^2 / 3) (a1 - a0).
+// The velocity update is an FP32 term added to the double-single v0; the position
+// update adds the exact product h * (v1 + v0).hi (product and FMA residual) and
+// FP32 terms to the double-single x0.  Results canonical.
+__device__ __forceinline__ void ds_correct_tsym(float dt, F2 x0, F2 v0, float a0, float j0, float a1, float j1,
+                                                F2 &x1, F2 &v1)
+{
+    const float h = __fmul_rn(0.5f, dt);
+    const float h2_3 = __fmul_rn(__fmul_rn(h, h), 1.0f / 3.0f);
+    const float dv = fmaf(h, __fadd_rn(a1, a0), -__fmul_rn(h2_3, __fadd_rn(j1, -j0)));
+    v1 = ds_canon(ds_add_f(v0, dv));
+    const F2 sv = ds_add(v0, v1);
+    const float p = __fmul_rn(h, sv.h);
+    const float pe = fmaf(h, sv.h, -p);
+    const float small = __fadd_rn(fmaf(h, sv.l, pe), -__fmul_rn(h2_3, __fadd_rn(a1, -a0)));
+    const F2 t = two_sum(x0.h, p);
+    x1 = ds_canon(two_sum(t.h, __fadd_rn(__fadd_rn(t.l, x0.l), small)));
+}
+
 // Correction (Sec. 2.4 step 7d, Hermite scheme) on the mixed path, laid out as
 // correct_slots64 (four lanes per particle): FP32 Hermite derivatives and
 // correction terms (the forces they come from are FP32-accurate), double-single
@@ -1064,8 +1095,12 @@ __device__ __forceinline__ void ds_correct(const Dev &d, bool real, long long dt
     const float da = __fadd_rn(a0, -a1);
     const float a2 = __fmul_rn(fmaf(-6.0f, da, -__fmul_rn(dt, fmaf(4.0f, j0, __fmul_rn(2.0f, j1)))), idt2);
     const float a3 = __fmul_rn(fmaf(12.0f, da, __fmul_rn(__fmul_rn(6.0f, dt), __fadd_rn(j0, j1))), idt3);
-    x1 = ds_canon(ds_add_f(xp, fmaf(a3, h5, __fmul_rn(a2, h4))));
-    v1 = ds_canon(ds_add_f(vp, fmaf(a3, h4, __fmul_rn(a2, h3))));
+    if (d.tsym) {
+        ds_correct_tsym(dt, x0, v0, a0, j0, a1, j1, x1, v1);
+    } else {
+        x1 = ds_canon(ds_add_f(xp, fmaf(a3, h5, __fmul_rn(a2, h4))));
+        v1 = ds_canon(ds_add_f(vp, fmaf(a3, h4, __fmul_rn(a2, h3))));
+    }
     const float a2e = fmaf(dt, a3, a2);  // 2nd derivative at the end of the step
     const float na1 = norm3_group(real ? a1 : 0.f), nj1 = norm3_group(real ? j1 : 0.f);
     const float na2 = norm3_group(real ? a2e : 0.f), na3 = norm3_group(real ? a3 : 0.f);
@@ -1171,8 +1206,15 @@ __device__ __forceinline__ void correct_slots64(const Dev &d, long long T, int k
         const double da = a0 - a1;
         const double a2 = (-6.0 * da - dt * (4.0 * j0 + 2.0 * j1)) * idt2;
         const double a3 = (12.0 * da + 6.0 * dt * (j0 + j1)) * idt3;
-        const double x1 = xp + a2 * h4 + a3 * h5;
-        const double v1 = vp + a2 * h3 + a3 * h4;
+        double x1, v1;
+        if (d.tsym) {  // time-symmetric form, h = dt / 2 (see ds_correct_tsym)
+            const double h = 0.5 * dt, hh3 = h * h / 3.0;
+            v1 = v0 + h * (a1 + a0) - hh3 * (j1 - j0);
+            x1 = x0 + h * (v1 + v0) - hh3 * (a1 - a0);
+        } else {
+            x1 = xp + a2 * h4 + a3 * h5;
+            v1 = vp + a2 * h3 + a3 * h4;
+        }
         const double a2e = fma(dt, a3, a2);  // 2nd derivative at the end of the step
         // squared norms, summed over the group's lanes
         double sA = real ? a1 * a1 : 0.0, sJ = real ? j1 * j1 : 0.0;

@@ -20,14 +20,15 @@ from . import build as _build
 
 GD_OK, GD_EINVAL, GD_ENOMEM, GD_ECUDA, GD_ENONFINITE, GD_ETIMEOUT, GD_ESTATE = 0, -1, -2, -3, -4, -5, -6
 GD_FP64, GD_MIXED = 0, 1
+GD_CORR_HERMITE, GD_CORR_TIMESYM = 0, 1
 _PRECISION = {"fp64": GD_FP64, "mixed": GD_MIXED, GD_FP64: GD_FP64, GD_MIXED: GD_MIXED}
 
 # every entry point the header declares
 EXPORTS = (
     "gd_opts_default", "gd_init", "gd_evolve", "gd_step_block", "gd_energy", "gd_get_state",
     "gd_set_state", "gd_get_stats", "gd_kernel_time", "gd_free", "gd_last_error", "gd_force",
-    "gd_predict", "gd_predict_records", "gd_step_block_small", "gd_active", "gd_replay_step", "gd_test_wait_timeout", "gd_test_fail_alloc", "gd_force_noalloc", "gd_autotune", "gd_get_tuning", "gd_set_tuning",
-    "gd_cluster_info", "gd_cluster_time",
+    "gd_predict", "gd_predict_records", "gd_step_block_small", "gd_active", "gd_replay_step", "gd_test_wait_timeout", "gd_test_fail_alloc", "gd_probe_fma", "gd_force_noalloc", "gd_autotune", "gd_get_tuning", "gd_set_tuning",
+    "gd_cluster_info", "gd_cluster_time", "gd_cluster_phases",
     "gd_ens_init", "gd_ens_evolve", "gd_ens_step_block", "gd_ens_energy", "gd_ens_get_state",
     "gd_ens_get_stats", "gd_ens_free", "gd_ens_last_error",
     "gd_h6_init", "gd_h6_init_scheme", "gd_h6_evolve", "gd_h6_step_block", "gd_h6_replay_step", "gd_h6_force", "gd_h6_energy",
@@ -58,6 +59,7 @@ class gd_opts(ctypes.Structure):
         ("pdl", ctypes.c_int32),
         ("tail_correct", ctypes.c_int32),
         ("cluster", ctypes.c_int32),
+        ("corrector", ctypes.c_int32),
     ]
 
 
@@ -106,6 +108,7 @@ def load(build_if_missing: bool = True):
             "gd_kernel_time": (ctypes.c_int, [P, P, P, P]),
             "gd_cluster_info": (ctypes.c_int, [P, P, P, P]),
             "gd_cluster_time": (ctypes.c_int, [P, P, P]),
+            "gd_cluster_phases": (ctypes.c_int, [P, P, I32, P]),
             "gd_free": (None, [P]),
             "gd_last_error": (ctypes.c_char_p, [P]),
             "gd_force": (ctypes.c_int, [P, I64, P, I64, P, P]),
@@ -116,6 +119,7 @@ def load(build_if_missing: bool = True):
             "gd_replay_step": (ctypes.c_int, [P, I64, P, I64]),
             "gd_test_wait_timeout": (ctypes.c_int, [P, I32]),
             "gd_test_fail_alloc": (ctypes.c_int, [I32, I32]),
+            "gd_probe_fma": (ctypes.c_int, [I32, I32, P, P]),
             "gd_force_noalloc": (ctypes.c_int, [I64, P, P, P, D, P, I64, P, P, P]),
             "gd_autotune": (ctypes.c_int, [P, I32]),
             "gd_get_tuning": (ctypes.c_int, [P, P, P, P, P, I32]),
@@ -164,7 +168,7 @@ def _check(rc, ctx=None):
 
 def make_opts(dt_min=2.0 ** -22, dt_max=0.125, precision="mixed", device=0, stream=None, use_graph=True,
               graph_steps=16, jsplit=0, mode_cut=0, time_force=False, autotune=False, fused=False, pdl=None,
-              tail_correct=None, cluster=None):
+              tail_correct=None, cluster=None, corrector="hermite"):
     o = gd_opts()
     load().gd_opts_default(ctypes.byref(o))
     o.dt_min = float(dt_min)
@@ -185,6 +189,7 @@ def make_opts(dt_min=2.0 ** -22, dt_max=0.125, precision="mixed", device=0, stre
         o.tail_correct = 1 if tail_correct else 0
     if cluster is not None:
         o.cluster = 1 if cluster else 0
+    o.corrector = {"hermite": GD_CORR_HERMITE, "timesym": GD_CORR_TIMESYM}[corrector]
     return o
 
 
@@ -282,6 +287,14 @@ def gd_cluster_time(ctx):
     return ms.value, k.value
 
 
+def gd_cluster_phases(ctx):
+    """(cycles[12], max SM clock kHz) of the small-step cluster's phase counters."""
+    cyc = np.zeros(12)
+    khz = ctypes.c_int32()
+    _check(load().gd_cluster_phases(ctx, _p(cyc), 12, ctypes.byref(khz)), ctx)
+    return cyc, khz.value
+
+
 def gd_autotune(ctx, reps=3):
     _check(load().gd_autotune(ctx, int(reps)), ctx)
 
@@ -351,6 +364,14 @@ def gd_test_fail_alloc(kind, nth):
     _check(rc)
 
 
+def gd_probe_fma(device=0, iters=1 << 16):
+    """(TFLOP/s, ms) of the FP32 FMA throughput probe."""
+    tf = ctypes.c_double()
+    ms = ctypes.c_double()
+    _check(load().gd_probe_fma(int(device), int(iters), ctypes.byref(tf), ctypes.byref(ms)))
+    return tf.value, ms.value
+
+
 def gd_force_noalloc(n, m_ptr, x_ptr, v_ptr, eps, idx_ptr, nact, acc_ptr, jerk_ptr, stream=None):
     """Allocation-free force/jerk evaluation on caller-owned device buffers
     (raw device addresses as ints); queues the work on ``stream`` and returns."""
@@ -412,6 +433,9 @@ class Integrator:
 
     def cluster_info(self):
         return gd_cluster_info(self._h)
+
+    def cluster_phases(self):
+        return gd_cluster_phases(self._h)
 
     def cluster_time(self):
         return gd_cluster_time(self._h)

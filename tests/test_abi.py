@@ -172,3 +172,10 @@ def test_tiny_softening_is_checked_against_the_masses_on_the_host():
             assert rc != gravidy.GD_EINVAL
             if h.value:
                 lib.gd_free(h)
+
+
+def test_fma_probe_rejects_bad_iteration_counts_on_the_host():
+    lib = gravidy.load()
+    tf = ctypes.c_double()
+    assert lib.gd_probe_fma(0, 0, ctypes.byref(tf), None) == gravidy.GD_EINVAL
+    assert lib.gd_probe_fma(0, (1 << 24) + 1, ctypes.byref(tf), None) == gravidy.GD_EINVAL

@@ -94,10 +94,12 @@ def _near_boundary(dt_new, rel):
     return abs(q - round(q)) <= rel / math.log(2)
 
 
-def _check_corrections(st0, st1, idx, T, a1, j1):
+def _check_corrections(st0, st1, idx, T, a1, j1, tsym=False):
     """Each active particle's corrected x, v and new step (st1) against the
-    oracle's chain from st0 and the end-point force (a1, j1); returns the worst
-    error / bound ratios and the number of step decisions taken at a boundary."""
+    oracle's chain from st0 and the end-point force (a1, j1): the Hermite
+    corrector (prediction, Hermite derivatives, correction) or, with tsym, the
+    time-symmetric one; returns the worst error / bound ratios and the number of
+    step decisions taken at a boundary."""
     worst_x = worst_v = 0.0
     flips = 0
     for k, i in enumerate(idx):
@@ -105,14 +107,25 @@ def _check_corrections(st0, st1, idx, T, a1, j1):
         dt = (T - st0["tau"][i]) * DT_MIN
         xo, vo = oracle.predict_one(x0, v0, a0, j0, dt)
         a2, a3 = oracle.hermite_derivs(a0, j0, a1[k], j1[k], dt)
-        x1, v1 = oracle.correct_one(xo, vo, a2, a3, dt)
         da = np.abs(a0 - a1[k])
         S2 = 6 * da + dt * (4 * np.abs(j0) + 2 * np.abs(j1[k]))
         S3 = 12 * da + 6 * dt * (np.abs(j0) + np.abs(j1[k]))
-        bx, _ = _pred_bounds(x0, v0, a0, j0, vo, dt)
-        bx = bx + 8 * U24 * (S2 / 24 + S3 / 120) * dt * dt + 4 * U48 * np.abs(x1)
-        bv = 4 * U48 * np.abs(v0) + 4 * U24 * (np.abs(a0) * dt + np.abs(j0) * dt * dt / 2) \
-            + 8 * U24 * (S2 / 6 + S3 / 24) * dt + 2.0 ** -44 * np.abs(v1)
+        if tsym:
+            x1, v1 = oracle.correct4s_one(x0, v0, a0, j0, a1[k], j1[k], dt)
+            h = dt / 2
+            # the FP32 velocity term h (a1 + a0) - h^2/3 (j1 - j0) and the double-single
+            # sums; the position adds h (v1 + v0) (exact product of the hi part) and the
+            # FP32 term h^2/3 (a1 - a0), and inherits h times the velocity's error
+            bv = 4 * U48 * np.abs(v1) + 4 * U24 * (h * (np.abs(a1[k]) + np.abs(a0))
+                                                   + h * h * (np.abs(j1[k]) + np.abs(j0)) / 3)
+            bx = 4 * U48 * (np.abs(x1) + 2 * h * (np.abs(v0) + np.abs(v1))) \
+                + 4 * U24 * h * h * (np.abs(a1[k]) + np.abs(a0)) / 3 + h * bv
+        else:
+            x1, v1 = oracle.correct_one(xo, vo, a2, a3, dt)
+            bx, _ = _pred_bounds(x0, v0, a0, j0, vo, dt)
+            bx = bx + 8 * U24 * (S2 / 24 + S3 / 120) * dt * dt + 4 * U48 * np.abs(x1)
+            bv = 4 * U48 * np.abs(v0) + 4 * U24 * (np.abs(a0) * dt + np.abs(j0) * dt * dt / 2) \
+                + 8 * U24 * (S2 / 6 + S3 / 24) * dt + 2.0 ** -44 * np.abs(v1)
         ex, ev = np.abs(st1["x"][i] - x1), np.abs(st1["v"][i] - v1)
         assert (ex <= bx).all(), (T, i, ex, bx)
         assert (ev <= bv).all(), (T, i, ev, bv)
@@ -136,17 +149,20 @@ def _check_corrections(st0, st1, idx, T, a1, j1):
     return worst_x, worst_v, flips
 
 
-def test_mixed_corrector_and_step_match_oracle_elementwise():
+@pytest.mark.parametrize("corrector", ["hermite", "timesym"])
+def test_mixed_corrector_and_step_match_oracle_elementwise(corrector):
     """Sixty consecutive block steps of an integrated N = 2048 system: each
     active particle's corrected position and velocity against the oracle's
-    prediction, Hermite derivatives and correction from the same state and the
-    same end-point force (the GPU's own, read through the force hook), and its
-    new block step against the oracle's Aarseth step and quantisation."""
+    prediction, Hermite derivatives and correction (or its time-symmetric
+    corrector) from the same state and the same end-point force (the GPU's own,
+    read through the force hook), and its new block step against the oracle's
+    Aarseth step and quantisation."""
     n = 2048
     m, x, v = inputs.plummer(n, seed=33)
     checked = flips = 0
     worst_x = worst_v = 0.0
-    with gravidy.Integrator(m, x, v, EPS, ETA, precision="mixed") as g:
+    tsym = corrector == "timesym"
+    with gravidy.Integrator(m, x, v, EPS, ETA, precision="mixed", corrector=corrector) as g:
         g.evolve(0.125)
         for _ in range(60):
             st0 = g.state()
@@ -160,17 +176,18 @@ def test_mixed_corrector_and_step_match_oracle_elementwise():
             # the corrector keeps exactly the force the hook returns
             assert np.array_equal(st1["a"][idx], a1) and np.array_equal(st1["j"][idx], j1)
             assert (st1["tau"][idx] == T).all()
-            wx, wv, fl = _check_corrections(st0, st1, idx, T, a1, j1)
+            wx, wv, fl = _check_corrections(st0, st1, idx, T, a1, j1, tsym)
             worst_x, worst_v = max(worst_x, wx), max(worst_v, wv)
             flips += fl
             checked += idx.size
-    print("corrector: %d corrections, worst |dx|/bound %.3f |dv|/bound %.3f, %d step decisions at a boundary"
+    print(corrector + " corrector: %d corrections, worst |dx|/bound %.3f |dv|/bound %.3f, %d step decisions at a boundary"
           % (checked, worst_x, worst_v, flips))
     assert checked > 500
     assert flips <= 0.01 * checked
 
 
-def test_cluster_step_force_and_correction_match_oracle():
+@pytest.mark.parametrize("corrector", ["hermite", "timesym"])
+def test_cluster_step_force_and_correction_match_oracle(corrector):
     """Block steps taken inside the small-step cluster (the kernel gd_evolve uses
     for steps with few active particles), one at a time: the end-point force the
     cluster computed (kept as the particles' new a and jerk) against the oracle's
@@ -185,7 +202,7 @@ def test_cluster_step_force_and_correction_match_oracle():
     rel_a, rel_j = [], []
     worst = [0.0, 0.0]
     flips = taken = 0
-    with gravidy.Integrator(m, x, v, EPS, ETA, precision="mixed") as g:
+    with gravidy.Integrator(m, x, v, EPS, ETA, precision="mixed", corrector=corrector) as g:
         csize, per_cta, ns = g.cluster_info()
         assert csize in (8, 16)
         bound = (8 + math.ceil(per_cta / 32) + 13) * U24
@@ -212,12 +229,12 @@ def test_cluster_step_force_and_correction_match_oracle():
             others = np.setdiff1d(np.arange(n), idx)
             for key in ("x", "v", "a", "j", "tau", "dtau"):
                 assert np.array_equal(st1[key][others], st0[key][others]), key
-            wx, wv, fl = _check_corrections(st0, st1, idx, T, a1, j1)
+            wx, wv, fl = _check_corrections(st0, st1, idx, T, a1, j1, corrector == "timesym")
             worst = [max(worst[0], wx), max(worst[1], wv)]
             flips += fl
             taken += idx.size
     ra, rj = np.array(rel_a), np.array(rel_j)
-    print("cluster steps: %d corrections; rel |da|/|a| median %.2e p99 %.2e max %.2e, |dj|/|j| median %.2e p99 %.2e "
+    print(corrector + " cluster steps: %d corrections; rel |da|/|a| median %.2e p99 %.2e max %.2e, |dj|/|j| median %.2e p99 %.2e "
           "max %.2e; worst |dx|/bound %.3f |dv|/bound %.3f; %d decisions at a boundary"
           % (taken, np.median(ra), np.percentile(ra, 99), ra.max(), np.median(rj), np.percentile(rj, 99), rj.max(),
              worst[0], worst[1], flips))

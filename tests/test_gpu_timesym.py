@@ -163,3 +163,115 @@ def test_three_bodies_sixteen_passes_replay():
     assert (st["tau"] == so["tau"]).all()
     assert np.abs(st["x"] - so["x"]).max() < 1e-11
     assert np.abs(st["v"] - so["v"]).max() < 1e-11
+
+
+# ---- the time-symmetric corrector on the fourth-order integrator (gd_init, both
+# precisions, option corrector = "timesym") against the order-4 oracle with one pass
+
+def _sim4s(m, x, v):
+    return oracle.Sim6(m, x, v, EPS, ETA4, eta_init=ETA4, order=4, n_iter=1)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_timesym_corrector_replays_the_oracle_schedule_n512_to_t1(prec):
+    """The order-4 time-symmetric oracle's free-running schedule replayed on the
+    fourth-order GPU integrator with the time-symmetric corrector: FP64 states to
+    round-off growth, mixed states to the same bound as the Hermite corrector's
+    mixed replay; the energy error against the oracle's."""
+    m, x, v = inputs.plummer(512, seed=1)
+    sim = _sim4s(m, x, v)
+    K0, U0 = sim.energy()
+    rec = []
+    while True:
+        tick, idx = sim.step()
+        rec.append((tick, idx))
+        if tick >= int(1.0 / DT_MIN):
+            break
+    so = sim.state()
+    K1, U1 = sim.energy()
+    with gravidy.Integrator(m, x, v, EPS, ETA4, precision=prec, corrector="timesym") as g:
+        E0 = sum(g.energy())
+        for tick, idx in rec:
+            g.replay_step(tick, idx)
+        st = g.state()
+        E1 = sum(g.energy())
+    de_or = (K1 + U1 - K0 - U0) / (K0 + U0)
+    de = (E1 - E0) / E0
+    dx = np.abs(st["x"] - so["x"]).max()
+    agree = np.mean(st["dtau"] == so["dtau"])
+    print("%s timesym replay n=512: %d steps |dE/E| oracle %.3e gpu %.3e max|dx| %.2e dtau agree %.4f"
+          % (prec, len(rec), abs(de_or), abs(de), dx, agree))
+    assert (st["tau"] == so["tau"]).all()
+    if prec == "fp64":
+        assert dx < 1e-9 and abs(de - de_or) < 1e-10 and agree > 0.99
+    else:
+        assert dx < 1e-4 and abs(de) < 2 * abs(de_or) + 1e-9
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_timesym_corrector_free_run_n512_to_t1(prec):
+    """Free run to t = 1 with the time-symmetric corrector: block and particle
+    step counts of the order-4 time-symmetric oracle (identical for FP64 up to a
+    quantisation decision at a boundary, within 1 % for the mixed path) and an
+    energy error within 2x of the oracle's."""
+    m, x, v = inputs.plummer(512, seed=1)
+    sim = _sim4s(m, x, v)
+    K0, U0 = sim.energy()
+    sim.evolve(1.0)
+    K1, U1 = sim.energy()
+    so = sim.stats()
+    de_or = abs((K1 + U1 - K0 - U0) / (K0 + U0))
+    with gravidy.Integrator(m, x, v, EPS, ETA4, precision=prec, corrector="timesym") as g:
+        E0 = sum(g.energy())
+        g.evolve(1.0)
+        de = abs((sum(g.energy()) - E0) / E0)
+        st = g.stats()
+    print("%s timesym free n=512 t=1: |dE/E| oracle %.3e gpu %.3e blocks %d/%d psteps %d/%d"
+          % (prec, de_or, de, st["block_steps"], so["nblock"], st["particle_steps"], so["nsteps"]))
+    tol = 0.002 if prec == "fp64" else 0.01
+    assert abs(st["block_steps"] - so["nblock"]) <= tol * so["nblock"]
+    assert abs(st["particle_steps"] - so["nsteps"]) <= tol * so["nsteps"]
+    assert de <= 2 * de_or + 1e-9
+
+
+@pytest.mark.parametrize("opts", [dict(cluster=False), dict(fused=True)])
+def test_timesym_corrector_paths_agree(opts):
+    """The small-step cluster (default) against every step on the full GPU (force
+    sums in another order: round-off growth), and the fused cooperative kernel
+    (the same arithmetic: bit-identical), with the time-symmetric corrector."""
+    m, x, v = inputs.plummer(3000, seed=17)
+    res = []
+    for o in (dict(), opts):
+        with gravidy.Integrator(m, x, v, EPS, ETA4, precision="mixed", corrector="timesym", **o) as g:
+            g.evolve(0.125)
+            res.append(g.state())
+    a, b = res
+    if opts.get("fused"):
+        for k in a:
+            assert np.array_equal(a[k], b[k]), k
+    else:
+        assert (a["tau"] == b["tau"]).all()
+        assert np.mean(a["dtau"] == b["dtau"]) > 0.99
+        assert np.abs(a["x"] - b["x"]).max() < 1e-6
+
+
+def test_timesym_corrector_in_an_ensemble_follows_each_cluster_alone():
+    sizes = [300, 777, 64]
+    ms, xs, vs = [], [], []
+    for q, n in enumerate(sizes):
+        m, x, v = inputs.plummer(n, seed=500 + q)
+        ms.append(m)
+        xs.append(x)
+        vs.append(v)
+    with gravidy.Ensemble(sizes, np.concatenate(ms), np.concatenate(xs), np.concatenate(vs), EPS, ETA4,
+                          corrector="timesym") as e:
+        e.evolve(0.25)
+        st = e.state()
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    for q, n in enumerate(sizes):
+        with gravidy.Integrator(ms[q], xs[q], vs[q], EPS, ETA4, precision="mixed", corrector="timesym") as g:
+            g.evolve(0.25)
+            so = g.state()
+        sl = slice(off[q], off[q + 1])
+        assert np.mean(st["dtau"][sl] == so["dtau"]) > 0.99
+        assert np.abs(st["x"][sl] - so["x"]).max() < 1e-6
