@@ -72,6 +72,9 @@ def _load():
             "or_sim_energy": (None, [_P, _P, _P]),
             "or_sim_get": (None, [_P, _P, _P, _P, _P, _P, _P]),
             "or_sim_stats": (None, [_P, _P, _P, _P, _P]),
+            "or_pn_accel": (None, [_D, _D, _P, _P, _D, ctypes.c_int, _P]),
+            "or_pn_jerk": (None, [_D, _D, _P, _P, _P, _D, ctypes.c_int, _P]),
+            "or_sim_set_pn": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _D, ctypes.c_int]),
             "or6_force": (None, [_I64, _P, _P, _P, _P, _D, _I64, _P, _P, _P, _P]),
             "or6_predict_one": (None, [_P, _P, _P, _P, _P, _P, _D, _P, _P, _P]),
             "or6_correct_one": (None, [_P, _P, _P, _P, _P, _P, _P, _P, _D, _P, _P]),
@@ -208,6 +211,25 @@ def quantise(dt_new, dtau_old, tick_now, dt_min, dtau_max):
     return _load().or_quantise(float(dt_new), int(dtau_old), int(tick_now), float(dt_min), int(dtau_max))
 
 
+PN_1 = 1     # 1PN terms of the pair
+PN_25 = 4    # 2.5PN (radiation reaction) terms of the pair
+
+
+def pn_accel(mp, mq, r, v, c, terms=PN_1 | PN_25):
+    """Post-Newtonian relative acceleration of a pair (r = x_p - x_q, v = v_p - v_q)."""
+    a = np.zeros(3)
+    _load().or_pn_accel(float(mp), float(mq), _ptr(_f64(r)), _ptr(_f64(v)), float(c), int(terms), _ptr(a))
+    return a
+
+
+def pn_jerk(mp, mq, r, v, arel, c, terms=PN_1 | PN_25):
+    """Time derivative of pn_accel along the relative motion (dv/dt = arel)."""
+    j = np.zeros(3)
+    _load().or_pn_jerk(float(mp), float(mq), _ptr(_f64(r)), _ptr(_f64(v)), _ptr(_f64(arel)), float(c), int(terms),
+                       _ptr(j))
+    return j
+
+
 class Sim:
     """The oracle integrator (GraviDy Sec. 2.4 steps 1-7)."""
 
@@ -229,6 +251,11 @@ class Sim:
         if h is not None and h.value:
             self._lib.or_sim_free(h)
             self._h = None
+
+    def set_pn(self, p, q, c, terms=PN_1 | PN_25):
+        """Post-Newtonian terms for the pair (p, q), before the first step."""
+        if self._lib.or_sim_set_pn(self._h, int(p), int(q), float(c), int(terms)) != 0:
+            raise ValueError("oracle rejected the post-Newtonian pair")
 
     def step(self):
         """One free-running block step -> (tick, ascending active indices)."""

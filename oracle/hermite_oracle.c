@@ -282,6 +282,101 @@ int64_t or_quantise(double dt_new, int64_t dtau_old, int64_t tick_now, double dt
 }
 
 /* ------------------------------------------------------------------------ */
+/* Post-Newtonian terms of one pair (Sec. 5: corrections for a binary with  */
+/* eps = 0).  The paper prints no formulas; these are the relative          */
+/* accelerations of the two-body problem in harmonic coordinates at 1PN and */
+/* 2.5PN (radiation reaction) as published by Kidder (1995, Phys. Rev. D    */
+/* 52, 821, Eq. 2.2) and Blanchet (2014, Living Rev. Relativ. 17, 2, with   */
+/* A and B of its Eq. 219 at those orders).  With r = x_p - x_q,            */
+/* v = v_p - v_q, M = m_p + m_q, eta = m_p m_q / M^2, n = r / |r|,          */
+/* rdot = n.v and c the speed of light in code units (G = 1):               */
+/*   1PN:   M / (c^2 r^2) { [(4 + 2 eta) M/r - (1 + 3 eta) v^2              */
+/*                           + 3/2 eta rdot^2] n + (4 - 2 eta) rdot v }     */
+/*   2.5PN: 8/5 eta M^2 / (c^5 r^3) { rdot [18 v^2 + 2/3 M/r - 25 rdot^2] n */
+/*                                    - [6 v^2 - 2 M/r - 15 rdot^2] v }     */
+/* terms: bit 1 selects 1PN, bit 4 selects 2.5PN (2PN is not built).  The   */
+/* pair's particles get m_q/M and -m_p/M of the relative term, which keeps  */
+/* the pair's centre of mass at rest at this order.                         */
+/* ------------------------------------------------------------------------ */
+
+void or_pn_accel(double mp, double mq, const double r[3], const double v[3], double c, int terms,
+                 double a[3])
+{
+    double M = mp + mq, eta = mp * mq / (M * M);
+    double rr = norm3(r), n[3], v2 = 0.0, rd = 0.0;
+    for (int k = 0; k < 3; k++) {
+        n[k] = r[k] / rr;
+        v2 += v[k] * v[k];
+    }
+    for (int k = 0; k < 3; k++)
+        rd += n[k] * v[k];
+    for (int k = 0; k < 3; k++)
+        a[k] = 0.0;
+    if (terms & 1) {
+        double K = M / (c * c * rr * rr);
+        double alpha = (4.0 + 2.0 * eta) * M / rr - (1.0 + 3.0 * eta) * v2 + 1.5 * eta * rd * rd;
+        double beta = (4.0 - 2.0 * eta) * rd;
+        for (int k = 0; k < 3; k++)
+            a[k] += K * (alpha * n[k] + beta * v[k]);
+    }
+    if (terms & 4) {
+        double K = 1.6 * eta * M * M / (pow(c, 5.0) * rr * rr * rr);
+        double alpha = rd * (18.0 * v2 + 2.0 / 3.0 * M / rr - 25.0 * rd * rd);
+        double beta = -(6.0 * v2 - 2.0 * M / rr - 15.0 * rd * rd);
+        for (int k = 0; k < 3; k++)
+            a[k] += K * (alpha * n[k] + beta * v[k]);
+    }
+}
+
+/* The time derivative of or_pn_accel along the relative motion, with
+ * dr/dt = v and dv/dt = arel, by the chain rule written out term by term:
+ * d|r|/dt = rdot, dn/dt = (v - rdot n)/|r|, d(v^2)/dt = 2 v.arel,
+ * d(rdot)/dt = (v^2 - rdot^2)/|r| + n.arel. */
+void or_pn_jerk(double mp, double mq, const double r[3], const double v[3], const double arel[3],
+                double c, int terms, double j[3])
+{
+    double M = mp + mq, eta = mp * mq / (M * M);
+    double rr = norm3(r), n[3], v2 = 0.0, rd = 0.0, va = 0.0, na = 0.0, dn[3];
+    for (int k = 0; k < 3; k++) {
+        n[k] = r[k] / rr;
+        v2 += v[k] * v[k];
+        va += v[k] * arel[k];
+    }
+    for (int k = 0; k < 3; k++) {
+        rd += n[k] * v[k];
+        na += n[k] * arel[k];
+    }
+    for (int k = 0; k < 3; k++)
+        dn[k] = (v[k] - rd * n[k]) / rr;
+    double drd = (v2 - rd * rd) / rr + na, dv2 = 2.0 * va;
+    for (int k = 0; k < 3; k++)
+        j[k] = 0.0;
+    if (terms & 1) {
+        double K = M / (c * c);
+        double alpha = (4.0 + 2.0 * eta) * M / rr - (1.0 + 3.0 * eta) * v2 + 1.5 * eta * rd * rd;
+        double beta = (4.0 - 2.0 * eta) * rd;
+        double dalpha = -(4.0 + 2.0 * eta) * M * rd / (rr * rr) - (1.0 + 3.0 * eta) * dv2 + 3.0 * eta * rd * drd;
+        double dbeta = (4.0 - 2.0 * eta) * drd;
+        double i2 = 1.0 / (rr * rr), di2 = -2.0 * rd / (rr * rr * rr);
+        for (int k = 0; k < 3; k++)
+            j[k] += K * (di2 * (alpha * n[k] + beta * v[k]) +
+                         i2 * (dalpha * n[k] + alpha * dn[k] + dbeta * v[k] + beta * arel[k]));
+    }
+    if (terms & 4) {
+        double K = 1.6 * eta * M * M / pow(c, 5.0);
+        double P = 18.0 * v2 + 2.0 / 3.0 * M / rr - 25.0 * rd * rd;
+        double dP = 18.0 * dv2 - 2.0 / 3.0 * M * rd / (rr * rr) - 50.0 * rd * drd;
+        double alpha = rd * P, dalpha = drd * P + rd * dP;
+        double beta = -(6.0 * v2 - 2.0 * M / rr - 15.0 * rd * rd);
+        double dbeta = -(6.0 * dv2 + 2.0 * M * rd / (rr * rr) - 30.0 * rd * drd);
+        double i3 = 1.0 / (rr * rr * rr), di3 = -3.0 * rd / (rr * rr * rr * rr);
+        for (int k = 0; k < 3; k++)
+            j[k] += K * (di3 * (alpha * n[k] + beta * v[k]) +
+                         i3 * (dalpha * n[k] + alpha * dn[k] + dbeta * v[k] + beta * arel[k]));
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* The integrator (Sec. 2.4 steps 1-7).                                      */
 /* ------------------------------------------------------------------------ */
 
@@ -297,6 +392,9 @@ typedef struct or_sim {
     int64_t tick;                /* time of the last block step */
     int64_t nblock, nsteps;      /* block steps, particle steps */
     double interactions;         /* sum of nact * n over force evaluations */
+    int32_t pn_p, pn_q;          /* post-Newtonian pair (pn_terms != 0) */
+    double pn_c;
+    int pn_terms;
 } or_sim;
 
 void or_sim_free(or_sim *s)
@@ -360,6 +458,60 @@ or_sim *or_sim_new(int64_t n, const double *m, const double *x, const double *v,
     return s;
 }
 
+/* Adds the post-Newtonian terms of the pair (p, q) to particle i's force and
+ * jerk, from positions x and velocities v of both (the same time); the jerk's
+ * relative acceleration is the pair's Newtonian one, -M r / |r|^3. */
+static void add_pn(const or_sim *s, int64_t i, const double *x, const double *v, double a[3], double j[3])
+{
+    int64_t p = s->pn_p, q = s->pn_q;
+    double mp = s->m[p], mq = s->m[q], M = mp + mq;
+    double r[3], vr[3], ar[3], apn[3], jpn[3];
+    for (int c = 0; c < 3; c++) {
+        r[c] = x[3 * p + c] - x[3 * q + c];
+        vr[c] = v[3 * p + c] - v[3 * q + c];
+    }
+    double rr = norm3(r);
+    for (int c = 0; c < 3; c++)
+        ar[c] = -M * r[c] / (rr * rr * rr);
+    or_pn_accel(mp, mq, r, vr, s->pn_c, s->pn_terms, apn);
+    or_pn_jerk(mp, mq, r, vr, ar, s->pn_c, s->pn_terms, jpn);
+    double w = i == p ? mq / M : -mp / M;
+    for (int c = 0; c < 3; c++) {
+        a[c] += w * apn[c];
+        j[c] += w * jpn[c];
+    }
+}
+
+/* Enables the post-Newtonian terms of the pair (p, q) (p != q, terms as for
+ * or_pn_accel, c > 0).  Called before the first block step: the initial
+ * forces and first steps of p and q are recomputed with the terms.  Returns 0,
+ * or -1 for a bad argument or a call after the first step. */
+int or_sim_set_pn(or_sim *s, int32_t p, int32_t q, double c, int terms)
+{
+    if (p < 0 || q < 0 || p >= s->n || q >= s->n || p == q || !(c > 0) || (terms & ~5) || s->nblock > 0)
+        return -1;
+    s->pn_p = p;
+    s->pn_q = q;
+    s->pn_c = c;
+    s->pn_terms = terms;
+    int32_t pq[2] = {p, q};
+    or_force(s->n, s->m, s->x, s->v, s->eps2, 2, pq, s->a1, s->j1);
+    for (int k = 0; k < 2; k++) {
+        int64_t i = pq[k];
+        add_pn(s, i, s->x, s->v, s->a1 + 3 * k, s->j1 + 3 * k);
+        for (int cc = 0; cc < 3; cc++) {
+            s->a[3 * i + cc] = s->a1[3 * k + cc];
+            s->j[3 * i + cc] = s->j1[3 * k + cc];
+        }
+        if (s->fixed_dtau <= 0) {
+            double dt0 = s->eta * norm3(s->a + 3 * i) / norm3(s->j + 3 * i);
+            s->dtau[i] = or_quantise_init(dt0, s->dt_min, s->dtau_max);
+            s->tnext[i] = s->dtau[i];
+        }
+    }
+    return 0;
+}
+
 /* Steps 6-7 for a given block time and active list (idx ascending or not). */
 static void block_step(or_sim *s, int64_t tick_next, int64_t nact, const int32_t *idx)
 {
@@ -373,6 +525,10 @@ static void block_step(or_sim *s, int64_t tick_next, int64_t nact, const int32_t
     /* 7c: new force and jerk of the active particles from predicted values */
     or_force(n, s->m, s->xp, s->vp, s->eps2, nact, idx, s->a1, s->j1);
     s->interactions += (double)nact * (double)n;
+    if (s->pn_terms)
+        for (int64_t k = 0; k < nact; k++)
+            if (idx[k] == s->pn_p || idx[k] == s->pn_q)
+                add_pn(s, idx[k], s->xp, s->vp, s->a1 + 3 * k, s->j1 + 3 * k);
     /* 7d + 6: correct, take the new step, and keep a1, j1 as the new a0, j0 */
     for (int64_t k = 0; k < nact; k++) {
         int64_t i = idx[k];
