@@ -204,6 +204,18 @@ void launch_part_sum(gd_ctx *c, int nact, const Tune &tn)
     c->launches += 1;
 }
 
+// The post-Newtonian pair terms added to the summed forces of the first nact
+// slots (the block steps add them in the corrector).
+void launch_pn_fsum(gd_ctx *c, int nact)
+{
+    if (!c->d.pn_terms) return;
+    if (c->mixed)
+        k_pn_fsum<true><<<(nact + 255) / 256, 256, 0, c->stream>>>(c->d, nact);
+    else
+        k_pn_fsum<false><<<(nact + 255) / 256, 256, 0, c->stream>>>(c->d, nact);
+    c->launches += 1;
+}
+
 // force only (no correction) of nact active slots, summed into fsum: hooks and
 // initial forces, with the same work decomposition as the block steps
 void launch_force(gd_ctx *c, int nact)
@@ -309,7 +321,7 @@ void launch_cycle(gd_ctx *c, int slot, cudaEvent_t e0, cudaEvent_t e1, bool capt
 void cluster_setup(gd_ctx *c)
 {
     c->cl_C = 0;
-    if (!c->mixed || !c->opt.cluster) return;
+    if (!c->mixed || !c->opt.cluster || c->d.pn_terms) return;
     const void *fn = c->soft ? (const void *)k_cluster_steps<true> : (const void *)k_cluster_steps<false>;
     int maxdyn = 0;
     cudaDeviceGetAttribute(&maxdyn, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev);
@@ -472,6 +484,7 @@ int first_forces(gd_ctx *c)
     k_iota<<<(n + 255) / 256, 256, 0, c->stream>>>(d.act, n);
     k_set_step<<<1, 1, 0, c->stream>>>(d.ctrl, 0, n);
     launch_force(c, n);
+    launch_pn_fsum(c, n);
     if (c->mixed)
         k_init_steps<true><<<(n + 255) / 256, 256, 0, c->stream>>>(d);
     else
@@ -696,6 +709,10 @@ void gd_opts_default(gd_opts *o)
     o->tail_correct = 0;
     o->cluster = 1;
     o->corrector = GD_CORR_HERMITE;
+    o->pn_terms = 0;
+    o->pn_p = 0;
+    o->pn_q = 1;
+    o->pn_c = 0.0;
 }
 
 }  // extern "C"
@@ -722,6 +739,14 @@ int ctx_init(gd_ctx **out, int64_t n, const double *m, const double *x, const do
     if (o.precision != GD_FP64 && o.precision != GD_MIXED) return fail(nullptr, GD_EINVAL, "bad precision");
     if (o.corrector != GD_CORR_HERMITE && o.corrector != GD_CORR_TIMESYM)
         return fail(nullptr, GD_EINVAL, "corrector must be GD_CORR_HERMITE or GD_CORR_TIMESYM");
+    if (o.pn_terms != 0) {
+        if (o.pn_terms & ~(GD_PN_1 | GD_PN_25))
+            return fail(nullptr, GD_EINVAL, "pn_terms must combine GD_PN_1 and GD_PN_25 (2PN is not built)");
+        if (o.pn_p < 0 || o.pn_q < 0 || o.pn_p >= n || o.pn_q >= n || o.pn_p == o.pn_q)
+            return fail(nullptr, GD_EINVAL, "pn_p and pn_q must be distinct indices in [0, n)");
+        if (!(o.pn_c > 0) || !std::isfinite(o.pn_c)) return fail(nullptr, GD_EINVAL, "pn_c must be finite and > 0");
+        if (!(m[o.pn_p] + m[o.pn_q] > 0)) return fail(nullptr, GD_EINVAL, "the post-Newtonian pair needs mass");
+    }
     // the mixed path counts steps in FP32: tick counts up to dtau_max and dt_min^5 stay exact
     if (o.precision == GD_MIXED && (o.dt_min < std::ldexp(1.0, -24) || o.dt_max / o.dt_min > std::ldexp(1.0, 24)))
         return fail(nullptr, GD_EINVAL, "mixed precision needs dt_min >= 2^-24 and dt_max/dt_min <= 2^24");
@@ -800,6 +825,10 @@ int ctx_init(gd_ctx **out, int64_t n, const double *m, const double *x, const do
     d.inv_dt_min_f = (float)(1.0 / o.dt_min);
     d.eta_f = (float)eta;
     d.tsym = o.corrector == GD_CORR_TIMESYM ? 1 : 0;
+    d.pn_terms = o.pn_terms;
+    d.pn_p = o.pn_p;
+    d.pn_q = o.pn_q;
+    d.pn_c = o.pn_c;
     c->nchunks = (d.n + ST - 1) / ST;
     // the select kernel's CTAs wait for the counts of lower CTAs: keep its grid co-resident
     c->grid_sel = std::max(1, std::min(c->nchunks, sms * std::max(1, occ_sel)));
@@ -1279,6 +1308,7 @@ int gd_force(gd_ctx *c, int64_t tick, const int32_t *idx, int64_t nact, double *
     if (c->opt.time_force) CK(cudaEventRecord(c->ev[0], c->stream));
     launch_force(c, (int)nact);
     if (c->opt.time_force) CK(cudaEventRecord(c->ev[1], c->stream));
+    launch_pn_fsum(c, (int)nact);
     CK(cudaGetLastError());
     // fsum planes (stride n) -> staging, first nact rows (the mixed path's FP32
     // sums widened into the FP64 planes pd first)
@@ -1511,6 +1541,7 @@ int gd_ens_init(gd_ens **out, int32_t nclusters, const int64_t *n_per, const dou
     gd_opts_default(&o);
     if (opt) o = *opt;
     if (o.precision != GD_MIXED) return ens_fail(nullptr, GD_EINVAL, "ensembles run in GD_MIXED precision");
+    if (o.pn_terms != 0) return ens_fail(nullptr, GD_EINVAL, "ensembles take no post-Newtonian pair");
     // padded layout
     std::vector<int> cs(nclusters), cnp(nclusters), cn(nclusters);
     long long total = 0, nreal = 0;

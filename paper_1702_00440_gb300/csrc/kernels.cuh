@@ -107,6 +107,9 @@ struct Dev {
     float eps2f;
     float dt_min_f, inv_dt_min_f, eta_f;  // FP32 copies (dt_min is a power of two: exact)
     int tsym;                 // corrector: 0 the Hermite scheme's, 1 the time-symmetric form
+    int pn_terms;             // post-Newtonian terms of the pair (pn_p, pn_q): 0 none, bit 1 1PN, bit 4 2.5PN
+    int pn_p, pn_q;
+    double pn_c;              // speed of light in code units
     // FP64 state at each particle's own time, structure of arrays (plane c at +c*n);
     // on the mixed path these planes only stage the state in and out (k_state_to_ds,
     // k_state_from_ds)
@@ -893,6 +896,149 @@ __device__ __forceinline__ P part_sum(const Dev &d, int nact, int S, int c, int 
     return combine8<P>(q);
 }
 
+// ---------------------------------------------------------------- post-Newtonian pair terms
+//
+// Sec. 5's corrections for a binary: the 1PN and 2.5PN relative accelerations of the
+// two-body problem in harmonic coordinates (Kidder 1995, Eq. 2.2; Blanchet 2014,
+// Eq. 219), with r = x_p - x_q, v = v_p - v_q, M = m_p + m_q, eta = m_p m_q / M^2,
+// n = r / |r|, rdot = n.v:
+//   1PN:   M / (c^2 r^2) {[(4 + 2 eta) M/r - (1 + 3 eta) v^2 + 3/2 eta rdot^2] n + (4 - 2 eta) rdot v}
+//   2.5PN: 8/5 eta M^2 / (c^5 r^3) {rdot [18 v^2 + 2/3 M/r - 25 rdot^2] n - [6 v^2 - 2 M/r - 15 rdot^2] v}
+// and their time derivative for the jerk, taken by carrying every quantity as a dual
+// number (value, d/dt) along r' = v, v' = -M r / |r|^3 (the pair's Newtonian relative
+// acceleration).  p gets m_q / M of the relative term, q gets -m_p / M.
+
+template <class T>
+struct Dual {
+    T v, d;
+};
+template <class T>
+__device__ __forceinline__ Dual<T> dadd(Dual<T> a, Dual<T> b) { return Dual<T>{a.v + b.v, a.d + b.d}; }
+template <class T>
+__device__ __forceinline__ Dual<T> dsub(Dual<T> a, Dual<T> b) { return Dual<T>{a.v - b.v, a.d - b.d}; }
+template <class T>
+__device__ __forceinline__ Dual<T> dmul(Dual<T> a, Dual<T> b) { return Dual<T>{a.v * b.v, a.d * b.v + a.v * b.d}; }
+template <class T>
+__device__ __forceinline__ Dual<T> dscale(T s, Dual<T> a) { return Dual<T>{s * a.v, s * a.d}; }
+template <class T>
+__device__ __forceinline__ Dual<T> dinv(Dual<T> a) { const T i = T(1) / a.v; return Dual<T>{i, -a.d * i * i}; }
+template <class T>
+__device__ __forceinline__ Dual<T> dsqrt(Dual<T> a) { const T s = sqrt(a.v); return Dual<T>{s, a.d / (T(2) * s)}; }
+
+// The pair's relative post-Newtonian acceleration (apn) and its time derivative (jpn)
+// from the relative position r and velocity v.
+template <class T>
+__device__ void pn_pair_terms(int terms, T mp, T mq, T c, const T r[3], const T v[3], T apn[3], T jpn[3])
+{
+    const T M = mp + mq, eta = mp * mq / (M * M);
+    const T r2v = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+    const T rinv3 = T(1) / (r2v * sqrt(r2v));
+    Dual<T> R[3], V[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        R[k] = Dual<T>{r[k], v[k]};
+        V[k] = Dual<T>{v[k], -M * r[k] * rinv3};
+    }
+    Dual<T> r2 = dmul(R[0], R[0]), v2 = dmul(V[0], V[0]), rv = dmul(R[0], V[0]);
+#pragma unroll
+    for (int k = 1; k < 3; k++) {
+        r2 = dadd(r2, dmul(R[k], R[k]));
+        v2 = dadd(v2, dmul(V[k], V[k]));
+        rv = dadd(rv, dmul(R[k], V[k]));
+    }
+    const Dual<T> rr = dsqrt(r2), ir = dinv(rr);
+    const Dual<T> rd = dmul(rv, ir);  // rdot
+    const Dual<T> Mr = dscale(M, ir);  // M / r
+    Dual<T> acc[3] = {{T(0), T(0)}, {T(0), T(0)}, {T(0), T(0)}};
+    if (terms & 1) {
+        const Dual<T> alpha = dadd(dsub(dscale(T(4) + T(2) * eta, Mr), dscale(T(1) + T(3) * eta, v2)),
+                                   dscale(T(1.5) * eta, dmul(rd, rd)));
+        const Dual<T> beta = dscale(T(4) - T(2) * eta, rd);
+        const Dual<T> K = dscale(M / (c * c), dmul(ir, ir));
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            acc[k] = dadd(acc[k], dmul(K, dadd(dmul(alpha, dmul(R[k], ir)), dmul(beta, V[k]))));
+    }
+    if (terms & 4) {
+        const Dual<T> rd2 = dmul(rd, rd);
+        const Dual<T> alpha = dmul(rd, dadd(dsub(dscale(T(18), v2), dscale(T(25), rd2)), dscale(T(2) / T(3), Mr)));
+        const Dual<T> beta = dsub(dadd(dscale(T(2), Mr), dscale(T(15), rd2)), dscale(T(6), v2));
+        const T c2 = c * c;
+        const Dual<T> K = dscale(T(1.6) * eta * M * M / (c2 * c2 * c), dmul(ir, dmul(ir, ir)));
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            acc[k] = dadd(acc[k], dmul(K, dadd(dmul(alpha, dmul(R[k], ir)), dmul(beta, V[k]))));
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        apn[k] = acc[k].v;
+        jpn[k] = acc[k].d;
+    }
+}
+
+// Particle i's share of the pair terms, component c, from the predicted j-records
+// (mixed: double-single positions, FP32 velocities; FP64: the planes pd) at the
+// block time.  Adds to a and j when i is one of the pair.
+template <bool MIXED, bool COH, class T>
+__device__ __forceinline__ void pn_add(const Dev &d, int i, int c, T &a, T &j)
+{
+    if (!d.pn_terms || (i != d.pn_p && i != d.pn_q)) return;
+    const int p = d.pn_p, q = d.pn_q;
+    T r[3], v[3], mp, mq;
+    if (MIXED) {
+        const float4 Ap = ldx<COH>(&d.jA[p]), Bp = ldx<COH>(&d.jB[p]), Aq = ldx<COH>(&d.jA[q]), Bq = ldx<COH>(&d.jB[q]);
+        const float2 Cp = ldx<COH>(&d.jC[p]), Cq = ldx<COH>(&d.jC[q]);
+        r[0] = (T)((Ap.x - Aq.x) + (Bp.x - Bq.x));
+        r[1] = (T)((Ap.y - Aq.y) + (Bp.y - Bq.y));
+        r[2] = (T)((Ap.z - Aq.z) + (Bp.z - Bq.z));
+        v[0] = (T)(Bp.w - Bq.w);
+        v[1] = (T)(Cp.x - Cq.x);
+        v[2] = (T)(Cp.y - Cq.y);
+        mp = (T)Ap.w;
+        mq = (T)Aq.w;
+    } else {
+        const int np = d.npad;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            r[k] = (T)(ldx<COH>(&d.pd[k * np + p]) - ldx<COH>(&d.pd[k * np + q]));
+            v[k] = (T)(ldx<COH>(&d.pd[(3 + k) * np + p]) - ldx<COH>(&d.pd[(3 + k) * np + q]));
+        }
+        mp = (T)d.pd[6 * np + p];
+        mq = (T)d.pd[6 * np + q];
+    }
+    T apn[3], jpn[3];
+    pn_pair_terms<T>(d.pn_terms, mp, mq, (T)d.pn_c, r, v, apn, jpn);
+    const T w = i == p ? mq / (mp + mq) : -mp / (mp + mq);
+    const T ac = c == 0 ? apn[0] : (c == 1 ? apn[1] : apn[2]);
+    const T jc = c == 0 ? jpn[0] : (c == 1 ? jpn[1] : jpn[2]);
+    a += w * ac;
+    j += w * jc;
+}
+
+// Adds the pair terms to the summed forces of the first nact active slots (the
+// initial forces and the force hook); one thread per slot.
+template <bool MIXED>
+__global__ void k_pn_fsum(Dev d, int nact)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nact) return;
+    const int i = d.act[k];
+    for (int c = 0; c < 3; c++) {
+        if (MIXED) {
+            float *fs = (float *)d.fsum;
+            float a = fs[(long long)c * d.n + k], j = fs[(long long)(3 + c) * d.n + k];
+            pn_add<true, false, float>(d, i, c, a, j);
+            fs[(long long)c * d.n + k] = a;
+            fs[(long long)(3 + c) * d.n + k] = j;
+        } else {
+            double a = d.fsum[(long long)c * d.n + k], j = d.fsum[(long long)(3 + c) * d.n + k];
+            pn_add<false, false, double>(d, i, c, a, j);
+            d.fsum[(long long)c * d.n + k] = a;
+            d.fsum[(long long)(3 + c) * d.n + k] = j;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- corrector + time step
 
 // The power-of-two block step after a correction at tick T, from the Aarseth
@@ -1130,8 +1276,9 @@ __device__ __forceinline__ void correct_slots_ds(const Dev &d, long long T, int 
         const bool behind = dtick > 0;
         const F2 x0 = ldx_ds<COH>(d.xs, n, c, i), v0 = ldx_ds<COH>(d.vs, n, c, i);
         const float a0 = ldx<COH>(&d.af[c * n + i]), j0 = ldx<COH>(&d.jf[c * n + i]);
-        const float a1 = S > 0 ? part_sum<float>(d, nact, S, c, kk) : ldc(&fs[c * n + kk]);
-        const float j1 = S > 0 ? part_sum<float>(d, nact, S, 3 + c, kk) : ldc(&fs[(3 + c) * n + kk]);
+        float a1 = S > 0 ? part_sum<float>(d, nact, S, c, kk) : ldc(&fs[c * n + kk]);
+        float j1 = S > 0 ? part_sum<float>(d, nact, S, 3 + c, kk) : ldc(&fs[(3 + c) * n + kk]);
+        pn_add<true, COH, float>(d, i, c, a1, j1);
         F2 x1, v1;
         long long dtau;
         ds_correct(d, real, behind ? dtick : 1, dtau_old, T, x0, v0, a0, j0, a1, j1, x1, v1, dtau);
@@ -1197,8 +1344,9 @@ __device__ __forceinline__ void correct_slots64(const Dev &d, long long T, int k
         const double h2 = 0.5 * dt2, h3 = dt3 * (1.0 / 6.0), h4 = dt4 * (1.0 / 24.0), h5 = dt5 * (1.0 / 120.0);
         const double x0 = ldx<COH>(&d.x[c * n + i]), v0 = ldx<COH>(&d.v[c * n + i]),
                      a0 = ldx<COH>(&d.a[c * n + i]), j0 = ldx<COH>(&d.jk[c * n + i]);
-        const double a1 = S > 0 ? part_sum<double>(d, nact, S, c, kk) : ldc(&d.fsum[(long long)c * n + kk]);
-        const double j1 = S > 0 ? part_sum<double>(d, nact, S, 3 + c, kk) : ldc(&d.fsum[(long long)(3 + c) * n + kk]);
+        double a1 = S > 0 ? part_sum<double>(d, nact, S, c, kk) : ldc(&d.fsum[(long long)c * n + kk]);
+        double j1 = S > 0 ? part_sum<double>(d, nact, S, 3 + c, kk) : ldc(&d.fsum[(long long)(3 + c) * n + kk]);
+        pn_add<false, COH, double>(d, i, c, a1, j1);
         // prediction of this component (Sec. 2.4 step 7a)
         const double xp = fma(j0, h3, fma(a0, h2, fma(v0, dt, x0)));
         const double vp = fma(j0, h2, fma(a0, dt, v0));

@@ -21,6 +21,7 @@ from . import build as _build
 GD_OK, GD_EINVAL, GD_ENOMEM, GD_ECUDA, GD_ENONFINITE, GD_ETIMEOUT, GD_ESTATE = 0, -1, -2, -3, -4, -5, -6
 GD_FP64, GD_MIXED = 0, 1
 GD_CORR_HERMITE, GD_CORR_TIMESYM = 0, 1
+GD_PN_1, GD_PN_25 = 1, 4
 _PRECISION = {"fp64": GD_FP64, "mixed": GD_MIXED, GD_FP64: GD_FP64, GD_MIXED: GD_MIXED}
 
 # every entry point the header declares
@@ -60,6 +61,10 @@ class gd_opts(ctypes.Structure):
         ("tail_correct", ctypes.c_int32),
         ("cluster", ctypes.c_int32),
         ("corrector", ctypes.c_int32),
+        ("pn_terms", ctypes.c_int32),
+        ("pn_p", ctypes.c_int32),
+        ("pn_q", ctypes.c_int32),
+        ("pn_c", ctypes.c_double),
     ]
 
 
@@ -168,7 +173,7 @@ def _check(rc, ctx=None):
 
 def make_opts(dt_min=2.0 ** -22, dt_max=0.125, precision="mixed", device=0, stream=None, use_graph=True,
               graph_steps=16, jsplit=0, mode_cut=0, time_force=False, autotune=False, fused=False, pdl=None,
-              tail_correct=None, cluster=None, corrector="hermite"):
+              tail_correct=None, cluster=None, corrector="hermite", pn=None):
     o = gd_opts()
     load().gd_opts_default(ctypes.byref(o))
     o.dt_min = float(dt_min)
@@ -190,6 +195,8 @@ def make_opts(dt_min=2.0 ** -22, dt_max=0.125, precision="mixed", device=0, stre
     if cluster is not None:
         o.cluster = 1 if cluster else 0
     o.corrector = {"hermite": GD_CORR_HERMITE, "timesym": GD_CORR_TIMESYM}[corrector]
+    if pn is not None:  # (p, q, c, terms)
+        o.pn_p, o.pn_q, o.pn_c, o.pn_terms = int(pn[0]), int(pn[1]), float(pn[2]), int(pn[3])
     return o
 
 

@@ -179,3 +179,42 @@ def test_fma_probe_rejects_bad_iteration_counts_on_the_host():
     tf = ctypes.c_double()
     assert lib.gd_probe_fma(0, 0, ctypes.byref(tf), None) == gravidy.GD_EINVAL
     assert lib.gd_probe_fma(0, (1 << 24) + 1, ctypes.byref(tf), None) == gravidy.GD_EINVAL
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """gd_opts and gd_stats as the C compiler lays them out (offset of every
+    field and the size) equal the ctypes structures the binding passes."""
+    import subprocess
+
+    include = os.path.dirname(HEADER)
+    lines = []
+    for st, cls in (("gd_opts", gravidy.gd_opts), ("gd_stats", gravidy.gd_stats)):
+        for name, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (st, name, st, name))
+        lines.append('printf("%s.size %%zu\\n", sizeof(%s));' % (st, st))
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "gravidy.h"\nint main(void) {\n'
+                   + "\n".join(lines) + "\nreturn 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", include, "-o", str(exe), str(src)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)]).decode().split("\n") if line)
+    for st, cls in (("gd_opts", gravidy.gd_opts), ("gd_stats", gravidy.gd_stats)):
+        for name, _ in cls._fields_:
+            assert int(got["%s.%s" % (st, name)]) == getattr(cls, name).offset, (st, name)
+        assert int(got["%s.size" % st]) == ctypes.sizeof(cls), st
+
+
+def test_post_newtonian_pair_is_checked_on_the_host():
+    lib = gravidy.load()
+    n, m, x, v = _small_system()
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    for pn in ((0, 0, 10.0, 1), (0, 4, 10.0, 1), (0, 1, -1.0, 1), (0, 1, 10.0, 2), (0, 1, float("nan"), 5)):
+        o = gravidy.make_opts(pn=pn)
+        h = ctypes.c_void_p()
+        assert lib.gd_init(ctypes.byref(h), n, p(m), p(x), p(v), 1e-4, 0.01, ctypes.byref(o)) == gravidy.GD_EINVAL
+        assert not h.value
+    sizes = np.array([n], dtype=np.int64)
+    o = gravidy.make_opts(pn=(0, 1, 10.0, 5))
+    h = ctypes.c_void_p()
+    assert lib.gd_ens_init(ctypes.byref(h), 1, p(sizes), p(m), p(x), p(v), 1e-4, 0.01,
+                           ctypes.byref(o)) == gravidy.GD_EINVAL
