@@ -429,16 +429,16 @@ def run_gravidy(a):
     peak_basis = "FP32 non-tensor: 152 SMs x 128 lanes x 2 flop x 2070 MHz (unit counts x max clock)"
     kernels = {}
     fname = "k_force_%s" % ("mixed" if a.precision == "mixed" else "fp64")
-    for name, ms, nl, inter in ((fname, f_ms, f_launches, f_inter),
-                                ("k_cluster_steps", c_ms, c_launches, c_inter)):
+    for name, ms, nl, k_inter in ((fname, f_ms, f_launches, f_inter),
+                                  ("k_cluster_steps", c_ms, c_launches, c_inter)):
         if nl <= 0 or ms <= 0:
             continue
-        ach = FLOP_PER_INTERACTION * inter / (ms / 1e3) / 1e12
+        ach = FLOP_PER_INTERACTION * k_inter / (ms / 1e3) / 1e12
         kernels[name] = {
             "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": ach / FP32_PEAK_TFLOPS, "traffic": _traffic(name), "kernel": name,
             "peak_basis": peak_basis, "flop_per_interaction": FLOP_PER_INTERACTION, "launches": nl,
-            "avg_launch_us": 1e3 * ms / nl, "interactions_per_launch": inter / nl,
+            "avg_launch_us": 1e3 * ms / nl, "interactions_per_launch": k_inter / nl,
             "share_of_step_time": ms / region_ms if region_ms > 0 else None,
         }
     if "k_cluster_steps" in kernels:
@@ -470,18 +470,23 @@ def run_gravidy(a):
         torch.cuda.synchronize()
         w0 = time.perf_counter()
         e_inter = 0.0
+        e_blocks = 0
         for _ in range(a.steps):
-            si = g.stats()["interactions"]
+            s_i = g.stats()
             g.set_state(pin["x"], pin["v"], pin["a"], pin["j"], pin["tau"], pin["dtau"])
             t_e += DT_STEP
             g.evolve(t_e)
             g.energy()
             g.state(out=pin)
-            e_inter += g.stats()["interactions"] - si
+            s_o = g.stats()
+            e_inter += s_o["interactions"] - s_i["interactions"]
+            e_blocks += s_o["block_steps"] - s_i["block_steps"]
         w1 = time.perf_counter()
         e_max = comm.reduce(w1 - w0, "MAX")
         e2e = {"value": comm.reduce(e_inter, "SUM") / e_max, "unit": UNIT, "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": bo, "same_block_steps_as_value": e_inter == inter,
+               "interactions": e_inter, "block_steps": e_blocks, "value_interactions": inter,
+               "value_block_steps": s1["block_steps"] - s0["block_steps"],
                "timing": "host wall clock, set_state + evolve(+1/8) + energy + get_state, replaying the timed "
                          "block steps from their starting state"}
 
@@ -680,7 +685,7 @@ def sweep_powerlaw(a):
     n = 262144
     m, x, v = inputs.plummer(n, seed=3, masses=inputs.power_law_masses(n, seed=3))
     g = gravidy.Integrator(m, x, v, EPS, ETA, precision="mixed", autotune=True)
-    _, split, mode, tms = g.tuning()
+    mode_cut, split, mode, tms = g.tuning()
     K0, U0 = g.energy()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -689,6 +694,19 @@ def sweep_powerlaw(a):
     K1, U1 = g.energy()
     st = g.stats()
     g.close()
+    # the same run on the cooperative fused path (every block step inside persistent
+    # launches: no per-step kernel launches), with the same tuning table
+    g = gravidy.Integrator(m, x, v, EPS, ETA, precision="mixed", fused=True)
+    g.set_tuning(mode_cut, split, mode)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.evolve(DT_STEP)
+    wall_f = time.perf_counter() - t0
+    Kf, Uf = g.energy()
+    stf = g.stats()
+    g.close()
+    fused = {"wall_s": wall_f, "s_per_nbu": wall_f / DT_STEP, "block_steps": stf["block_steps"],
+             "particle_steps": stf["particle_steps"], "dE_E": abs((Kf + Uf - K0 - U0) / (K0 + U0))}
     # the same run again one block step at a time, for the active-set histogram
     g = gravidy.Integrator(m, x, v, EPS, ETA, precision="mixed")
     hist = {}
@@ -713,7 +731,7 @@ def sweep_powerlaw(a):
     out = {"sweep": "powerlaw", "n": n, "t_end": DT_STEP, "wall_s": wall, "s_per_nbu": wall / DT_STEP,
            "block_steps": st["block_steps"], "particle_steps": st["particle_steps"],
            "interactions_per_s": (st["interactions"] - float(n) * n) / wall,
-           "dE_E": abs((K1 + U1 - K0 - U0) / (K0 + U0)), "histogram": per_bucket}
+           "dE_E": abs((K1 + U1 - K0 - U0) / (K0 + U0)), "fused_path": fused, "histogram": per_bucket}
     print(json.dumps(out))
     return 0
 

@@ -230,6 +230,21 @@ __device__ __forceinline__ T ldx(const T *p)
     return *p;
 }
 
+// Asynchronous global -> shared copies of 16 bytes through L2 (cp.async.cg: no L1,
+// so also coherent in the fused kernel), in commit groups; wait_group<N> returns once
+// at most N of this thread's groups are still in flight.
+__device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ long long warp_min_ll(long long v)
 {
     for (int o = 16; o > 0; o >>= 1) {
@@ -1532,20 +1547,57 @@ __device__ __forceinline__ void finish_item(const Dev &d, int nact, const Plan &
 
 constexpr int BJB = 256;  // warp mode j-tile (2 records per thread)
 
+// j-tiles of the force phases: nt records from jt (nt even) into buffer buf of the
+// CTA's double-buffered shared-memory tile, by asynchronous copies (one commit group
+// per tile, so the next tile loads while the warps work on the current one); the
+// C fields travel two records per 16-byte copy.
+struct JTile {
+    float4 A[2][BJB], B[2][BJB];
+    float2 C[2][BJB];
+};
+
+__device__ __forceinline__ void stage_jtile(const Dev &d, JTile &s, int buf, int jt, int nt)
+{
+    for (int q = threadIdx.x; q < nt; q += FT) {
+        cp_async16(&s.A[buf][q], &d.jA[jt + q]);
+        cp_async16(&s.B[buf][q], &d.jB[jt + q]);
+    }
+    for (int q = threadIdx.x; q < nt / 2; q += FT) cp_async16(&s.C[buf][2 * q], &d.jC[jt + 2 * q]);
+    cp_async_commit();
+}
+
+// Waits for the tile in the current buffer, first putting the next one (if any) in
+// flight; ends with a CTA barrier so every warp sees the current tile.
+__device__ __forceinline__ void next_jtile(const Dev &d, JTile &s, int buf, int jt, int tile, int jend)
+{
+    const int jn = jt + tile;
+    if (jn < jend) {
+        stage_jtile(d, s, buf ^ 1, jn, min(tile, jend - jn));
+        cp_async_wait<1>();
+    } else {
+        cp_async_wait<0>();
+    }
+    __syncthreads();
+}
+
 template <bool SOFT, bool COH>
 __device__ void phase_force_mixed(const Dev &d, int nact, const Plan &pl, bool tail, long long T,
                                   unsigned long long *Tacc, bool defer = false)
 {
     const float eps2 = d.eps2f;
-    __shared__ float4 sA[BJB], sB[BJB];
-    __shared__ float2 sC[BJB];
+    __shared__ __align__(16) JTile sj;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     for (long long item = blockIdx.x; item < pl.items; item += gridDim.x) {
         const int it = (int)(item / pl.S), s = (int)(item % pl.S);
         const int jbeg = s * pl.chunk;
         const int jend = min(jbeg + pl.chunk, d.npad);
+        // the j-range [jbeg, jend) comes in tiles of BJ (i-parallel) or BJB (warp mode)
+        // records, a multiple of BJ each; the first is put in flight here
+        const int tile = pl.mode == 0 ? BJ : BJB;
+        __syncthreads();  // the previous item's warps are done with both buffers
+        if (jbeg < jend) stage_jtile(d, sj, 0, jbeg, min(tile, jend - jbeg));
         if (pl.mode == 0) {
-            // i-parallel: thread t owns active slots k0 and k1; j-tiles staged in shared memory
+            // i-parallel: thread t owns active slots k0 and k1
             const int k0 = it * ITILE_A_MIX + t, k1 = k0 + FT;
             const int i0 = ldx<COH>(&d.act[min(k0, nact - 1)]), i1 = ldx<COH>(&d.act[min(k1, nact - 1)]);
             const float4 A0 = ldx<COH>(&d.jA[i0]), B0 = ldx<COH>(&d.jB[i0]);
@@ -1559,13 +1611,12 @@ __device__ void phase_force_mixed(const Dev &d, int nact, const Plan &pl, bool t
                 g0[c].zero();
                 g1[c].zero();
             }
-            for (int jt = jbeg; jt < jend; jt += BJ) {
-                __syncthreads();
-                sA[t] = ldx<COH>(&d.jA[jt + t]);
-                sB[t] = ldx<COH>(&d.jB[jt + t]);
-                sC[t] = ldx<COH>(&d.jC[jt + t]);
-                __syncthreads();
+            int buf = 0;
+            for (int jt = jbeg; jt < jend; jt += BJ, buf ^= 1) {
+                next_jtile(d, sj, buf, jt, BJ, jend);
                 if (busy) {
+                    const float4 *sA = sj.A[buf], *sB = sj.B[buf];
+                    const float2 *sC = sj.C[buf];
                     float f0[6] = {0, 0, 0, 0, 0, 0}, f1[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll 4
                     for (int jj = 0; jj < BJ; jj++) {
@@ -1580,6 +1631,7 @@ __device__ void phase_force_mixed(const Dev &d, int nact, const Plan &pl, bool t
                         g1[c].add(f1[c]);
                     }
                 }
+                __syncthreads();  // every warp is done with this buffer before it is refilled
             }
             float r0[6], r1[6];
 #pragma unroll
@@ -1590,8 +1642,8 @@ __device__ void phase_force_mixed(const Dev &d, int nact, const Plan &pl, bool t
             if (k0 < nact) store_partial<float>(d, nact, s, k0, r0);
             if (k1 < nact) store_partial<float>(d, nact, s, k1, r1);
         } else {
-            // warp j-parallel: warp w owns slots k0, k0+1; j-tiles of BJB staged in shared
-            // memory, the warp's lanes split each tile
+            // warp j-parallel: warp w owns slots k0, k0+1; the warp's lanes split each
+            // staged tile of BJB records
             const int k0 = it * ITILE_B_MIX + 2 * warp;
             const bool busy = k0 < nact;
             const bool has1 = k0 + 1 < nact;
@@ -1606,58 +1658,35 @@ __device__ void phase_force_mixed(const Dev &d, int nact, const Plan &pl, bool t
                 g0[c].zero();
                 g1[c].zero();
             }
-            if (COH) {
-                // same order as the direct loop below: FP32 sums over 32 * FOLD_B = 2 BJB
-                // j's, folded into the compensated sums
-                static_assert(32 * FOLD_B == 2 * BJB, "fold blocks span two staged tiles");
-                float f0[6] = {0, 0, 0, 0, 0, 0}, f1[6] = {0, 0, 0, 0, 0, 0};
-                for (int jt = jbeg; jt < jend; jt += BJB) {
-                    const int nt = min(BJB, jend - jt);  // a multiple of BJ
-                    __syncthreads();
-                    for (int q = t; q < nt; q += FT) {
-                        sA[q] = ldx<COH>(&d.jA[jt + q]);
-                        sB[q] = ldx<COH>(&d.jB[jt + q]);
-                        sC[q] = ldx<COH>(&d.jC[jt + q]);
-                    }
-                    __syncthreads();
-                    if (busy) {
+            // FP32 sums over 32 * FOLD_B = 2 BJB j's (each lane: FOLD_B of them), folded
+            // into the compensated sums
+            static_assert(32 * FOLD_B == 2 * BJB, "fold blocks span two staged tiles");
+            float f0[6] = {0, 0, 0, 0, 0, 0}, f1[6] = {0, 0, 0, 0, 0, 0};
+            int buf = 0;
+            for (int jt = jbeg; jt < jend; jt += BJB, buf ^= 1) {
+                const int nt = min(BJB, jend - jt);  // a multiple of BJ
+                next_jtile(d, sj, buf, jt, BJB, jend);
+                if (busy) {
+                    const float4 *sA = sj.A[buf], *sB = sj.B[buf];
+                    const float2 *sC = sj.C[buf];
 #pragma unroll 4
-                        for (int jj = lane; jj < nt; jj += 32) {
-                            const float4 A = sA[jj], B = sB[jj];
-                            const float2 C = sC[jj];
-                            pair_mixed<SOFT>(A, B, C, A0.x, A0.y, A0.z, B0.x, B0.y, B0.z, B0.w, C0.x, C0.y, eps2, f0);
-                            pair_mixed<SOFT>(A, B, C, A1.x, A1.y, A1.z, B1.x, B1.y, B1.z, B1.w, C1.x, C1.y, eps2, f1);
-                        }
-                        if (((jt - jbeg) / BJB) % 2 == 1 || jt + BJB >= jend) {
-#pragma unroll
-                            for (int c = 0; c < 6; c++) {
-                                g0[c].add(f0[c]);
-                                g1[c].add(f1[c]);
-                                f0[c] = 0.f;
-                                f1[c] = 0.f;
-                            }
-                        }
-                    }
-                }
-            } else if (busy) {
-                // between kernels the j-records are read-only: each lane reads its own
-                // j's through the read-only path, no shared-memory staging
-                for (int jb = jbeg; jb < jend; jb += 32 * FOLD_B) {
-                    const int je = min(jb + 32 * FOLD_B, jend);
-                    float f0[6] = {0, 0, 0, 0, 0, 0}, f1[6] = {0, 0, 0, 0, 0, 0};
-#pragma unroll 4
-                    for (int j = jb + lane; j < je; j += 32) {
-                        const float4 A = __ldg(&d.jA[j]), B = __ldg(&d.jB[j]);
-                        const float2 C = __ldg(&d.jC[j]);
+                    for (int jj = lane; jj < nt; jj += 32) {
+                        const float4 A = sA[jj], B = sB[jj];
+                        const float2 C = sC[jj];
                         pair_mixed<SOFT>(A, B, C, A0.x, A0.y, A0.z, B0.x, B0.y, B0.z, B0.w, C0.x, C0.y, eps2, f0);
                         pair_mixed<SOFT>(A, B, C, A1.x, A1.y, A1.z, B1.x, B1.y, B1.z, B1.w, C1.x, C1.y, eps2, f1);
                     }
+                    if (((jt - jbeg) / BJB) % 2 == 1 || jt + BJB >= jend) {
 #pragma unroll
-                    for (int c = 0; c < 6; c++) {
-                        g0[c].add(f0[c]);
-                        g1[c].add(f1[c]);
+                        for (int c = 0; c < 6; c++) {
+                            g0[c].add(f0[c]);
+                            g1[c].add(f1[c]);
+                            f0[c] = 0.f;
+                            f1[c] = 0.f;
+                        }
                     }
                 }
+                __syncthreads();  // every warp is done with this buffer before it is refilled
             }
             if (busy) {
                 float r0[6], r1[6];
