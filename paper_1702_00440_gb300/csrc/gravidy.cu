@@ -141,9 +141,10 @@ Tune effective_tune(const gd_ctx *c)
     return t;
 }
 
-// The block-step kernels leave i-parallel plans' j-split partials to k_correct
-// (FArgs::defer): summing them there uses the whole GPU instead of one CTA per tile.
-constexpr int DEFER_SUMS = 1;
+// The block-step kernels leave the j-split partials to k_correct (FArgs::defer; 2:
+// both work decompositions, unless warp-mode tiles correct in the force kernel's
+// tails): summing them there uses the whole GPU instead of one CTA per tile.
+constexpr int DEFER_SUMS = 2;
 
 FArgs fargs(const gd_ctx *c, int tail_ok, int defer = 0)
 {
@@ -195,7 +196,7 @@ void launch_force_with(gd_ctx *c, const FArgs &fa)
 void launch_part_sum(gd_ctx *c, int nact, const Tune &tn)
 {
     const Plan pl = make_plan(nact, c->d.npad, c->grid_force, tn, c->mixed, c->d.cap);
-    if (!DEFER_SUMS || pl.mode != 0) return;
+    if (!((DEFER_SUMS && pl.mode == 0) || DEFER_SUMS == 2)) return;
     const int g = (3 * nact + 255) / 256;
     if (c->mixed)
         k_part_sum<float><<<g, 256, 0, c->stream>>>(c->d, nact, pl.S);
@@ -579,7 +580,9 @@ int autotune(gd_ctx *c, int reps)
         for (int mode = 0; mode < 2; mode++) {
             const int itile = mode == 0 ? (c->mixed ? ITILE_A_MIX : ITILE_A_64) : (c->mixed ? ITILE_B_MIX : ITILE_B_64);
             const int itiles = (nact + itile - 1) / itile;
-            for (int S = 1; S <= smax; S *= 2) {
+            // j-split factors 1, 2, 3, 4, 6, 8, 12, ...: the work items (i-tiles x S) can
+            // then come close to a whole number of waves over the SMs
+            for (int S = 1; S <= smax; S = (S & (S - 1)) == 0 ? S + (S + 1) / 2 : S / 3 * 4) {
                 if ((long long)itiles * S > 16LL * c->grid_force) break;
                 if ((long long)S * nact > d.cap) break;
                 Tune t = base;

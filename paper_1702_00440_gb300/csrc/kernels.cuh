@@ -578,7 +578,6 @@ __global__ void __launch_bounds__(ST) k_select_predict(Dev d, int slot, int nchu
     __shared__ unsigned s_wcnt[ST / 32];
     __shared__ unsigned s_part[ST / 32];
     __shared__ long long s_wmin[ST / 32];
-    __shared__ unsigned s_base;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned tag = (ctrl->sel_gen & 0x7FFFFFFFu) + 1u;  // never 0 (the words start at 0)
     const int G = gridDim.x, b = blockIdx.x;
@@ -840,7 +839,8 @@ struct FArgs {
     int grid;
     Tune tn;
     int tail_ok;  // the host's choice of the TAIL kernel instance (the kernels use the template parameter)
-    int defer;    // 1: i-parallel plans leave their j-split partials to k_correct (see finish_item)
+    int defer;    // 1: i-parallel plans leave their j-split partials to k_correct, 2: every plan
+                  // whose tiles are not corrected in the force kernel's tails (see finish_item)
 };
 
 // ---------------------------------------------------------------- canonical sums of j-split partials
@@ -1503,16 +1503,17 @@ __device__ void tile_reduce_small(const Dev &d, int nact, int S, int k0, int nva
 // With `defer` an i-parallel plan (mode 0) stops after the partial stores: its
 // tiles hold up to ITILE_A_MIX slots and S partials each, which one CTA would sum
 // as a long chain of L2 round trips, while k_correct sums them spread over the GPU
-// (part_sum, the same canonical order).
+// (part_sum, the same canonical order).  With defer = 2 warp-mode plans do the same
+// unless they correct their tiles in the tail.
 template <class P, bool COH>
 __device__ __forceinline__ void finish_item(const Dev &d, int nact, const Plan &pl, int it, bool tail, long long T,
-                                            unsigned long long *Tacc, bool defer = false)
+                                            unsigned long long *Tacc, int defer = 0)
 {
     __shared__ int s_last;
     // the barrier gathers this CTA's partial stores; thread 0's fence releases them
     // before the arrival is counted
     __syncthreads();
-    if (defer && pl.mode == 0) return;
+    if ((defer && pl.mode == 0) || (defer == 2 && !tail)) return;
     if (threadIdx.x == 0) {
         __threadfence();
         const unsigned prev = atomicAdd(&d.tilecnt[it], 1u);
@@ -1582,7 +1583,7 @@ __device__ __forceinline__ void next_jtile(const Dev &d, JTile &s, int buf, int 
 
 template <bool SOFT, bool COH>
 __device__ void phase_force_mixed(const Dev &d, int nact, const Plan &pl, bool tail, long long T,
-                                  unsigned long long *Tacc, bool defer = false)
+                                  unsigned long long *Tacc, int defer = 0)
 {
     const float eps2 = d.eps2f;
     __shared__ __align__(16) JTile sj;
@@ -1750,10 +1751,10 @@ __global__ void __launch_bounds__(FT, 4) k_force_mixed(FArgs fa)
     const Plan pl = make_plan(nact, d.npad, fa.grid, fa.tn, true, d.cap);
     if (TAIL && pl.mode == 1) {
         const long long T = d.ctrl->T_cur;
-        phase_force_mixed<SOFT, false>(d, nact, pl, true, T, (unsigned long long *)&d.ctrl->T_acc, fa.defer != 0);
+        phase_force_mixed<SOFT, false>(d, nact, pl, true, T, (unsigned long long *)&d.ctrl->T_acc, fa.defer);
         finalize_step(d, nact, T, pl.items);
     } else {
-        phase_force_mixed<SOFT, false>(d, nact, pl, false, 0, nullptr, fa.defer != 0);
+        phase_force_mixed<SOFT, false>(d, nact, pl, false, 0, nullptr, fa.defer);
     }
 }
 
@@ -1819,7 +1820,7 @@ __global__ void __launch_bounds__(FT, 4) k_force_fp64(FArgs fa)
                 if (lane == 0) store_partial<double>(d, nact, s, k, g);
             }
         }
-        finish_item<double, false>(d, nact, pl, it, tail, T, (unsigned long long *)&d.ctrl->T_acc, fa.defer != 0);
+        finish_item<double, false>(d, nact, pl, it, tail, T, (unsigned long long *)&d.ctrl->T_acc, fa.defer);
     }
     if (tail) finalize_step(d, nact, T, pl.items);
 }
@@ -1830,7 +1831,7 @@ struct CArgs {
     Tune tn;       // force kernel has already corrected and finalized the step
     int tail_ok;
     int mixed;
-    int defer;     // the force kernel ran with FArgs::defer: i-parallel plans are summed here
+    int defer;     // the force kernel ran with FArgs::defer: its deferred plans are summed here
 };
 
 // Corrects every active particle and (last CTA) turns the running minimum into the
@@ -1846,7 +1847,7 @@ __global__ void __launch_bounds__(CT) k_correct(CArgs ca)
     if (nact <= 0) return;
     const Plan pl = make_plan(nact, d.npad, ca.grid, ca.tn, ca.mixed != 0, d.cap);
     if (ca.tail_ok && pl.mode == 1) return;
-    const int S = ca.defer && pl.mode == 0 ? pl.S : 0;
+    const int S = (ca.defer && pl.mode == 0) || ca.defer == 2 ? pl.S : 0;
     // only the CTAs that have particles to correct take part (eight per warp); the
     // others leave at once, so a small active set costs a few CTAs, not the grid
     constexpr int PER_CTA = (CT / 32) * 8;
