@@ -57,6 +57,9 @@ TRAFFIC_PER_LAUNCH = {
     # grid barrier's poll loop moved into a helper: the two captured kernels'
     # code is unchanged
     "ba8ae45d": {"k_cluster_steps": 1570560, "k_force_mixed": 714880},
+    # asynchronous double-buffered j-tiles in the force kernel, per-bucket choice of
+    # where warp-mode j-split sums are taken
+    "2d1d3ec0": {"k_cluster_steps": 1582080, "k_force_mixed": 716288},
 }
 
 
@@ -725,7 +728,7 @@ def sweep_powerlaw(a):
         if tms[b] > 0:
             row["force_ms"] = float(tms[b])
             row["interactions_per_s"] = float(2 ** b) * n / (float(tms[b]) / 1e3)
-            row["mode"] = "i-parallel" if mode[b] == 0 else "warp"
+            row["mode"] = {0: "i-parallel", 1: "warp", 2: "warp, sums in the corrector"}.get(int(mode[b]), "rule")
             row["jsplit"] = int(split[b])
         per_bucket.append(row)
     out = {"sweep": "powerlaw", "n": n, "t_end": DT_STEP, "wall_s": wall, "s_per_nbu": wall / DT_STEP,

@@ -173,20 +173,22 @@ int gd_set_state(gd_ctx *c, const double *x, const double *v, const double *a,
 /* Force-kernel autotuner: for every active-count bucket floor(log2 N_act) up to
  * 2^34 interactions, times the force kernel (CUDA events, median of reps
  * launches, 1 <= reps <= 100) on the current particles for both work
- * decompositions (i-parallel tiles, warp j-parallel tiles) and a ladder of
+ * decompositions (i-parallel tiles; warp j-parallel tiles, their j-split sums
+ * taken in the force kernel or in the corrector) and a ladder of
  * j-split factors (the j-range split of Sec. 2.5), and keeps the fastest choice
  * for later steps.  The integration state is not changed. */
 int gd_autotune(gd_ctx *c, int32_t reps);
 
 /* The tuning table: *mode_cut, and for buckets b < nbuckets (<= 32) the j-split
- * factor split[b] (0 = rule), the mode mode[b] (0 i-parallel, 1 warp, -1 rule)
+ * factor split[b] (0 = rule), the mode mode[b] (0 i-parallel, 1 warp, 2 warp with
+ * the j-split partials summed in the corrector, -1 rule)
  * and the autotuner's best force-kernel time ms[b] for N_act = 2^b (0 = not
  * measured).  Any pointer may be NULL. */
 int gd_get_tuning(gd_ctx *c, int32_t *mode_cut, int16_t *split, int8_t *mode, float *ms,
                   int32_t nbuckets);
 
 /* Replace the tuning table (the inverse of gd_get_tuning): mode_cut >= 1, and
- * for buckets b < nbuckets (<= 32) split[b] >= 0 and mode[b] in {-1, 0, 1}
+ * for buckets b < nbuckets (<= 32) split[b] >= 0 and mode[b] in {-1, 0, 1, 2}
  * (meanings as in gd_get_tuning; NULL leaves that column unchanged).  Two
  * contexts with the same table and state take the same block steps with the
  * same arithmetic.  The integration state is not changed. */

@@ -141,10 +141,10 @@ Tune effective_tune(const gd_ctx *c)
     return t;
 }
 
-// The block-step kernels leave the j-split partials to k_correct (FArgs::defer; 2:
-// both work decompositions, unless warp-mode tiles correct in the force kernel's
-// tails): summing them there uses the whole GPU instead of one CTA per tile.
-constexpr int DEFER_SUMS = 2;
+// The block-step kernels leave the j-split partials of late-summed plans (Plan::late:
+// i-parallel ones, and warp-mode ones tuned so) to k_correct (FArgs::defer): summing
+// them there uses the whole GPU instead of one CTA per tile.
+constexpr int DEFER_SUMS = 1;
 
 FArgs fargs(const gd_ctx *c, int tail_ok, int defer = 0)
 {
@@ -196,7 +196,7 @@ void launch_force_with(gd_ctx *c, const FArgs &fa)
 void launch_part_sum(gd_ctx *c, int nact, const Tune &tn)
 {
     const Plan pl = make_plan(nact, c->d.npad, c->grid_force, tn, c->mixed, c->d.cap);
-    if (!((DEFER_SUMS && pl.mode == 0) || DEFER_SUMS == 2)) return;
+    if (!DEFER_SUMS || !pl.late) return;
     const int g = (3 * nact + 255) / 256;
     if (c->mixed)
         k_part_sum<float><<<g, 256, 0, c->stream>>>(c->d, nact, pl.S);
@@ -577,7 +577,8 @@ int autotune(gd_ctx *c, int reps)
         float best = 1e30f;
         int best_mode = -1, best_s = 0;
         const int smax = std::max(1, d.npad / std::max(BJ, base.jchunk_min));
-        for (int mode = 0; mode < 2; mode++) {
+        // modes: 0 i-parallel, 1 warp (sums in the force kernel), 2 warp (sums in the corrector)
+        for (int mode = 0; mode < 3; mode++) {
             const int itile = mode == 0 ? (c->mixed ? ITILE_A_MIX : ITILE_A_64) : (c->mixed ? ITILE_B_MIX : ITILE_B_64);
             const int itiles = (nact + itile - 1) / itile;
             // j-split factors 1, 2, 3, 4, 6, 8, 12, ...: the work items (i-tiles x S) can
@@ -950,7 +951,7 @@ int gd_set_tuning(gd_ctx *c, int32_t mode_cut, const int16_t *split, const int8_
     if (mode_cut < 1) return fail(c, GD_EINVAL, "mode_cut must be >= 1");
     for (int b = 0; b < nbuckets; b++) {
         if (split && split[b] < 0) return fail(c, GD_EINVAL, "split factors must be >= 0");
-        if (mode && (mode[b] < -1 || mode[b] > 1)) return fail(c, GD_EINVAL, "modes must be -1, 0 or 1");
+        if (mode && (mode[b] < -1 || mode[b] > 2)) return fail(c, GD_EINVAL, "modes must be -1, 0, 1 or 2");
     }
     c->tn.mode_cut = mode_cut;
     for (int b = 0; b < nbuckets; b++) {

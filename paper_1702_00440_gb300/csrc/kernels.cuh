@@ -93,7 +93,8 @@ struct Tune {
     int jchunk_min;           // smallest j-chunk of a split (multiple of BJ)
     int items_x4;             // target work items = grid * items_x4 / 4
     short s_fixed[32];        // per floor(log2 N_act): > 0 forces the j-split factor
-    signed char mode_b[32];   // per floor(log2 N_act): 0 / 1 forces the mode, -1 = mode_cut
+    signed char mode_b[32];   // per floor(log2 N_act): 0 / 1 / 2 forces the mode (2: warp mode whose
+                              // j-split sums are left to the corrector), -1 = mode_cut
 };
 
 // ---------------------------------------------------------------- device state
@@ -143,6 +144,7 @@ struct Dev {
 
 struct Plan {
     int mode;     // 0 = i-parallel, 1 = warp j-parallel
+    int late;     // the j-split partials may be left to the corrector (i-parallel, or warp mode tuned 2)
     int itile;    // active particles per work item
     int itiles;
     int S;        // j-split factor
@@ -165,7 +167,8 @@ __host__ __device__ inline Plan make_plan(int nact, int npad, int grid, const Tu
     Plan p;
     const int b = nact > 0 ? ilog2_floor(nact) : 0;
     const int mb = tn.mode_b[b < 32 ? b : 31];
-    p.mode = mb >= 0 ? mb : (nact >= tn.mode_cut ? 0 : 1);
+    p.mode = mb >= 0 ? (mb == 0 ? 0 : 1) : (nact >= tn.mode_cut ? 0 : 1);
+    p.late = p.mode == 0 || mb == 2;
     p.itile = p.mode == 0 ? (mixed ? ITILE_A_MIX : ITILE_A_64) : (mixed ? ITILE_B_MIX : ITILE_B_64);
     p.itiles = (nact + p.itile - 1) / p.itile;
     if (p.itiles < 1) p.itiles = 1;
@@ -839,8 +842,8 @@ struct FArgs {
     int grid;
     Tune tn;
     int tail_ok;  // the host's choice of the TAIL kernel instance (the kernels use the template parameter)
-    int defer;    // 1: i-parallel plans leave their j-split partials to k_correct, 2: every plan
-                  // whose tiles are not corrected in the force kernel's tails (see finish_item)
+    int defer;    // 1: plans with Plan::late leave their j-split partials to k_correct, unless
+                  // their tiles are corrected in the force kernel's tails (see finish_item)
 };
 
 // ---------------------------------------------------------------- canonical sums of j-split partials
@@ -1503,8 +1506,9 @@ __device__ void tile_reduce_small(const Dev &d, int nact, int S, int k0, int nva
 // With `defer` an i-parallel plan (mode 0) stops after the partial stores: its
 // tiles hold up to ITILE_A_MIX slots and S partials each, which one CTA would sum
 // as a long chain of L2 round trips, while k_correct sums them spread over the GPU
-// (part_sum, the same canonical order).  With defer = 2 warp-mode plans do the same
-// unless they correct their tiles in the tail.
+// (part_sum, the same canonical order).  A warp-mode plan does the same where the
+// tuning table asks for it (mode 2: chosen by the autotuner where it measured
+// faster), unless it corrects its tiles in the tail.
 template <class P, bool COH>
 __device__ __forceinline__ void finish_item(const Dev &d, int nact, const Plan &pl, int it, bool tail, long long T,
                                             unsigned long long *Tacc, int defer = 0)
@@ -1513,7 +1517,7 @@ __device__ __forceinline__ void finish_item(const Dev &d, int nact, const Plan &
     // the barrier gathers this CTA's partial stores; thread 0's fence releases them
     // before the arrival is counted
     __syncthreads();
-    if ((defer && pl.mode == 0) || (defer == 2 && !tail)) return;
+    if (defer && pl.late && !tail) return;
     if (threadIdx.x == 0) {
         __threadfence();
         const unsigned prev = atomicAdd(&d.tilecnt[it], 1u);
@@ -1847,7 +1851,7 @@ __global__ void __launch_bounds__(CT) k_correct(CArgs ca)
     if (nact <= 0) return;
     const Plan pl = make_plan(nact, d.npad, ca.grid, ca.tn, ca.mixed != 0, d.cap);
     if (ca.tail_ok && pl.mode == 1) return;
-    const int S = (ca.defer && pl.mode == 0) || ca.defer == 2 ? pl.S : 0;
+    const int S = ca.defer && pl.late ? pl.S : 0;
     // only the CTAs that have particles to correct take part (eight per warp); the
     // others leave at once, so a small active set costs a few CTAs, not the grid
     constexpr int PER_CTA = (CT / 32) * 8;

@@ -372,6 +372,29 @@ def test_graph_eager_and_fused_paths_identical(prec, n):
             assert np.array_equal(out[0][k], other[k]), k
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("cluster", [False, True])
+def test_warp_mode_sums_in_force_kernel_or_corrector_identical(prec, cluster):
+    """Warp-mode plans sum their j-split partials either in the force kernel (the
+    last CTA of each tile, tuning mode 1) or in the corrector (mode 2); both take
+    the same canonical order, so a run with either table is bit-identical."""
+    n = 3000
+    m, x, v = inputs.plummer(n, seed=31)
+    if prec == "fp64" and cluster:
+        pytest.skip("the cluster path is mixed precision only")
+    out = []
+    for mode in (1, 2):
+        with gravidy.Integrator(m, x, v, EPS, ETA, precision=prec, cluster=cluster) as g:
+            g.set_tuning(10 ** 9, np.full(32, 12, np.int16), np.full(32, mode, np.int8))
+            assert (g.tuning()[2] == mode).all()
+            g.evolve(0.125)
+            st = g.state()
+            st["stats"] = np.array([g.stats()[k] for k in ("tick", "block_steps", "particle_steps")])
+            out.append(st)
+    for k in out[0]:
+        assert np.array_equal(out[0][k], out[1][k]), k
+
+
 @pytest.mark.parametrize("n", [1000, 4097, 20000])
 def test_cluster_small_steps_vs_full_gpu(n):
     """Small block steps inside one thread-block cluster (the default) against
