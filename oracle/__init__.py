@@ -212,17 +212,18 @@ def quantise(dt_new, dtau_old, tick_now, dt_min, dtau_max):
 
 
 PN_1 = 1     # 1PN terms of the pair
+PN_2 = 2     # 2PN terms of the pair
 PN_25 = 4    # 2.5PN (radiation reaction) terms of the pair
 
 
-def pn_accel(mp, mq, r, v, c, terms=PN_1 | PN_25):
+def pn_accel(mp, mq, r, v, c, terms=PN_1 | PN_2 | PN_25):
     """Post-Newtonian relative acceleration of a pair (r = x_p - x_q, v = v_p - v_q)."""
     a = np.zeros(3)
     _load().or_pn_accel(float(mp), float(mq), _ptr(_f64(r)), _ptr(_f64(v)), float(c), int(terms), _ptr(a))
     return a
 
 
-def pn_jerk(mp, mq, r, v, arel, c, terms=PN_1 | PN_25):
+def pn_jerk(mp, mq, r, v, arel, c, terms=PN_1 | PN_2 | PN_25):
     """Time derivative of pn_accel along the relative motion (dv/dt = arel)."""
     j = np.zeros(3)
     _load().or_pn_jerk(float(mp), float(mq), _ptr(_f64(r)), _ptr(_f64(v)), _ptr(_f64(arel)), float(c), int(terms),
@@ -252,7 +253,7 @@ class Sim:
             self._lib.or_sim_free(h)
             self._h = None
 
-    def set_pn(self, p, q, c, terms=PN_1 | PN_25):
+    def set_pn(self, p, q, c, terms=PN_1 | PN_2 | PN_25):
         """Post-Newtonian terms for the pair (p, q), before the first step."""
         if self._lib.or_sim_set_pn(self._h, int(p), int(q), float(c), int(terms)) != 0:
             raise ValueError("oracle rejected the post-Newtonian pair")

@@ -284,17 +284,26 @@ int64_t or_quantise(double dt_new, int64_t dtau_old, int64_t tick_now, double dt
 /* ------------------------------------------------------------------------ */
 /* Post-Newtonian terms of one pair (Sec. 5: corrections for a binary with  */
 /* eps = 0).  The paper prints no formulas; these are the relative          */
-/* accelerations of the two-body problem in harmonic coordinates at 1PN and */
-/* 2.5PN (radiation reaction) as published by Kidder (1995, Phys. Rev. D    */
-/* 52, 821, Eq. 2.2) and Blanchet (2014, Living Rev. Relativ. 17, 2, with   */
+/* accelerations of the two-body problem in harmonic coordinates at 1PN,   */
+/* 2PN and 2.5PN (radiation reaction) as published by Kidder (1995, Phys.   */
+/* Rev. D 52, 821, Eq. 2.2) and Blanchet (2014, Living Rev. Relativ. 17, 2, */
 /* A and B of its Eq. 219 at those orders).  With r = x_p - x_q,            */
 /* v = v_p - v_q, M = m_p + m_q, eta = m_p m_q / M^2, n = r / |r|,          */
 /* rdot = n.v and c the speed of light in code units (G = 1):               */
 /*   1PN:   M / (c^2 r^2) { [(4 + 2 eta) M/r - (1 + 3 eta) v^2              */
 /*                           + 3/2 eta rdot^2] n + (4 - 2 eta) rdot v }     */
+/*   2PN:   M / (c^4 r^2) { [ -15/8 eta (1 - 3 eta) rdot^4                  */
+/*                            + 3/2 eta (3 - 4 eta) v^2 rdot^2              */
+/*                            - eta (3 - 4 eta) v^4                         */
+/*                            + 1/2 eta (13 - 4 eta) (M/r) v^2              */
+/*                            + (2 + 25 eta + 2 eta^2) (M/r) rdot^2         */
+/*                            - 3/4 (12 + 29 eta) (M/r)^2 ] n               */
+/*              + 1/2 rdot [ eta (15 + 4 eta) v^2                           */
+/*                           - (4 + 41 eta + 8 eta^2) M/r                   */
+/*                           - 3 eta (3 + 2 eta) rdot^2 ] v }               */
 /*   2.5PN: 8/5 eta M^2 / (c^5 r^3) { rdot [18 v^2 + 2/3 M/r - 25 rdot^2] n */
 /*                                    - [6 v^2 - 2 M/r - 15 rdot^2] v }     */
-/* terms: bit 1 selects 1PN, bit 4 selects 2.5PN (2PN is not built).  The   */
+/* terms: bit 1 selects 1PN, bit 2 2PN, bit 4 2.5PN.  The                   */
 /* pair's particles get m_q/M and -m_p/M of the relative term, which keeps  */
 /* the pair's centre of mass at rest at this order.                         */
 /* ------------------------------------------------------------------------ */
@@ -316,6 +325,19 @@ void or_pn_accel(double mp, double mq, const double r[3], const double v[3], dou
         double K = M / (c * c * rr * rr);
         double alpha = (4.0 + 2.0 * eta) * M / rr - (1.0 + 3.0 * eta) * v2 + 1.5 * eta * rd * rd;
         double beta = (4.0 - 2.0 * eta) * rd;
+        for (int k = 0; k < 3; k++)
+            a[k] += K * (alpha * n[k] + beta * v[k]);
+    }
+    if (terms & 2) {
+        double K = M / (pow(c, 4.0) * rr * rr), Mr = M / rr, rd2 = rd * rd;
+        double alpha = -15.0 / 8.0 * eta * (1.0 - 3.0 * eta) * rd2 * rd2
+                       + 1.5 * eta * (3.0 - 4.0 * eta) * v2 * rd2
+                       - eta * (3.0 - 4.0 * eta) * v2 * v2
+                       + 0.5 * eta * (13.0 - 4.0 * eta) * Mr * v2
+                       + (2.0 + 25.0 * eta + 2.0 * eta * eta) * Mr * rd2
+                       - 0.75 * (12.0 + 29.0 * eta) * Mr * Mr;
+        double beta = 0.5 * rd * (eta * (15.0 + 4.0 * eta) * v2 - (4.0 + 41.0 * eta + 8.0 * eta * eta) * Mr
+                                  - 3.0 * eta * (3.0 + 2.0 * eta) * rd2);
         for (int k = 0; k < 3; k++)
             a[k] += K * (alpha * n[k] + beta * v[k]);
     }
@@ -357,6 +379,24 @@ void or_pn_jerk(double mp, double mq, const double r[3], const double v[3], cons
         double beta = (4.0 - 2.0 * eta) * rd;
         double dalpha = -(4.0 + 2.0 * eta) * M * rd / (rr * rr) - (1.0 + 3.0 * eta) * dv2 + 3.0 * eta * rd * drd;
         double dbeta = (4.0 - 2.0 * eta) * drd;
+        double i2 = 1.0 / (rr * rr), di2 = -2.0 * rd / (rr * rr * rr);
+        for (int k = 0; k < 3; k++)
+            j[k] += K * (di2 * (alpha * n[k] + beta * v[k]) +
+                         i2 * (dalpha * n[k] + alpha * dn[k] + dbeta * v[k] + beta * arel[k]));
+    }
+    if (terms & 2) {
+        double K = M / pow(c, 4.0);
+        double Mr = M / rr, dMr = -M * rd / (rr * rr), rd2 = rd * rd, drd2 = 2.0 * rd * drd;
+        double e1 = -15.0 / 8.0 * eta * (1.0 - 3.0 * eta), e2 = 1.5 * eta * (3.0 - 4.0 * eta);
+        double e3 = -eta * (3.0 - 4.0 * eta), e4 = 0.5 * eta * (13.0 - 4.0 * eta);
+        double e5 = 2.0 + 25.0 * eta + 2.0 * eta * eta, e6 = -0.75 * (12.0 + 29.0 * eta);
+        double alpha = e1 * rd2 * rd2 + e2 * v2 * rd2 + e3 * v2 * v2 + e4 * Mr * v2 + e5 * Mr * rd2 + e6 * Mr * Mr;
+        double dalpha = e1 * 2.0 * rd2 * drd2 + e2 * (dv2 * rd2 + v2 * drd2) + e3 * 2.0 * v2 * dv2
+                        + e4 * (dMr * v2 + Mr * dv2) + e5 * (dMr * rd2 + Mr * drd2) + e6 * 2.0 * Mr * dMr;
+        double f1 = eta * (15.0 + 4.0 * eta), f2 = -(4.0 + 41.0 * eta + 8.0 * eta * eta);
+        double f3 = -3.0 * eta * (3.0 + 2.0 * eta);
+        double Q = f1 * v2 + f2 * Mr + f3 * rd2, dQ = f1 * dv2 + f2 * dMr + f3 * drd2;
+        double beta = 0.5 * rd * Q, dbeta = 0.5 * (drd * Q + rd * dQ);
         double i2 = 1.0 / (rr * rr), di2 = -2.0 * rd / (rr * rr * rr);
         for (int k = 0; k < 3; k++)
             j[k] += K * (di2 * (alpha * n[k] + beta * v[k]) +
@@ -488,7 +528,7 @@ static void add_pn(const or_sim *s, int64_t i, const double *x, const double *v,
  * or -1 for a bad argument or a call after the first step. */
 int or_sim_set_pn(or_sim *s, int32_t p, int32_t q, double c, int terms)
 {
-    if (p < 0 || q < 0 || p >= s->n || q >= s->n || p == q || !(c > 0) || (terms & ~5) || s->nblock > 0)
+    if (p < 0 || q < 0 || p >= s->n || q >= s->n || p == q || !(c > 0) || (terms & ~7) || s->nblock > 0)
         return -1;
     s->pn_p = p;
     s->pn_q = q;

@@ -6,6 +6,14 @@ coordinates) against facts they must reproduce, not against a retyped formula:
   (Richardson-extrapolated central differences of the acceleration itself);
 - 1PN: an eccentric binary's periastron advances by 6 pi M / (c^2 a (1 - e^2))
   per orbit (Einstein; e.g. Robertson 1938, Damour & Deruelle 1985);
+- 2PN: a circular orbit's frequency follows the harmonic-coordinate relation
+  omega^2 = (M / r^3) [1 + (-3 + eta) g + (6 + 41/4 eta + eta^2) g^2], g = M / (c^2 r),
+  up to terms of order g^3 (residual halving g shrinks 8-fold), which checks the
+  terms without rdot; and the 1PN + 2PN equations of motion conserve the 2PN
+  two-body energy (the expression in harmonic coordinates, e.g. Blanchet 2014,
+  Living Rev. Relativ. 17, 2) up to terms of the next order: its rate of change at
+  any phase-space point shrinks as c^-6, where a wrong coefficient of any 2PN term,
+  or of the energy, leaves a c^-4 rate;
 - 2.5PN: the orbit-averaged decay of the semi-major axis and eccentricity
   follows Peters (1964): da/dt = -64/5 eta M^3 / (c^5 a^3 (1 - e^2)^(7/2))
   (1 + 73/24 e^2 + 37/96 e^4), de/dt = -304/15 eta M^3 e / (c^5 a^4
@@ -37,7 +45,7 @@ def _binary(a, e):
     return np.array([M1, M2]), x, vv
 
 
-@pytest.mark.parametrize("terms", [oracle.PN_1, oracle.PN_25, oracle.PN_1 | oracle.PN_25])
+@pytest.mark.parametrize("terms", [oracle.PN_1, oracle.PN_2, oracle.PN_25, oracle.PN_1 | oracle.PN_2 | oracle.PN_25])
 def test_pn_jerk_is_the_derivative_of_the_acceleration(terms):
     rng = np.random.default_rng(terms)
     for _ in range(5):
@@ -147,6 +155,81 @@ def test_25pn_orbit_decay_follows_peters():
     assert np.abs(ps).max() < 1e-13
 
 
+def _circular_residual(m1, m2, g):
+    """Relative radial residual of the Newtonian + 1PN + 2PN acceleration on a circular
+    orbit whose frequency comes from the 2PN frequency-separation relation (c = 1)."""
+    M = m1 + m2
+    eta = m1 * m2 / M ** 2
+    r = M / g
+    w2 = M / r ** 3 * (1 + (-3 + eta) * g + (6 + 41 / 4 * eta + eta ** 2) * g * g)
+    rv = np.array([r, 0.0, 0.0])
+    vv = np.array([0.0, np.sqrt(w2) * r, 0.0])
+    a = -M * rv / r ** 3 + oracle.pn_accel(m1, m2, rv, vv, 1.0, oracle.PN_1 | oracle.PN_2)
+    assert a[1] == 0.0 and a[2] == 0.0  # rdot = 0: no term along v
+    return (a[0] + w2 * r) / (w2 * r)
+
+
+@pytest.mark.parametrize("masses", [(0.5, 0.5), (0.9, 0.1), (0.99, 0.01)])
+def test_2pn_circular_orbit_frequency(masses):
+    r1 = _circular_residual(*masses, 2e-3)
+    r2 = _circular_residual(*masses, 1e-3)
+    print("2PN circular orbit residual: g = 2e-3 %.3e, g = 1e-3 %.3e, ratio %.3f" % (r1, r2, r1 / r2))
+    # the leftover is the third order: 8x smaller for half the g (a wrong 2PN
+    # coefficient would leave a g^2 term: 4x)
+    assert 7.5 < r1 / r2 < 8.5
+    assert abs(r2) < 1e-7
+
+
+def _energy_rate(m1, m2, r, v, c, order, terms):
+    """d/dt of the two-body energy per reduced mass in harmonic coordinates (through
+    1PN or 2PN: v^2/2 - M/r, then 3/8 (1 - 3 eta) v^4 + 1/2 (3 + eta) (M/r) v^2 +
+    1/2 eta (M/r) rdot^2 + 1/2 (M/r)^2 over c^2, then the 2PN polynomial below over
+    c^4), along the motion r' = v, v' = Newtonian + the oracle's pair terms `terms`,
+    by the chain rule through v^2, M/r and rdot."""
+    M = m1 + m2
+    n = m1 * m2 / M ** 2
+    rr = np.linalg.norm(r)
+    a = -M * r / rr ** 3 + oracle.pn_accel(m1, m2, r, v, c, terms)
+    v2 = v @ v
+    rd = r @ v / rr
+    Mr = M / rr
+    dv2, dMr, drd = 2 * v @ a, -M * rd / rr ** 2, (v2 - rd * rd) / rr + r @ a / rr
+    Ev2 = 0.5 + (3 / 4 * (1 - 3 * n) * v2 + 0.5 * (3 + n) * Mr) / c ** 2
+    EMr = -1.0 + (0.5 * (3 + n) * v2 + 0.5 * n * rd ** 2 + Mr) / c ** 2
+    Erd = n * Mr * rd / c ** 2
+    if order >= 2:
+        # E2 = 5/16 (1 - 7n + 13n^2) v^6 + 1/8 (21 - 23n - 27n^2) (M/r) v^4
+        #      + 1/4 n (1 - 15n) (M/r) v^2 rdot^2 - 3/8 n (1 - 3n) (M/r) rdot^4
+        #      + 1/8 (14 - 55n + 4n^2) (M/r)^2 v^2 + 1/8 (4 + 69n + 12n^2) (M/r)^2 rdot^2
+        #      - 1/4 (2 + 15n) (M/r)^3
+        Ev2 += (15 / 16 * (1 - 7 * n + 13 * n * n) * v2 ** 2 + 1 / 4 * (21 - 23 * n - 27 * n * n) * Mr * v2
+                + 1 / 4 * n * (1 - 15 * n) * Mr * rd ** 2 + 1 / 8 * (14 - 55 * n + 4 * n * n) * Mr ** 2) / c ** 4
+        EMr += (1 / 8 * (21 - 23 * n - 27 * n * n) * v2 ** 2 + 1 / 4 * n * (1 - 15 * n) * v2 * rd ** 2
+                - 3 / 8 * n * (1 - 3 * n) * rd ** 4 + 1 / 4 * (14 - 55 * n + 4 * n * n) * Mr * v2
+                + 1 / 4 * (4 + 69 * n + 12 * n * n) * Mr * rd ** 2 - 3 / 4 * (2 + 15 * n) * Mr ** 2) / c ** 4
+        Erd += (1 / 2 * n * (1 - 15 * n) * Mr * v2 * rd - 3 / 2 * n * (1 - 3 * n) * Mr * rd ** 3
+                + 1 / 4 * (4 + 69 * n + 12 * n * n) * Mr ** 2 * rd) / c ** 4
+    return Ev2 * dv2 + EMr * dMr + Erd * drd
+
+
+def test_2pn_motion_conserves_the_2pn_energy():
+    """At random phase-space points and mass ratios the 1PN + 2PN equations of motion
+    change the 2PN energy only at the next order: the rate shrinks 64-fold when c
+    doubles (c^-6), where the 1PN motion changes the 1PN energy 16-fold (c^-4).  A
+    wrong coefficient in any 2PN term of the acceleration (or of the energy) leaves a
+    c^-4 rate."""
+    rng = np.random.default_rng(11)
+    for _ in range(8):
+        m1, m2 = rng.uniform(0.02, 1.0, size=2)
+        r = rng.normal(size=3)
+        v = rng.normal(size=3) * 0.8
+        d2 = [_energy_rate(m1, m2, r, v, c, 2, oracle.PN_1 | oracle.PN_2) for c in (100.0, 200.0)]
+        d1 = [_energy_rate(m1, m2, r, v, c, 1, oracle.PN_1) for c in (100.0, 200.0)]
+        print("energy rates: 2PN %.3e -> %.3e (x%.2f), 1PN x%.4f" % (d2[0], d2[1], d2[0] / d2[1], d1[0] / d1[1]))
+        assert 60 < d2[0] / d2[1] < 68
+        assert abs(d1[0] / d1[1] - 16) < 1e-3
+
+
 def test_pn_pair_rejects_bad_arguments():
     m, x, v = _binary(1.0, 0.1)
     sim = oracle.Sim(m, x, v, 0.0, 0.01)
@@ -155,7 +238,7 @@ def test_pn_pair_rejects_bad_arguments():
     with pytest.raises(ValueError):
         sim.set_pn(0, 1, -1.0)
     with pytest.raises(ValueError):
-        sim.set_pn(0, 1, 10.0, terms=2)  # 2PN is not built
+        sim.set_pn(0, 1, 10.0, terms=8)  # no such term
     sim.set_pn(0, 1, 10.0)
     sim.step()
     with pytest.raises(ValueError):
