@@ -60,6 +60,9 @@ TRAFFIC_PER_LAUNCH = {
     # asynchronous double-buffered j-tiles in the force kernel, per-bucket choice of
     # where warp-mode j-split sums are taken
     "2d1d3ec0": {"k_cluster_steps": 1582080, "k_force_mixed": 716288},
+    # 2d1d3ec0 plus the 2PN pair terms, which only the corrector and the force hooks
+    # contain: the two captured kernels' code is unchanged
+    "ddb7dccc": {"k_cluster_steps": 1582080, "k_force_mixed": 716288},
 }
 
 

@@ -97,18 +97,19 @@ typedef struct gd_opts {
                            and block quantisation, in every path (three kernels, small-step
                            cluster, fused kernel, ensembles) and both precisions */
     int32_t pn_terms;   /* post-Newtonian terms of one pair (Sec. 5: corrections for a binary):
-                           0 (default) none; GD_PN_1 the 1PN and/or GD_PN_25 the 2.5PN (radiation
-                           reaction) relative acceleration of the two-body problem in harmonic
-                           coordinates (Kidder 1995; Blanchet 2014), added with its time derivative
-                           to the force and jerk of particles pn_p (share m_q/M) and pn_q (share
-                           -m_p/M) whenever they are active; 2PN terms are not built.  gd_init only
-                           (not ensembles); the small-step cluster is not used with them */
+                           0 (default) none; a combination of GD_PN_1, GD_PN_2 and GD_PN_25: the
+                           1PN, 2PN and 2.5PN (radiation reaction) relative accelerations of the
+                           two-body problem in harmonic coordinates (Kidder 1995; Blanchet 2014),
+                           added with their time derivative to the force and jerk of particles
+                           pn_p (share m_q/M) and pn_q (share -m_p/M) whenever they are active.
+                           gd_init only (not ensembles); the small-step cluster is not used with
+                           them */
     int32_t pn_p, pn_q; /* the pair, distinct indices in [0, n) */
     double pn_c;        /* speed of light in the caller's units (G = 1), > 0 */
 } gd_opts;
 
 enum { GD_CORR_HERMITE = 0, GD_CORR_TIMESYM = 1 };
-enum { GD_PN_1 = 1, GD_PN_25 = 4 };
+enum { GD_PN_1 = 1, GD_PN_2 = 2, GD_PN_25 = 4 };
 
 typedef struct gd_stats {
     int64_t tick;          /* time of the last block step, in ticks */

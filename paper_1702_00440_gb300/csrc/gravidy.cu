@@ -744,8 +744,8 @@ int ctx_init(gd_ctx **out, int64_t n, const double *m, const double *x, const do
     if (o.corrector != GD_CORR_HERMITE && o.corrector != GD_CORR_TIMESYM)
         return fail(nullptr, GD_EINVAL, "corrector must be GD_CORR_HERMITE or GD_CORR_TIMESYM");
     if (o.pn_terms != 0) {
-        if (o.pn_terms & ~(GD_PN_1 | GD_PN_25))
-            return fail(nullptr, GD_EINVAL, "pn_terms must combine GD_PN_1 and GD_PN_25 (2PN is not built)");
+        if (o.pn_terms & ~(GD_PN_1 | GD_PN_2 | GD_PN_25))
+            return fail(nullptr, GD_EINVAL, "pn_terms must combine GD_PN_1, GD_PN_2 and GD_PN_25");
         if (o.pn_p < 0 || o.pn_q < 0 || o.pn_p >= n || o.pn_q >= n || o.pn_p == o.pn_q)
             return fail(nullptr, GD_EINVAL, "pn_p and pn_q must be distinct indices in [0, n)");
         if (!(o.pn_c > 0) || !std::isfinite(o.pn_c)) return fail(nullptr, GD_EINVAL, "pn_c must be finite and > 0");

@@ -916,11 +916,16 @@ __device__ __forceinline__ P part_sum(const Dev &d, int nact, int S, int c, int 
 
 // ---------------------------------------------------------------- post-Newtonian pair terms
 //
-// Sec. 5's corrections for a binary: the 1PN and 2.5PN relative accelerations of the
-// two-body problem in harmonic coordinates (Kidder 1995, Eq. 2.2; Blanchet 2014,
+// Sec. 5's corrections for a binary: the 1PN, 2PN and 2.5PN relative accelerations of
+// the two-body problem in harmonic coordinates (Kidder 1995, Eq. 2.2; Blanchet 2014,
 // Eq. 219), with r = x_p - x_q, v = v_p - v_q, M = m_p + m_q, eta = m_p m_q / M^2,
 // n = r / |r|, rdot = n.v:
 //   1PN:   M / (c^2 r^2) {[(4 + 2 eta) M/r - (1 + 3 eta) v^2 + 3/2 eta rdot^2] n + (4 - 2 eta) rdot v}
+//   2PN:   M / (c^4 r^2) {[-15/8 eta (1 - 3 eta) rdot^4 + 3/2 eta (3 - 4 eta) v^2 rdot^2
+//                          - eta (3 - 4 eta) v^4 + 1/2 eta (13 - 4 eta) (M/r) v^2
+//                          + (2 + 25 eta + 2 eta^2) (M/r) rdot^2 - 3/4 (12 + 29 eta) (M/r)^2] n
+//                         + 1/2 rdot [eta (15 + 4 eta) v^2 - (4 + 41 eta + 8 eta^2) M/r
+//                                     - 3 eta (3 + 2 eta) rdot^2] v}
 //   2.5PN: 8/5 eta M^2 / (c^5 r^3) {rdot [18 v^2 + 2/3 M/r - 25 rdot^2] n - [6 v^2 - 2 M/r - 15 rdot^2] v}
 // and their time derivative for the jerk, taken by carrying every quantity as a dual
 // number (value, d/dt) along r' = v, v' = -M r / |r|^3 (the pair's Newtonian relative
@@ -973,6 +978,25 @@ __device__ void pn_pair_terms(int terms, T mp, T mq, T c, const T r[3], const T 
                                    dscale(T(1.5) * eta, dmul(rd, rd)));
         const Dual<T> beta = dscale(T(4) - T(2) * eta, rd);
         const Dual<T> K = dscale(M / (c * c), dmul(ir, ir));
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            acc[k] = dadd(acc[k], dmul(K, dadd(dmul(alpha, dmul(R[k], ir)), dmul(beta, V[k]))));
+    }
+    if (terms & 2) {
+        const Dual<T> rd2 = dmul(rd, rd), v4 = dmul(v2, v2), rd4 = dmul(rd2, rd2);
+        const T e2 = eta * eta;
+        Dual<T> alpha = dscale(T(-15) / T(8) * eta * (T(1) - T(3) * eta), rd4);
+        alpha = dadd(alpha, dscale(T(1.5) * eta * (T(3) - T(4) * eta), dmul(v2, rd2)));
+        alpha = dsub(alpha, dscale(eta * (T(3) - T(4) * eta), v4));
+        alpha = dadd(alpha, dscale(T(0.5) * eta * (T(13) - T(4) * eta), dmul(Mr, v2)));
+        alpha = dadd(alpha, dscale(T(2) + T(25) * eta + T(2) * e2, dmul(Mr, rd2)));
+        alpha = dsub(alpha, dscale(T(0.75) * (T(12) + T(29) * eta), dmul(Mr, Mr)));
+        Dual<T> Q = dscale(eta * (T(15) + T(4) * eta), v2);
+        Q = dsub(Q, dscale(T(4) + T(41) * eta + T(8) * e2, Mr));
+        Q = dsub(Q, dscale(T(3) * eta * (T(3) + T(2) * eta), rd2));
+        const Dual<T> beta = dscale(T(0.5), dmul(rd, Q));
+        const T c2 = c * c;
+        const Dual<T> K = dscale(M / (c2 * c2), dmul(ir, ir));
 #pragma unroll
         for (int k = 0; k < 3; k++)
             acc[k] = dadd(acc[k], dmul(K, dadd(dmul(alpha, dmul(R[k], ir)), dmul(beta, V[k]))));

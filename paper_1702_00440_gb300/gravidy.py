@@ -21,7 +21,7 @@ from . import build as _build
 GD_OK, GD_EINVAL, GD_ENOMEM, GD_ECUDA, GD_ENONFINITE, GD_ETIMEOUT, GD_ESTATE = 0, -1, -2, -3, -4, -5, -6
 GD_FP64, GD_MIXED = 0, 1
 GD_CORR_HERMITE, GD_CORR_TIMESYM = 0, 1
-GD_PN_1, GD_PN_25 = 1, 4
+GD_PN_1, GD_PN_2, GD_PN_25 = 1, 2, 4
 _PRECISION = {"fp64": GD_FP64, "mixed": GD_MIXED, GD_FP64: GD_FP64, GD_MIXED: GD_MIXED}
 
 # every entry point the header declares

@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 EPS, ETA = 1e-4, 0.01
 DT_MIN = 2.0 ** -22
 U24 = 2.0 ** -24
-PN_ALL = gravidy.GD_PN_1 | gravidy.GD_PN_25
+PN_ALL = gravidy.GD_PN_1 | gravidy.GD_PN_2 | gravidy.GD_PN_25
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -46,7 +46,7 @@ def _pn_share(m, x, v, p, q, c, terms, i):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("terms", [gravidy.GD_PN_1, gravidy.GD_PN_25, PN_ALL])
+@pytest.mark.parametrize("terms", [gravidy.GD_PN_1, gravidy.GD_PN_2, gravidy.GD_PN_25, PN_ALL])
 def test_pn_force_hook_matches_the_oracle(prec, terms):
     m, x, v = _cluster_with_binary()
     c = 30.0
@@ -105,11 +105,13 @@ def test_pn_replayed_schedule_matches_the_oracle(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_pn_periastron_advance_under_block_steps(prec):
+@pytest.mark.parametrize("terms", [gravidy.GD_PN_1, gravidy.GD_PN_1 | gravidy.GD_PN_2])
+def test_pn_periastron_advance_under_block_steps(prec, terms):
     """An isolated eccentric binary (eps = 0) integrated by gd_evolve with the
-    1PN terms: its periastron advances by 6 pi M / (c^2 a (1 - e^2)) per orbit,
-    to within 1 % at M / (c^2 a) = 1.1e-3 (the formula's own next order), as the
-    oracle's free run with the same block steps does."""
+    1PN (and 2PN) terms: its periastron advances by 6 pi M / (c^2 a (1 - e^2)) per
+    orbit, to within 1 % at M / (c^2 a) = 1.1e-3 (the formula's own next order,
+    where the 2PN terms act), as the oracle's free run with the same block steps
+    and terms does."""
     a, e, c = 1.0, 0.5, 30.0
     m, x, v = _binary(0.6, 0.4, a, e)
     M = m.sum()
@@ -131,20 +133,20 @@ def test_pn_periastron_advance_under_block_steps(prec):
 
     # sample both runs at the same times: every dt_max (all particles synchronised)
     t_samples = np.arange(1, int(6 * period / dt_max)) * dt_max
-    with gravidy.Integrator(m, x, v, 0.0, ETA, precision=prec, dt_max=dt_max, pn=(0, 1, c, gravidy.GD_PN_1)) as g:
+    with gravidy.Integrator(m, x, v, 0.0, ETA, precision=prec, dt_max=dt_max, pn=(0, 1, c, terms)) as g:
         gs = []
         for t in t_samples:
             g.evolve(t)
             gs.append(g.state()["x"])
     sim = oracle.Sim(m, x, v, 0.0, ETA, dt_max=dt_max)
-    sim.set_pn(0, 1, c, oracle.PN_1)
+    sim.set_pn(0, 1, c, terms)
     os_ = []
     for t in t_samples:
         sim.evolve(t)
         os_.append(sim.state()["x"])
     want = 6 * np.pi * M / (c * c * a * (1 - e * e))
     got_g, got_o = advance(gs), advance(os_)
-    print("%s pn periastron advance per orbit: gpu %.5e oracle %.5e formula %.5e" % (prec, got_g, got_o, want))
+    print("%s pn %d periastron advance per orbit: gpu %.5e oracle %.5e formula %.5e" % (prec, terms, got_g, got_o, want))
     assert abs(got_o / want - 1) < 0.01
     assert abs(got_g / want - 1) < 0.01
     assert abs(got_g / got_o - 1) < (1e-6 if prec == "fp64" else 2e-3)
