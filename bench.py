@@ -61,7 +61,9 @@ TRAFFIC_PER_LAUNCH = {
     # where warp-mode j-split sums are taken
     "2d1d3ec0": {"k_cluster_steps": 1582080, "k_force_mixed": 716288},
     # 2d1d3ec0 plus the 2PN pair terms, which only the corrector and the force hooks
-    # contain: the two captured kernels' code is unchanged
+    # contain, and the P(EC)^n trial passes of the corrector (a branch the captured
+    # force kernel compiles out): the two captured kernels' memory accesses are unchanged
+    "fe3ba5e9": {"k_cluster_steps": 1582080, "k_force_mixed": 716288},
     "ddb7dccc": {"k_cluster_steps": 1582080, "k_force_mixed": 716288},
 }
 

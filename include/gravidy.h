@@ -106,6 +106,14 @@ typedef struct gd_opts {
                            them */
     int32_t pn_p, pn_q; /* the pair, distinct indices in [0, n) */
     double pn_c;        /* speed of light in the caller's units (G = 1), > 0 */
+    int32_t n_iter;     /* evaluation-correction passes per block step, 1 (default) to 16: with
+                           n_iter > 1 (P(EC)^n, Kokubo, Yoshinaga & Makino 1998; needs the
+                           time-symmetric corrector) every pass but the last evaluates the
+                           active particles' force and jerk and writes their corrected position
+                           and velocity over their predicted ones, which the next pass evaluates
+                           against; the last pass corrects as usual.  Each pass counts its
+                           N_act * N interactions.  Runs the three-kernel step (not the small-step
+                           cluster, the fused kernel or ensembles; no post-Newtonian pair) */
 } gd_opts;
 
 enum { GD_CORR_HERMITE = 0, GD_CORR_TIMESYM = 1 };

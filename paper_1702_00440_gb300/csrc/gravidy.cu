@@ -248,16 +248,37 @@ void launch_select(gd_ctx *c, int slot)
 
 // The force of a block step: warp-mode tiles are corrected in the force kernel's
 // tile tails, which then finalizes the step; k_correct handles i-parallel plans.
-void launch_force_step(gd_ctx *c) { launch_force_with(c, fargs(c, c->opt.tail_correct ? 1 : 0, DEFER_SUMS)); }
+// Tail correction only with one pass per step (a pass before the last corrects in
+// k_correct without committing).
+bool tail_ok(const gd_ctx *c) { return c->opt.tail_correct && c->opt.n_iter <= 1; }
 
-void launch_correct(gd_ctx *c)
+void launch_force_step(gd_ctx *c) { launch_force_with(c, fargs(c, tail_ok(c) ? 1 : 0, DEFER_SUMS)); }
+
+void launch_correct(gd_ctx *c, int commit = 1)
 {
     c->launches += 1;
-    const CArgs a{c->d, c->grid_force, effective_tune(c), c->opt.tail_correct ? 1 : 0, c->mixed ? 1 : 0, DEFER_SUMS};
+    const CArgs a{c->d, c->grid_force, effective_tune(c), tail_ok(c) ? 1 : 0, c->mixed ? 1 : 0, DEFER_SUMS, commit};
     if (c->mixed)
         launch_pdl(c->opt.pdl != 0, k_correct<true>, c->grid_corr, CT, c->stream, a);
     else
         launch_pdl(c->opt.pdl != 0, k_correct<false>, c->grid_corr, CT, c->stream, a);
+}
+
+// The evaluation and correction of a selected block step: with n_iter > 1 passes
+// (P(EC)^n), each pass but the last evaluates the active particles' forces and
+// writes their corrected positions and velocities over their predicted records,
+// which the next pass evaluates against; the last pass commits.  The events (when
+// given) bracket the last force launch.
+void launch_passes(gd_ctx *c, cudaEvent_t e0, cudaEvent_t e1, bool capturing)
+{
+    for (int p = 1; p < c->opt.n_iter; p++) {
+        launch_force_step(c);
+        launch_correct(c, 0);
+    }
+    if (e0) cudaEventRecordWithFlags(e0, c->stream, capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+    launch_force_step(c);
+    if (e1) cudaEventRecordWithFlags(e1, c->stream, capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+    launch_correct(c);
 }
 
 // One free-running block step: select+predict, force (+ correction of small
@@ -265,10 +286,7 @@ void launch_correct(gd_ctx *c)
 void launch_step(gd_ctx *c, int slot, cudaEvent_t e0, cudaEvent_t e1, bool capturing)
 {
     launch_select(c, slot);
-    if (e0) cudaEventRecordWithFlags(e0, c->stream, capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
-    launch_force_step(c);
-    if (e1) cudaEventRecordWithFlags(e1, c->stream, capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
-    launch_correct(c);
+    launch_passes(c, e0, e1, capturing);
 }
 
 // Small block steps inside one cluster (cluster.cuh), up to CL_STEPS per launch.
@@ -307,10 +325,7 @@ void launch_cycle(gd_ctx *c, int slot, cudaEvent_t e0, cudaEvent_t e1, bool capt
         if (c->opt.time_force) cudaEventRecordWithFlags(c->ev[CL_EV + 2 * slot], c->stream, fl);
         launch_cluster(c, 1, slot);
         if (c->opt.time_force) cudaEventRecordWithFlags(c->ev[CL_EV + 2 * slot + 1], c->stream, fl);
-        if (e0) cudaEventRecordWithFlags(e0, c->stream, fl);
-        launch_force_step(c);
-        if (e1) cudaEventRecordWithFlags(e1, c->stream, fl);
-        launch_correct(c);
+        launch_passes(c, e0, e1, capturing);
         return;
     }
     launch_step(c, slot, e0, e1, capturing);
@@ -322,7 +337,7 @@ void launch_cycle(gd_ctx *c, int slot, cudaEvent_t e0, cudaEvent_t e1, bool capt
 void cluster_setup(gd_ctx *c)
 {
     c->cl_C = 0;
-    if (!c->mixed || !c->opt.cluster || c->d.pn_terms) return;
+    if (!c->mixed || !c->opt.cluster || c->d.pn_terms || c->opt.n_iter > 1) return;
     const void *fn = c->soft ? (const void *)k_cluster_steps<true> : (const void *)k_cluster_steps<false>;
     int maxdyn = 0;
     cudaDeviceGetAttribute(&maxdyn, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev);
@@ -713,6 +728,7 @@ void gd_opts_default(gd_opts *o)
     o->tail_correct = 0;
     o->cluster = 1;
     o->corrector = GD_CORR_HERMITE;
+    o->n_iter = 1;
     o->pn_terms = 0;
     o->pn_p = 0;
     o->pn_q = 1;
@@ -743,6 +759,13 @@ int ctx_init(gd_ctx **out, int64_t n, const double *m, const double *x, const do
     if (o.precision != GD_FP64 && o.precision != GD_MIXED) return fail(nullptr, GD_EINVAL, "bad precision");
     if (o.corrector != GD_CORR_HERMITE && o.corrector != GD_CORR_TIMESYM)
         return fail(nullptr, GD_EINVAL, "corrector must be GD_CORR_HERMITE or GD_CORR_TIMESYM");
+    if (o.n_iter < 1 || o.n_iter > 16) return fail(nullptr, GD_EINVAL, "n_iter must be in [1, 16]");
+    if (o.n_iter > 1) {
+        if (o.corrector != GD_CORR_TIMESYM)
+            return fail(nullptr, GD_EINVAL, "n_iter > 1 needs the time-symmetric corrector");
+        if (o.pn_terms) return fail(nullptr, GD_EINVAL, "n_iter > 1 takes no post-Newtonian pair");
+        if (o.fused) return fail(nullptr, GD_EINVAL, "n_iter > 1 runs the three-kernel step, not the fused one");
+    }
     if (o.pn_terms != 0) {
         if (o.pn_terms & ~(GD_PN_1 | GD_PN_2 | GD_PN_25))
             return fail(nullptr, GD_EINVAL, "pn_terms must combine GD_PN_1, GD_PN_2 and GD_PN_25");
@@ -829,6 +852,7 @@ int ctx_init(gd_ctx **out, int64_t n, const double *m, const double *x, const do
     d.inv_dt_min_f = (float)(1.0 / o.dt_min);
     d.eta_f = (float)eta;
     d.tsym = o.corrector == GD_CORR_TIMESYM ? 1 : 0;
+    d.n_iter = o.n_iter;
     d.pn_terms = o.pn_terms;
     d.pn_p = o.pn_p;
     d.pn_q = o.pn_q;
@@ -1425,8 +1449,7 @@ int gd_replay_step(gd_ctx *c, int64_t tick_next, const int32_t *idx, int64_t nac
     CK(cudaMemcpyAsync(d.act, stage_i64(c, 0), sizeof(int) * nact, cudaMemcpyHostToDevice, c->stream));
     launch_predict_all(c, tick_next, c->mixed);
     k_set_step<<<1, 1, 0, c->stream>>>(d.ctrl, tick_next, (int)nact);
-    launch_force_step(c);
-    launch_correct(c);
+    launch_passes(c, nullptr, nullptr, false);
     k_resync<<<1, 1024, 0, c->stream>>>(d);
     c->launches += 2;
     CK(cudaGetLastError());
@@ -1546,6 +1569,7 @@ int gd_ens_init(gd_ens **out, int32_t nclusters, const int64_t *n_per, const dou
     if (opt) o = *opt;
     if (o.precision != GD_MIXED) return ens_fail(nullptr, GD_EINVAL, "ensembles run in GD_MIXED precision");
     if (o.pn_terms != 0) return ens_fail(nullptr, GD_EINVAL, "ensembles take no post-Newtonian pair");
+    if (o.n_iter != 1) return ens_fail(nullptr, GD_EINVAL, "ensembles take one pass per block step");
     // padded layout
     std::vector<int> cs(nclusters), cnp(nclusters), cn(nclusters);
     long long total = 0, nreal = 0;

@@ -108,6 +108,7 @@ struct Dev {
     float eps2f;
     float dt_min_f, inv_dt_min_f, eta_f;  // FP32 copies (dt_min is a power of two: exact)
     int tsym;                 // corrector: 0 the Hermite scheme's, 1 the time-symmetric form
+    int n_iter;               // evaluation-correction passes per block step (P(EC)^n; 1 = PEC)
     int pn_terms;             // post-Newtonian terms of the pair (pn_p, pn_q): 0 none, bit 1 1PN, bit 4 2.5PN
     int pn_p, pn_q;
     double pn_c;              // speed of light in code units
@@ -1299,7 +1300,7 @@ __device__ __forceinline__ void ds_correct(const Dev &d, bool real, long long dt
 // (part_sum, over nact slots); S = 0: it is read from fsum.
 template <bool COH>
 __device__ __forceinline__ void correct_slots_ds(const Dev &d, long long T, int k_lo, int k_hi, int w0, int ws,
-                                                 long long &mymin, int &bad, int S, int nact)
+                                                 long long &mymin, int &bad, int S, int nact, bool trial = false)
 {
     const int n = d.n;
     const int lane = threadIdx.x & 31;
@@ -1325,6 +1326,22 @@ __device__ __forceinline__ void correct_slots_ds(const Dev &d, long long T, int 
         long long dtau;
         ds_correct(d, real, behind ? dtick : 1, dtau_old, T, x0, v0, a0, j0, a1, j1, x1, v1, dtau);
         const bool fin = isfinite(x1.h) && isfinite(v1.h) && isfinite(a1) && isfinite(j1);
+        if (trial) {
+            // a pass before the last (P(EC)^n): the corrected position and velocity
+            // replace the particle's predicted j-record; the state stays
+            if (valid && behind && real) {
+                if (!fin) bad |= 1;
+                ((float *)&d.jA[i])[c] = x1.h;
+                ((float *)&d.jB[i])[c] = x1.l;
+                const float vr = __fadd_rn(v1.h, v1.l);
+                if (c == 0)
+                    d.jB[i].w = vr;
+                else
+                    ((float *)&d.jC[i])[c - 1] = vr;
+            }
+            if (valid && !behind) bad |= 2;
+            continue;
+        }
         if (valid) {
             if (!behind) {
                 bad |= 2;
@@ -1357,7 +1374,7 @@ __device__ __forceinline__ void correct_slots_ds(const Dev &d, long long T, int 
 // (1 non-finite, 2 a particle not behind T, which is left untouched).
 template <bool COH>
 __device__ __forceinline__ void correct_slots64(const Dev &d, long long T, int k_lo, int k_hi, int w0, int ws,
-                                                long long &mymin, int &bad, int S, int nact)
+                                                long long &mymin, int &bad, int S, int nact, bool trial = false)
 {
     const int n = d.n;
     const int lane = threadIdx.x & 31;
@@ -1424,6 +1441,16 @@ __device__ __forceinline__ void correct_slots64(const Dev &d, long long T, int k
         const double den = sJC + sB;
         const long long dtau = next_block_step(d, num, den, dtau_old, T);
         const bool fin = isfinite(x1) && isfinite(v1) && isfinite(a1) && isfinite(j1);
+        if (trial) {
+            // a pass before the last (P(EC)^n): corrected x, v into the predicted record
+            if (valid && behind && real) {
+                if (!fin) bad |= 1;
+                d.pd[c * d.npad + i] = x1;
+                d.pd[(3 + c) * d.npad + i] = v1;
+            }
+            if (valid && !behind) bad |= 2;
+            continue;
+        }
         if (valid) {
             if (!behind) {
                 bad |= 2;
@@ -1449,12 +1476,13 @@ __device__ __forceinline__ void correct_slots64(const Dev &d, long long T, int k
 
 template <bool MIXED, bool COH>
 __device__ __forceinline__ void correct_slots(const Dev &d, long long T, int k_lo, int k_hi, int w0, int ws,
-                                              long long &mymin, int &bad, int S = 0, int nact = 0)
+                                              long long &mymin, int &bad, int S = 0, int nact = 0,
+                                              bool trial = false)
 {
     if (MIXED)
-        correct_slots_ds<COH>(d, T, k_lo, k_hi, w0, ws, mymin, bad, S, nact);
+        correct_slots_ds<COH>(d, T, k_lo, k_hi, w0, ws, mymin, bad, S, nact, trial);
     else
-        correct_slots64<COH>(d, T, k_lo, k_hi, w0, ws, mymin, bad, S, nact);
+        correct_slots64<COH>(d, T, k_lo, k_hi, w0, ws, mymin, bad, S, nact, trial);
 }
 
 // ---------------------------------------------------------------- j-split reduction
@@ -1860,6 +1888,8 @@ struct CArgs {
     int tail_ok;
     int mixed;
     int defer;     // the force kernel ran with FArgs::defer: its deferred plans are summed here
+    int commit;    // 1: the block step's last pass (state, steps, next block time); 0: a pass
+                   // before it (P(EC)^n), which only writes the corrected active records
 };
 
 // Corrects every active particle and (last CTA) turns the running minimum into the
@@ -1888,9 +1918,10 @@ __global__ void __launch_bounds__(CT) k_correct(CArgs ca)
     const int nwarps = (ncta * CT) >> 5;
     long long mymin = LLONG_MAX;
     int bad = 0;
-    correct_slots<MIXED, false>(d, T, 0, nact, gwarp, nwarps, mymin, bad, S, nact);
+    correct_slots<MIXED, false>(d, T, 0, nact, gwarp, nwarps, mymin, bad, S, nact, ca.commit == 0);
     if (bad & 2) set_err(ctrl, ST_EINVAL);
     if (bad & 1) set_err(ctrl, ST_ENONFINITE);
+    if (!ca.commit) return;
     mymin = warp_min_ll(mymin);
     if (lane == 0 && mymin != LLONG_MAX) atomicMin((unsigned long long *)&ctrl->T_acc, (unsigned long long)mymin);
     // the barrier orders this CTA's minimum updates before thread 0's release fence
@@ -1907,7 +1938,7 @@ __global__ void __launch_bounds__(CT) k_correct(CArgs ca)
             ctrl->T_acc = LLONG_MAX;
             ctrl->nblock += 1;
             ctrl->nsteps += nact;
-            ctrl->interactions += (double)nact * (double)n;
+            ctrl->interactions += (double)nact * (double)n * d.n_iter;  // every pass evaluated the forces
             ctrl->epoch += 1;
             ctrl->done = 0;
         }

@@ -65,6 +65,7 @@ class gd_opts(ctypes.Structure):
         ("pn_p", ctypes.c_int32),
         ("pn_q", ctypes.c_int32),
         ("pn_c", ctypes.c_double),
+        ("n_iter", ctypes.c_int32),
     ]
 
 
@@ -173,7 +174,7 @@ def _check(rc, ctx=None):
 
 def make_opts(dt_min=2.0 ** -22, dt_max=0.125, precision="mixed", device=0, stream=None, use_graph=True,
               graph_steps=16, jsplit=0, mode_cut=0, time_force=False, autotune=False, fused=False, pdl=None,
-              tail_correct=None, cluster=None, corrector="hermite", pn=None):
+              tail_correct=None, cluster=None, corrector="hermite", pn=None, n_iter=1):
     o = gd_opts()
     load().gd_opts_default(ctypes.byref(o))
     o.dt_min = float(dt_min)
@@ -197,6 +198,7 @@ def make_opts(dt_min=2.0 ** -22, dt_max=0.125, precision="mixed", device=0, stre
     o.corrector = {"hermite": GD_CORR_HERMITE, "timesym": GD_CORR_TIMESYM}[corrector]
     if pn is not None:  # (p, q, c, terms)
         o.pn_p, o.pn_q, o.pn_c, o.pn_terms = int(pn[0]), int(pn[1]), float(pn[2]), int(pn[3])
+    o.n_iter = int(n_iter)
     return o
 
 

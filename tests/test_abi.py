@@ -204,6 +204,27 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(got["%s.size" % st]) == ctypes.sizeof(cls), st
 
 
+def test_pass_count_is_checked_on_the_host():
+    """gd_opts.n_iter: 1 to 16 passes; more than one needs the time-symmetric
+    corrector and takes neither a post-Newtonian pair nor the fused kernel nor an
+    ensemble (rejected before any device work)."""
+    lib = gravidy.load()
+    n, m, x, v = _small_system()
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    bad = (dict(n_iter=0), dict(n_iter=17), dict(n_iter=2), dict(n_iter=2, corrector="timesym", fused=True),
+           dict(n_iter=2, corrector="timesym", pn=(0, 1, 10.0, 1)))
+    for kw in bad:
+        o = gravidy.make_opts(**kw)
+        h = ctypes.c_void_p()
+        assert lib.gd_init(ctypes.byref(h), n, p(m), p(x), p(v), 1e-4, 0.01, ctypes.byref(o)) == gravidy.GD_EINVAL, kw
+        assert not h.value
+    sizes = np.array([n], dtype=np.int64)
+    o = gravidy.make_opts(n_iter=2, corrector="timesym")
+    h = ctypes.c_void_p()
+    assert lib.gd_ens_init(ctypes.byref(h), 1, p(sizes), p(m), p(x), p(v), 1e-4, 0.01,
+                           ctypes.byref(o)) == gravidy.GD_EINVAL
+
+
 def test_post_newtonian_pair_is_checked_on_the_host():
     lib = gravidy.load()
     n, m, x, v = _small_system()

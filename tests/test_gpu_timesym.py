@@ -275,3 +275,84 @@ def test_timesym_corrector_in_an_ensemble_follows_each_cluster_alone():
         sl = slice(off[q], off[q + 1])
         assert np.mean(st["dtau"][sl] == so["dtau"]) > 0.99
         assert np.abs(st["x"][sl] - so["x"]).max() < 1e-6
+
+
+# ---- P(EC)^n passes on the fourth-order integrator (gd_init, gd_opts.n_iter, with
+# the time-symmetric corrector) against the order-4 oracle with the same passes
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("n_iter", [2, 3])
+def test_passes_replay_the_oracle_schedule_n512(prec, n_iter):
+    """The oracle's free-running P(EC)^n schedule replayed on the fourth-order GPU
+    integrator with the same passes: FP64 states to round-off growth, mixed states
+    within the bound of the one-pass mixed replay; every pass counts its
+    interactions."""
+    m, x, v = inputs.plummer(512, seed=2)
+    sim = oracle.Sim6(m, x, v, EPS, ETA4, eta_init=ETA4, order=4, n_iter=n_iter)
+    rec = []
+    while True:
+        tick, idx = sim.step()
+        rec.append((tick, idx))
+        if tick >= int(0.5 / DT_MIN):
+            break
+    so = sim.state()
+    with gravidy.Integrator(m, x, v, EPS, ETA4, precision=prec, corrector="timesym", n_iter=n_iter,
+                            cluster=False) as g:
+        i0 = g.stats()["interactions"]
+        for tick, idx in rec:
+            g.replay_step(tick, idx)
+        st = g.state()
+        inter = g.stats()["interactions"] - i0
+    dx = np.abs(st["x"] - so["x"]).max()
+    print("%s n_iter %d replay n=512: %d steps, max|dx| %.2e, dtau agree %.4f"
+          % (prec, n_iter, len(rec), dx, np.mean(st["dtau"] == so["dtau"])))
+    assert inter == n_iter * 512.0 * sum(len(idx) for _, idx in rec)
+    assert (st["tau"] == so["tau"]).all()
+    if prec == "fp64":
+        assert dx < 1e-9 and np.mean(st["dtau"] == so["dtau"]) > 0.99
+    else:
+        assert dx < 1e-4
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_two_passes_free_run_n512_to_t1(prec):
+    m, x, v = inputs.plummer(512, seed=1)
+    sim = oracle.Sim6(m, x, v, EPS, ETA4, eta_init=ETA4, order=4, n_iter=2)
+    K0, U0 = sim.energy()
+    sim.evolve(1.0)
+    K1, U1 = sim.energy()
+    so = sim.stats()
+    de_or = abs((K1 + U1 - K0 - U0) / (K0 + U0))
+    with gravidy.Integrator(m, x, v, EPS, ETA4, precision=prec, corrector="timesym", n_iter=2) as g:
+        assert g.cluster_info()[0] == 0
+        E0 = sum(g.energy())
+        g.evolve(1.0)
+        de = abs((sum(g.energy()) - E0) / E0)
+        st = g.stats()
+    print("%s n_iter 2 free n=512 t=1: |dE/E| oracle %.3e gpu %.3e blocks %d/%d psteps %d/%d"
+          % (prec, de_or, de, st["block_steps"], so["nblock"], st["particle_steps"], so["nsteps"]))
+    tol = 0.002 if prec == "fp64" else 0.01
+    assert abs(st["block_steps"] - so["nblock"]) <= tol * so["nblock"]
+    assert abs(st["particle_steps"] - so["nsteps"]) <= tol * so["nsteps"]
+    assert de <= 2 * de_or + 1e-9
+
+
+def test_two_passes_reversible_on_the_fourth_order_integrator():
+    """Shared constant steps on a Kepler orbit (FP64): forward to t = 6, velocities
+    reversed, forward again; two passes return to the start to round-off, one pass
+    does not (its map is not time-symmetric)."""
+    dt = 2.0 ** -8
+    m, x, v = kepler_ic(0.5)
+    err = {}
+    for n_iter in (1, 2):
+        kw = dict(precision="fp64", corrector="timesym", n_iter=n_iter, dt_min=dt, dt_max=dt)
+        with gravidy.Integrator(m, x, v, 0.0, 0.2, **kw) as g:
+            g.evolve(6.0)
+            fw = g.state()
+        with gravidy.Integrator(m, fw["x"], -fw["v"], 0.0, 0.2, **kw) as g:
+            g.evolve(6.0)
+            bk = g.state()
+        err[n_iter] = max(np.abs(bk["x"] - x).max(), np.abs(bk["v"] + v).max())
+    print("fourth-order integrator Kepler round trip: one pass %.2e, two passes %.2e" % (err[1], err[2]))
+    assert err[2] < 1e-12
+    assert err[1] > 30 * err[2]
