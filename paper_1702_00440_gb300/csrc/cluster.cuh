@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
             const float2 C0 = iC[k0], C1 = iC[k1];
             float f0[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, f1[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (has1) {
-#pragma unroll 4
+#pragma unroll 8
                 for (int j = jb + lane; j < je; j += 32) {
                     const float4 A = jA[j], B = jB[j];
                     const float2 Cj = jC[j];

@@ -1675,7 +1675,7 @@ __device__ void phase_force_mixed(const Dev &d, int nact, const Plan &pl, bool t
                     const float4 *sA = sj.A[buf], *sB = sj.B[buf];
                     const float2 *sC = sj.C[buf];
                     float f0[6] = {0, 0, 0, 0, 0, 0}, f1[6] = {0, 0, 0, 0, 0, 0};
-#pragma unroll 4
+#pragma unroll 8
                     for (int jj = 0; jj < BJ; jj++) {
                         const float4 A = sA[jj], B = sB[jj];
                         const float2 C = sC[jj];
@@ -1726,7 +1726,7 @@ __device__ void phase_force_mixed(const Dev &d, int nact, const Plan &pl, bool t
                 if (busy) {
                     const float4 *sA = sj.A[buf], *sB = sj.B[buf];
                     const float2 *sC = sj.C[buf];
-#pragma unroll 4
+#pragma unroll 8
                     for (int jj = lane; jj < nt; jj += 32) {
                         const float4 A = sA[jj], B = sB[jj];
                         const float2 C = sC[jj];
