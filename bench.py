@@ -60,11 +60,13 @@ TRAFFIC_PER_LAUNCH = {
     # asynchronous double-buffered j-tiles in the force kernel, per-bucket choice of
     # where warp-mode j-split sums are taken
     "2d1d3ec0": {"k_cluster_steps": 1582080, "k_force_mixed": 716288},
-    # 2d1d3ec0 plus the 2PN pair terms, which only the corrector and the force hooks
-    # contain, and the P(EC)^n trial passes of the corrector (a branch the captured
-    # force kernel compiles out): the two captured kernels' memory accesses are unchanged
-    "fe3ba5e9": {"k_cluster_steps": 1582080, "k_force_mixed": 716288},
+    # 2d1d3ec0 plus the 2PN pair terms (only in the corrector and the force hooks),
+    # then plus the P(EC)^n trial passes of the corrector (a branch the captured force
+    # kernel compiles out): the two captured kernels' memory accesses are unchanged
     "ddb7dccc": {"k_cluster_steps": 1582080, "k_force_mixed": 716288},
+    "fe3ba5e9": {"k_cluster_steps": 1582080, "k_force_mixed": 716288},
+    # j-loops unrolled 8 in the force kernel and the cluster's force tasks
+    "2dc045bc": {"k_cluster_steps": 1579264, "k_force_mixed": 722688},
 }
 
 
