@@ -798,8 +798,10 @@ def sweep_accuracy(a):
 
 def sweep_ensemble(a):
     """256 independent Plummer spheres, N_c log-uniform in [256, 8192] (seeded),
-    eps = 1e-4, eta = 0.01, mixed: advanced together as one ensemble vs the same
-    clusters one after another (one context each, captured-graph steps)."""
+    eps = 1e-4, eta = 0.01, mixed: advanced together as one ensemble (each system in
+    its own thread-block cluster, the default; and the global-block-time forms: two
+    kernels per global step, the cooperative kernel) vs the same clusters one after
+    another (one context each, captured-graph steps)."""
     import torch
 
     from paper_1702_00440_gb300 import gravidy, inputs
@@ -845,6 +847,20 @@ def sweep_ensemble(a):
         steps_seq += st1["block_steps"] - st0["block_steps"]
         g.close()
     inter_ens = s1["interactions"] - s0["interactions"]
+    # the global-block-time form: two kernels per global step in a captured graph
+    e = gravidy.Ensemble(sizes, np.concatenate(ms), np.concatenate(xs), np.concatenate(vs), EPS, ETA, cluster=False)
+    sg0 = e.stats()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e.evolve(t_end)
+    wall_g = time.perf_counter() - t0
+    sg1 = e.stats()
+    Kg, Ug = e.energy()
+    e.close()
+    two_kernel = {"wall_s": wall_g, "global_block_steps": sg1["block_steps"] - sg0["block_steps"],
+                  "particle_steps": sg1["particle_steps"] - sg0["particle_steps"],
+                  "interactions_per_s": (sg1["interactions"] - sg0["interactions"]) / wall_g,
+                  "max_rel_energy_difference_vs_systems": float(np.max(np.abs((Kg + Ug) - (K1 + U1)) / np.abs(K1 + U1)))}
     # the cooperative form: select and force + correction of a global step in one
     # launch with a grid barrier between them, one step or 64 steps per launch
     fused = {}
@@ -861,11 +877,14 @@ def sweep_ensemble(a):
         fused["steps_per_launch_%d" % spl] = {
             "wall_s": wf, "global_block_steps": sf1["block_steps"] - sf0["block_steps"],
             "interactions_per_s": (sf1["interactions"] - sf0["interactions"]) / wf,
-            "same_steps_as_two_kernel": sf1["block_steps"] - sf0["block_steps"] == s1["block_steps"] - s0["block_steps"]}
+            "same_steps_as_two_kernel": sf1["block_steps"] - sf0["block_steps"] == two_kernel["global_block_steps"]}
     out = {"sweep": "ensemble", "clusters": int(sizes.size), "particles": int(sizes.sum()),
            "n_min": int(sizes.min()), "n_max": int(sizes.max()), "t_end": t_end,
-           "ensemble": {"wall_s": wall_ens, "global_block_steps": s1["block_steps"] - s0["block_steps"],
+           "ensemble": {"wall_s": wall_ens, "path": "independent systems (one thread-block cluster each)",
+                        "system_block_steps": s1["block_steps"] - s0["block_steps"],
+                        "particle_steps": s1["particle_steps"] - s0["particle_steps"],
                         "interactions_per_s": inter_ens / wall_ens},
+           "two_kernel_global_steps": two_kernel,
            "fused": fused,
            "one_by_one": {"wall_s": wall_seq, "block_steps": steps_seq, "interactions_per_s": inter_seq / wall_seq},
            "speedup": wall_seq / wall_ens,

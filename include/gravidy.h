@@ -333,7 +333,14 @@ typedef struct gd_ens gd_ens;
 int gd_ens_init(gd_ens **out, int32_t nclusters, const int64_t *n_per, const double *m, const double *x,
                 const double *v, double eps, double eta, const gd_opts *opt);
 
-/* Advance every cluster until no particle's next time is <= t_end. */
+/* Advance every cluster until no particle's next time is <= t_end.  With
+ * opts.cluster = 1 (the default), opts.fused = 0 and every cluster small enough
+ * (at most 16 x 1024 particles), each cluster is integrated on its own, without a
+ * global block time: one launch whose thread-block clusters (the fewest CTAs of
+ * 1024 particles that hold the largest cluster, up to 16) take whole clusters from
+ * a work queue, largest first, and run all of a cluster's block steps in shared
+ * memory; the same schedule and arithmetic per particle as the global steps, force
+ * sums split over those CTAs.  Otherwise global block steps, as above. */
 int gd_ens_evolve(gd_ens *s, double t_end);
 
 /* One global block step; *t_out its time, *nact_out its active particles (all clusters). */
@@ -347,7 +354,9 @@ int gd_ens_energy(gd_ens *s, double *K, double *U);
 /* Concatenated state (cluster order, as given to gd_ens_init); any pointer may be NULL. */
 int gd_ens_get_state(gd_ens *s, double *x, double *v, int64_t *tau, int64_t *dtau);
 
-/* Counters over all clusters (interactions count only pairs within a cluster). */
+/* Counters over all clusters (interactions count only pairs within a cluster).
+ * block_steps counts global block steps, except that gd_ens_evolve on the
+ * independent-cluster path adds every cluster's own block steps. */
 int gd_ens_get_stats(gd_ens *s, gd_stats *st);
 
 void gd_ens_free(gd_ens *s);

@@ -20,6 +20,7 @@
 #include "kernels.cuh"
 #include "ensemble.cuh"
 #include "cluster.cuh"
+#include "ens_systems.cuh"
 
 using namespace gdk;
 
@@ -1474,6 +1475,14 @@ struct gd_ens {
     int grid_ens;
     int grid_steps;      // fused: co-resident grid of k_ens_steps (0 = not available)
     bool fused;          // gd_ens_evolve runs k_ens_steps, graph_steps global steps per cooperative launch
+    int es_C;            // 1: gd_ens_evolve integrates the systems independently (k_ens_systems)
+    int es_n[ES_CLASSES], es_first[ES_CLASSES], es_G[ES_CLASSES];  // per class of 2^k CTAs: systems,
+                                                                   // their place in d_order, clusters launched
+    cudaStream_t es_stream[ES_CLASSES];
+    cudaEvent_t es_ev[ES_CLASSES], es_ev0;
+    size_t es_smem;
+    int *d_order;        // systems by class, largest first within a class
+    unsigned int *d_queue;  // one work-queue position per class
     std::string err;
 };
 
@@ -1490,10 +1499,16 @@ int ens_fail(gd_ens *s, int code, const std::string &msg)
 
 void ens_free_dev(gd_ens *s)
 {
-    void *ps[] = {s->d_cs, s->d_cnp, s->d_cn, s->d_cnact, s->d_pcl, s->d_tilecnt, s->d_part, s->d_K, s->d_U};
+    void *ps[] = {s->d_cs,   s->d_cnp, s->d_cn, s->d_cnact, s->d_pcl,   s->d_tilecnt,
+                  s->d_part, s->d_K,   s->d_U,  s->d_order, s->d_queue};
     for (void *p : ps)
         if (p) cudaFree(p);
     if (s->graph) cudaGraphExecDestroy(s->graph);
+    for (int k = 0; k < ES_CLASSES; k++) {
+        if (s->es_stream[k]) cudaStreamDestroy(s->es_stream[k]);
+        if (s->es_ev[k]) cudaEventDestroy(s->es_ev[k]);
+    }
+    if (s->es_ev0) cudaEventDestroy(s->es_ev0);
 }
 
 // One cooperative launch of up to max_steps fused global block steps.
@@ -1513,6 +1528,125 @@ int ens_launch_fused(gd_ens *s, int max_steps)
 // gd_ens_evolve through k_ens_steps: launches of graph_steps global steps each,
 // one kept in flight while the host reads the previous one's control-block
 // snapshot (as gd_evolve does).
+// Chooses the independent-systems path (k_ens_systems): each system goes to the
+// class of thread-block clusters with the fewest CTAs (1, 2, 4, 8 or 16, ES_P
+// particles each) that hold it, and each non-empty class gets its own launch on its
+// own stream, with a work queue of its systems, largest first (the classes run side
+// by side; no launch waits on another).  Leaves es_C = 0 when a system is too large
+// or such clusters cannot be launched.
+int ens_systems_setup(gd_ens *s, int device)
+{
+    s->es_C = 0;
+    gd_ctx *c = s->c;
+    const size_t bytes = EsLayout().bytes;
+    int maxdyn = 0;
+    cudaDeviceGetAttribute(&maxdyn, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    std::vector<int> order;
+    for (int k = 0; k < ES_CLASSES; k++) {
+        const int CE = 1 << k;
+        std::vector<int> sys;
+        for (int q = 0; q < s->C; q++) {
+            const int need = (s->cn[q] + ES_P - 1) / ES_P;
+            int ce = 1;
+            while (ce < need) ce *= 2;
+            if (ce == CE) sys.push_back(q);
+        }
+        s->es_n[k] = (int)sys.size();
+        s->es_first[k] = (int)order.size();
+        s->es_G[k] = 0;
+        if (sys.empty()) continue;
+        std::stable_sort(sys.begin(), sys.end(), [&](int x, int y) { return s->cn[x] > s->cn[y]; });
+        order.insert(order.end(), sys.begin(), sys.end());
+        const void *fn = c->soft ? (const void *)k_ens_systems<true> : (const void *)k_ens_systems<false>;
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess || bytes + fa.sharedSizeBytes > (size_t)maxdyn ||
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess ||
+            cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, CE > 8 ? 1 : 0) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            return GD_OK;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(CE);
+        cfg.blockDim = dim3(ES_T);
+        cfg.dynamicSmemBytes = bytes;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = CE;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int ncl = 0;
+        if (cudaOccupancyMaxActiveClusters(&ncl, fn, &cfg) != cudaSuccess || ncl < 1) {
+            cudaGetLastError();
+            return GD_OK;
+        }
+        s->es_G[k] = std::min(s->es_n[k], ncl);
+    }
+    if ((int)order.size() != s->C) return GD_OK;  // a system larger than 16 x ES_P
+    cudaError_t e = gd_alloc_fails(1) ? cudaErrorMemoryAllocation : cudaMalloc((void **)&s->d_order, sizeof(int) * s->C);
+    if (e == cudaSuccess)
+        e = gd_alloc_fails(1) ? cudaErrorMemoryAllocation
+                              : cudaMalloc((void **)&s->d_queue, sizeof(unsigned int) * ES_CLASSES);
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_order, order.data(), sizeof(int) * s->C, cudaMemcpyHostToDevice);
+    for (int k = 0; k < ES_CLASSES && e == cudaSuccess; k++) {
+        e = cudaStreamCreateWithFlags(&s->es_stream[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->es_ev[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->es_ev0, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? GD_ENOMEM : GD_ECUDA;
+    }
+    s->es_C = 1;
+    s->es_smem = bytes;
+    return GD_OK;
+}
+
+// gd_ens_evolve through k_ens_systems: one launch per class of thread-block clusters
+// integrates that class's systems to tick_end (the launches run side by side on their
+// own streams and join the context's stream); the control block then holds the
+// latest of the systems' last block times (T_last) and, after k_resync, the next
+// block time over all of them.
+int ens_evolve_systems(gd_ens *s, long long tick_end)
+{
+    gd_ctx *c = s->c;
+    cudaStream_t st = c->stream;
+    cudaError_t e = cudaMemsetAsync(s->d_queue, 0, sizeof(unsigned int) * ES_CLASSES, st);
+    if (e == cudaSuccess) e = cudaEventRecord(s->es_ev0, st);
+    for (int k = 0; k < ES_CLASSES && e == cudaSuccess; k++) {
+        if (!s->es_n[k]) continue;
+        const int CE = 1 << k;
+        cudaStream_t sk = s->es_stream[k];
+        e = cudaStreamWaitEvent(sk, s->es_ev0, 0);
+        if (e != cudaSuccess) break;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(s->es_G[k] * CE);
+        cfg.blockDim = dim3(ES_T);
+        cfg.dynamicSmemBytes = s->es_smem;
+        cfg.stream = sk;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = CE;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        const EsArgs a{c->d, s->e, s->d_order + s->es_first[k], s->es_n[k], s->d_queue + k, tick_end};
+        e = c->soft ? cudaLaunchKernelEx(&cfg, k_ens_systems<true>, a) : cudaLaunchKernelEx(&cfg, k_ens_systems<false>, a);
+        if (e == cudaSuccess) e = cudaEventRecord(s->es_ev[k], sk);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, s->es_ev[k], 0);
+        c->launches += 1;
+    }
+    if (e != cudaSuccess) return ens_fail(s, GD_ECUDA, std::string("systems launch: ") + cudaGetErrorString(e));
+    k_resync<<<1, 1024, 0, st>>>(c->d);
+    c->launches += 1;
+    int rc = sync_ctrl(c);
+    if (rc) return ens_fail(s, rc, c->err);
+    return GD_OK;
+}
+
 int ens_evolve_fused(gd_ens *s, long long tick_end)
 {
     gd_ctx *c = s->c;
@@ -1698,6 +1832,7 @@ int gd_ens_init(gd_ens **out, int32_t nclusters, const int64_t *n_per, const dou
         if (e != cudaSuccess) return bail(ens_fail(s, GD_ECUDA, std::string("first forces: ") + cudaGetErrorString(e)));
         if ((rc = sync_ctrl(c))) return bail(ens_fail(s, rc, c->err));
     }
+    if (o.cluster && !s->fused && (rc = ens_systems_setup(s, o.device))) return bail(ens_fail(s, rc, "systems setup"));
     *out = s;
     return GD_OK;
 }
@@ -1713,6 +1848,7 @@ int gd_ens_evolve(gd_ens *s, double t_end)
     if (tick_end < c->h_ctrl->T_last) return ens_fail(s, GD_EINVAL, "t_end is before the current time");
     const int G = c->graph_steps;
     if (s->fused) return ens_evolve_fused(s, tick_end);
+    if (s->es_C) return ens_evolve_systems(s, tick_end);
     if (c->opt.use_graph && !s->graph) {
         cudaGraph_t g;
         cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);

@@ -110,7 +110,7 @@ def test_fused_ensemble_launches_match_the_two_kernel_steps(steps_per_launch):
     sizes = [300, 1000, 64, 2500, 777]
     ms, xs, vs = _clusters(sizes, seed0=300)
     out = []
-    for opts in (dict(), dict(fused=True, graph_steps=steps_per_launch)):
+    for opts in (dict(cluster=False), dict(fused=True, graph_steps=steps_per_launch)):
         with gravidy.Ensemble(sizes, np.concatenate(ms), np.concatenate(xs), np.concatenate(vs), EPS, ETA,
                               **opts) as e:
             e.evolve(0.25)
@@ -121,3 +121,48 @@ def test_fused_ensemble_launches_match_the_two_kernel_steps(steps_per_launch):
             out.append(st)
     for k in out[0]:
         assert np.array_equal(out[0][k], out[1][k]), k
+
+
+@pytest.mark.parametrize("t_end", [0.125, 0.375])
+def test_independent_systems_follow_the_global_steps(t_end):
+    """Each system integrated to the end inside its own thread-block cluster (the
+    default ensemble path) against the global-block-time two-kernel path: the same
+    scheme and arithmetic per particle, force sums split over other CTAs, so the
+    runs agree to round-off growth.  The sizes include a three-body system (CTAs
+    without particles), systems whose steps take more active particles than one
+    batch, and one whose CTAs own more active particles than their outbox holds."""
+    sizes = [2500, 3, 700, 129, 1500, 64]
+    ms, xs, vs = _clusters(sizes, seed0=500)
+    out = []
+    for opts in (dict(), dict(cluster=False)):
+        with gravidy.Ensemble(sizes, np.concatenate(ms), np.concatenate(xs), np.concatenate(vs), EPS, ETA,
+                              **opts) as e:
+            e.evolve(t_end)
+            st = e.state()
+            s = e.stats()
+            K, U = e.energy()
+            out.append((st, s, K + U))
+    (a, sa, Ea), (b, sb, Eb) = out
+    print("systems vs global: psteps %d / %d, dtau agree %.4f, max|dx| %.2e, max rel dE %.2e"
+          % (sa["particle_steps"], sb["particle_steps"], np.mean(a["dtau"] == b["dtau"]),
+             np.abs(a["x"] - b["x"]).max(), np.max(np.abs(Ea - Eb) / np.abs(Eb))))
+    tick = int(t_end / 2.0 ** -22)
+    assert (a["tau"] == tick).all() and (b["tau"] == tick).all()
+    assert np.mean(a["dtau"] == b["dtau"]) > 0.99
+    assert np.abs(a["x"] - b["x"]).max() < 1e-6
+    assert abs(sa["particle_steps"] - sb["particle_steps"]) <= 0.01 * sb["particle_steps"]
+    assert abs(sa["interactions"] - sb["interactions"]) <= 0.01 * sb["interactions"]
+    assert np.all(np.abs(Ea - Eb) <= 1e-6 * np.abs(Eb))
+
+
+def test_independent_systems_then_global_steps():
+    """The state after the independent-systems path continues on the global path
+    (step_block) at the next block time of all systems."""
+    sizes = [300, 1000]
+    ms, xs, vs = _clusters(sizes, seed0=9)
+    with gravidy.Ensemble(sizes, np.concatenate(ms), np.concatenate(xs), np.concatenate(vs), EPS, ETA) as e:
+        e.evolve(0.125)
+        st = e.state()
+        t, nact = e.step_block()
+    assert t > 0.125 and nact >= 1
+    assert t == 0.125 + st["dtau"].min() * 2.0 ** -22
