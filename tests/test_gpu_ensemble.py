@@ -166,3 +166,23 @@ def test_independent_systems_then_global_steps():
         t, nact = e.step_block()
     assert t > 0.125 and nact >= 1
     assert t == 0.125 + st["dtau"].min() * 2.0 ** -22
+
+
+def test_independent_systems_with_a_sixteen_cta_cluster():
+    """A cluster of 9000 particles needs the 16-CTA class (more than 8 x 1024), a
+    small one the 1-CTA class: both against the global two-kernel path."""
+    sizes = [9000, 500]
+    ms, xs, vs = _clusters(sizes, seed0=700)
+    out = []
+    for opts in (dict(), dict(cluster=False)):
+        with gravidy.Ensemble(sizes, np.concatenate(ms), np.concatenate(xs), np.concatenate(vs), EPS, ETA,
+                              **opts) as e:
+            e.evolve(0.125)
+            out.append((e.state(), e.stats()))
+    (a, sa), (b, sb) = out
+    print("16-CTA class: psteps %d / %d, dtau agree %.4f, max|dx| %.2e"
+          % (sa["particle_steps"], sb["particle_steps"], np.mean(a["dtau"] == b["dtau"]), np.abs(a["x"] - b["x"]).max()))
+    assert (a["tau"] == b["tau"]).all()
+    assert np.mean(a["dtau"] == b["dtau"]) > 0.99
+    assert np.abs(a["x"] - b["x"]).max() < 1e-6
+    assert abs(sa["particle_steps"] - sb["particle_steps"]) <= 0.01 * sb["particle_steps"]
