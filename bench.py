@@ -67,6 +67,10 @@ TRAFFIC_PER_LAUNCH = {
     "fe3ba5e9": {"k_cluster_steps": 1582080, "k_force_mixed": 716288},
     # j-loops unrolled 8 in the force kernel and the cluster's force tasks
     "2dc045bc": {"k_cluster_steps": 1579264, "k_force_mixed": 722688},
+    # 2dc045bc plus the independent-cluster ensemble kernel (a separate file) and the
+    # post-Newtonian pair in the cluster's correction (a branch the benchmark, with no
+    # pair, does not take): the two captured kernels' memory accesses are unchanged
+    "e180922f": {"k_cluster_steps": 1579264, "k_force_mixed": 722688},
 }
 
 

@@ -101,9 +101,9 @@ typedef struct gd_opts {
                            1PN, 2PN and 2.5PN (radiation reaction) relative accelerations of the
                            two-body problem in harmonic coordinates (Kidder 1995; Blanchet 2014),
                            added with their time derivative to the force and jerk of particles
-                           pn_p (share m_q/M) and pn_q (share -m_p/M) whenever they are active.
-                           gd_init only (not ensembles); the small-step cluster is not used with
-                           them */
+                           pn_p (share m_q/M) and pn_q (share -m_p/M) whenever they are active,
+                           in every path (three kernels, small-step cluster, fused kernel).
+                           gd_init only (not ensembles) */
     int32_t pn_p, pn_q; /* the pair, distinct indices in [0, n) */
     double pn_c;        /* speed of light in the caller's units (G = 1), > 0 */
     int32_t n_iter;     /* evaluation-correction passes per block step, 1 (default) to 16: with

@@ -407,7 +407,18 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
                         pa[q] = __fadd_rn(pa[q], pa[q + h]);
                         pj[q] = __fadd_rn(pj[q], pj[q + h]);
                     }
-                const float a1 = pa[0], j1 = pj[0];
+                float a1 = pa[0], j1 = pj[0];
+                if (d.pn_terms) {
+                    // a post-Newtonian pair member: the pair terms from both members'
+                    // predicted records, wherever in the cluster they are held
+                    const int gi = p0 + p;
+                    if (gi == d.pn_p || gi == d.pn_q) {
+                        const int op = d.pn_p / P, lp = d.pn_p % P, oq = d.pn_q / P, lq = d.pn_q % P;
+                        pn_add_records(d, gi, c, cl.map_shared_rank(jA, op)[lp], cl.map_shared_rank(jB, op)[lp],
+                                       cl.map_shared_rank(jC, op)[lp], cl.map_shared_rank(jA, oq)[lq],
+                                       cl.map_shared_rank(jB, oq)[lq], cl.map_shared_rank(jC, oq)[lq], a1, j1);
+                    }
+                }
                 const F2 x0{xh[c * P + p], xl[c * P + p]}, v0{vh[c * P + p], vl[c * P + p]};
                 const float a0 = af[c * P + p], j0 = jf[c * P + p];
                 const long long dtau_old = dtau[p];

@@ -338,7 +338,7 @@ void launch_cycle(gd_ctx *c, int slot, cudaEvent_t e0, cudaEvent_t e1, bool capt
 void cluster_setup(gd_ctx *c)
 {
     c->cl_C = 0;
-    if (!c->mixed || !c->opt.cluster || c->d.pn_terms || c->opt.n_iter > 1) return;
+    if (!c->mixed || !c->opt.cluster || c->opt.n_iter > 1) return;
     const void *fn = c->soft ? (const void *)k_cluster_steps<true> : (const void *)k_cluster_steps<false>;
     int maxdyn = 0;
     cudaDeviceGetAttribute(&maxdyn, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev);

@@ -1022,24 +1022,44 @@ __device__ void pn_pair_terms(int terms, T mp, T mq, T c, const T r[3], const T 
 // Particle i's share of the pair terms, component c, from the predicted j-records
 // (mixed: double-single positions, FP32 velocities; FP64: the planes pd) at the
 // block time.  Adds to a and j when i is one of the pair.
+// The pair terms' share of particle i (one of the pair), component c, from the two
+// members' predicted mixed j-records (p's and q's), added to a and j.
+__device__ __forceinline__ void pn_add_records(const Dev &d, int i, int c, float4 Ap, float4 Bp, float2 Cp,
+                                               float4 Aq, float4 Bq, float2 Cq, float &a, float &j)
+{
+    float r[3], v[3];
+    r[0] = (Ap.x - Aq.x) + (Bp.x - Bq.x);
+    r[1] = (Ap.y - Aq.y) + (Bp.y - Bq.y);
+    r[2] = (Ap.z - Aq.z) + (Bp.z - Bq.z);
+    v[0] = Bp.w - Bq.w;
+    v[1] = Cp.x - Cq.x;
+    v[2] = Cp.y - Cq.y;
+    const float mp = Ap.w, mq = Aq.w;
+    float apn[3], jpn[3];
+    pn_pair_terms<float>(d.pn_terms, mp, mq, (float)d.pn_c, r, v, apn, jpn);
+    const float w = i == d.pn_p ? mq / (mp + mq) : -mp / (mp + mq);
+    const float ac = c == 0 ? apn[0] : (c == 1 ? apn[1] : apn[2]);
+    const float jc = c == 0 ? jpn[0] : (c == 1 ? jpn[1] : jpn[2]);
+    a += w * ac;
+    j += w * jc;
+}
+
 template <bool MIXED, bool COH, class T>
 __device__ __forceinline__ void pn_add(const Dev &d, int i, int c, T &a, T &j)
 {
     if (!d.pn_terms || (i != d.pn_p && i != d.pn_q)) return;
     const int p = d.pn_p, q = d.pn_q;
-    T r[3], v[3], mp, mq;
     if (MIXED) {
         const float4 Ap = ldx<COH>(&d.jA[p]), Bp = ldx<COH>(&d.jB[p]), Aq = ldx<COH>(&d.jA[q]), Bq = ldx<COH>(&d.jB[q]);
         const float2 Cp = ldx<COH>(&d.jC[p]), Cq = ldx<COH>(&d.jC[q]);
-        r[0] = (T)((Ap.x - Aq.x) + (Bp.x - Bq.x));
-        r[1] = (T)((Ap.y - Aq.y) + (Bp.y - Bq.y));
-        r[2] = (T)((Ap.z - Aq.z) + (Bp.z - Bq.z));
-        v[0] = (T)(Bp.w - Bq.w);
-        v[1] = (T)(Cp.x - Cq.x);
-        v[2] = (T)(Cp.y - Cq.y);
-        mp = (T)Ap.w;
-        mq = (T)Aq.w;
-    } else {
+        float af = (float)a, jf = (float)j;
+        pn_add_records(d, i, c, Ap, Bp, Cp, Aq, Bq, Cq, af, jf);
+        a = (T)af;
+        j = (T)jf;
+        return;
+    }
+    T r[3], v[3], mp, mq;
+    {
         const int np = d.npad;
 #pragma unroll
         for (int k = 0; k < 3; k++) {
