@@ -122,6 +122,9 @@ def _args():
                    help="profiling hook: autotune on the --n workload, then evaluate the force of K random "
                         "particles (gd_force) once, and twice more between cudaProfilerStart/Stop; print the "
                         "tuning table and exit")
+    p.add_argument("--profile-ensemble", type=int, default=0, metavar="K",
+                   help="profiling hook: the first K clusters of the 256-cluster ensemble workload, advanced "
+                        "from t = 0 to 1/64 between cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     p.add_argument("--profile-steps", type=int, default=0, metavar="K",
                    help="profiling hook: integrate the --n workload to t = 0.375, then advance K/64 "
                         "N-body time units between cudaProfilerStart/Stop (for ncu --profile-from-start off)")
@@ -1396,6 +1399,35 @@ def profile_steps(a):
     return 0
 
 
+def profile_ensemble(a):
+    """The first K clusters of the ensemble workload (seeded sizes, Plummer), advanced
+    to t = 1/64 with the default (independent-cluster) path between
+    cudaProfilerStart/Stop; prints the wall time and the counters."""
+    import torch
+    from paper_1702_00440_gb300 import gravidy, inputs
+
+    sizes = inputs.ensemble_sizes(256, seed=1)[:a.profile_ensemble]
+    ms, xs, vs = [], [], []
+    for q, n in enumerate(sizes):
+        m, x, v = inputs.plummer(int(n), seed=1000 + q)
+        ms.append(m)
+        xs.append(x)
+        vs.append(v)
+    with gravidy.Ensemble(sizes, np.concatenate(ms), np.concatenate(xs), np.concatenate(vs), EPS, ETA) as e:
+        s0 = e.stats()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        torch.cuda.profiler.start()
+        e.evolve(1.0 / 64)
+        torch.cuda.profiler.stop()
+        wall = time.perf_counter() - t0
+        s1 = e.stats()
+    print(json.dumps({"clusters": int(sizes.size), "particles": int(sizes.sum()), "wall_s": wall,
+                      "interactions_per_s": (s1["interactions"] - s0["interactions"]) / wall,
+                      "block_steps": s1["block_steps"] - s0["block_steps"]}))
+    return 0
+
+
 def profile_nact(a):
     import torch
     from paper_1702_00440_gb300 import gravidy, inputs
@@ -1425,6 +1457,8 @@ def main():
         return profile_force_h6(a)
     if a.profile_steps:
         return profile_steps(a)
+    if a.profile_ensemble:
+        return profile_ensemble(a)
     if a.sweep:
         return {"force": sweep_force, "powerlaw": sweep_powerlaw, "accuracy": sweep_accuracy,
                 "ensemble": sweep_ensemble, "eta": sweep_eta, "soft": sweep_soft,
