@@ -186,3 +186,32 @@ def test_independent_systems_with_a_sixteen_cta_cluster():
     assert np.mean(a["dtau"] == b["dtau"]) > 0.99
     assert np.abs(a["x"] - b["x"]).max() < 1e-6
     assert abs(sa["particle_steps"] - sb["particle_steps"]) <= 0.01 * sb["particle_steps"]
+
+
+def test_independent_systems_at_the_class_edges_and_the_size_limit():
+    """Clusters of exactly 1024, 1025 and 16384 particles (a full 1-CTA cluster, the
+    smallest 2-CTA one, a full 16-CTA one) against the global path; an ensemble with
+    a cluster above 16 x 1024 particles falls back to the global path as a whole."""
+    sizes = [1024, 1025, 16384]
+    ms, xs, vs = _clusters(sizes, seed0=800)
+    out = []
+    for opts in (dict(), dict(cluster=False)):
+        with gravidy.Ensemble(sizes, np.concatenate(ms), np.concatenate(xs), np.concatenate(vs), EPS, ETA,
+                              **opts) as e:
+            e.evolve(0.125)
+            out.append((e.state(), e.stats()))
+    (a, sa), (b, sb) = out
+    assert (a["tau"] == b["tau"]).all()
+    assert np.mean(a["dtau"] == b["dtau"]) > 0.99
+    assert np.abs(a["x"] - b["x"]).max() < 1e-6
+    assert abs(sa["particle_steps"] - sb["particle_steps"]) <= 0.01 * sb["particle_steps"]
+    sizes = [17000, 100]
+    ms, xs, vs = _clusters(sizes, seed0=900)
+    res = []
+    for opts in (dict(), dict(cluster=False)):
+        with gravidy.Ensemble(sizes, np.concatenate(ms), np.concatenate(xs), np.concatenate(vs), EPS, ETA,
+                              **opts) as e:
+            e.evolve(0.125)
+            res.append(e.state())
+    for k in res[0]:
+        assert np.array_equal(res[0][k], res[1][k]), k
