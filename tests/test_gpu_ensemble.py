@@ -215,3 +215,24 @@ def test_independent_systems_at_the_class_edges_and_the_size_limit():
             res.append(e.state())
     for k in res[0]:
         assert np.array_equal(res[0][k], res[1][k]), k
+
+
+def test_independent_systems_to_an_end_time_between_synchronisations():
+    """t_end not a multiple of dt_max: every particle stops at its last step at or
+    before t_end, as on the global path, and the next global block step is the same."""
+    sizes = [700, 1500, 40]
+    ms, xs, vs = _clusters(sizes, seed0=950)
+    out = []
+    for opts in (dict(), dict(cluster=False)):
+        with gravidy.Ensemble(sizes, np.concatenate(ms), np.concatenate(xs), np.concatenate(vs), EPS, ETA,
+                              **opts) as e:
+            e.evolve(0.3)
+            st = e.state()
+            t_next, _ = e.step_block()
+            out.append((st, t_next))
+    (a, ta), (b, tb) = out
+    assert (a["tau"] == b["tau"]).all()
+    assert a["tau"].max() <= int(0.3 / 2.0 ** -22)
+    assert np.mean(a["dtau"] == b["dtau"]) > 0.99
+    assert np.abs(a["x"] - b["x"]).max() < 1e-6
+    assert ta == tb
