@@ -235,6 +235,7 @@ def test_independent_systems_to_an_end_time_between_synchronisations():
     assert np.mean(a["tau"] == b["tau"]) > 0.99
     assert a["tau"].max() <= int(0.3 / 2.0 ** -22)
     assert np.mean(a["dtau"] == b["dtau"]) > 0.99
-    assert np.abs(a["x"] - b["x"]).max() < 1e-6
+    same = a["tau"] == b["tau"]  # particles at the same time (a flipped step moves the rest)
+    assert np.abs(a["x"][same] - b["x"][same]).max() < 1e-6
     for st, t in ((a, ta), (b, tb)):
         assert t == (st["tau"] + st["dtau"]).min() * 2.0 ** -22
