@@ -71,6 +71,9 @@ TRAFFIC_PER_LAUNCH = {
     # post-Newtonian pair in the cluster's correction (a branch the benchmark, with no
     # pair, does not take): the two captured kernels' memory accesses are unchanged
     "e180922f": {"k_cluster_steps": 1579264, "k_force_mixed": 722688},
+    # e180922f with the cluster kernel's pair terms and P(EC)^n passes in a separate
+    # template instance (the benchmark launches the plain one)
+    "e618334d": {"k_cluster_steps": 1579264, "k_force_mixed": 722688},
 }
 
 

@@ -112,8 +112,9 @@ typedef struct gd_opts {
                            active particles' force and jerk and writes their corrected position
                            and velocity over their predicted ones, which the next pass evaluates
                            against; the last pass corrects as usual.  Each pass counts its
-                           N_act * N interactions.  Runs the three-kernel step (not the small-step
-                           cluster, the fused kernel or ensembles; no post-Newtonian pair) */
+                           N_act * N interactions.  The three-kernel step and the small-step
+                           cluster take the passes (not the fused kernel or ensembles; no
+                           post-Newtonian pair) */
 } gd_opts;
 
 enum { GD_CORR_HERMITE = 0, GD_CORR_TIMESYM = 1 };

@@ -93,7 +93,9 @@ struct ClArgs {
 };
 
 
-template <bool SOFT>
+// EXTRA: the instance that takes P(EC)^n passes and a post-Newtonian pair (the
+// other compiles to the plain single-pass step).
+template <bool SOFT, bool EXTRA>
 __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
 {
     cgx::cluster_group cl = cgx::this_cluster();
@@ -299,7 +301,15 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
             iC[k] = cl.map_shared_rank(oC, q)[kl];
         }
         __syncthreads();
-        const long long P5 = clock64();
+        int bad = 0;
+        long long P5 = 0, P6 = 0, P7 = 0, P8 = 0;
+        unsigned long long t2 = 0;
+        // evaluation-correction passes (P(EC)^n): each pass but the last writes the
+        // owners' corrected positions and velocities over the active particles'
+        // records, which the next pass evaluates against
+        for (int pass = 1;; pass++) {
+        const bool last = !EXTRA || pass >= d.n_iter;
+        P5 = clock64();
         // forces over this CTA's j-range: tasks (pair of active particles, j-segment),
         // so every j-record loaded from shared memory serves two pair terms; with
         // fewer than CL_W pairs each pair's j-range is cut into Sw = 2^lgS segments
@@ -356,7 +366,7 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
                 }
             }
         }
-        const long long P6 = clock64();
+        P6 = clock64();
         if (Sw > 1) {
             // this CTA's partial of active k: a pairwise tree over its Sw segment sums
             for (int lh = lgS - 1; lh >= 0; lh--) {
@@ -375,15 +385,14 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
                 dst[(aloc[k] * CL_MAXC + r) * 6 + c] = tp[((k << lgS) * 6) + c];
             }
         }
-        const long long P7 = clock64();
+        P7 = clock64();
         cl.sync();  // B2: every partial has reached its owner
-        const unsigned long long t2 = global_ns();
-        const long long P8 = clock64();
+        t2 = global_ns();
+        P8 = clock64();
         ph[1] += t2 - t1;
 
         // ---- 3. owners: sum the C partials (rank order), correct, new steps
         const int mine = s_off[r + 1] - s_off[r];
-        int bad = 0;
         {
             const int q4 = lane & 3;
             const int c = q4 < 3 ? q4 : 2;
@@ -408,7 +417,7 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
                         pj[q] = __fadd_rn(pj[q], pj[q + h]);
                     }
                 float a1 = pa[0], j1 = pj[0];
-                if (d.pn_terms) {
+                if (EXTRA && d.pn_terms) {
                     // a post-Newtonian pair member: the pair terms from both members'
                     // predicted records, wherever in the cluster they are held
                     const int gi = p0 + p;
@@ -427,7 +436,25 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
                 ds_correct(d, real, T - tau[p], dtau_old, T, x0, v0, a0, j0, a1, j1, x1, v1, dtn);
                 const bool fin = isfinite(x1.h) && isfinite(v1.h) && isfinite(a1) && isfinite(j1);
                 __syncwarp();
-                if (valid) {
+                if (!last) {
+                    // a trial pass: the corrected x, v into the particle's j-record and
+                    // its outbox copy; the state stays
+                    if (valid && real) {
+                        if (!fin) bad |= 1;
+                        const float vr = __fadd_rn(v1.h, v1.l);
+                        ((float *)&jA[p])[c] = x1.h;
+                        ((float *)&jB[p])[c] = x1.l;
+                        ((float *)&oA[kk])[c] = x1.h;
+                        ((float *)&oB[kk])[c] = x1.l;
+                        if (c == 0) {
+                            jB[p].w = vr;
+                            oB[kk].w = vr;
+                        } else {
+                            ((float *)&jC[p])[c - 1] = vr;
+                            ((float *)&oC[kk])[c - 1] = vr;
+                        }
+                    }
+                } else if (valid) {
                     if (real) {
                         if (!fin) bad |= 1;
                         xh[c * P + p] = x1.h;
@@ -444,6 +471,16 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
                     }
                 }
             }
+        }
+        if (last) break;
+        cl.sync();  // the trial records are written; the owners have read the partials
+        for (int k = t; k < nact; k += CL_T) {  // the active particles' corrected records
+            const int q = aown[k], kl = aloc[k];
+            iA[k] = cl.map_shared_rank(oA, q)[kl];
+            iB[k] = cl.map_shared_rank(oB, q)[kl];
+            iC[k] = cl.map_shared_rank(oC, q)[kl];
+        }
+        __syncthreads();
         }
         mn = warp_min_ll(mn);
         bad = __reduce_or_sync(0xffffffffu, bad);
@@ -540,7 +577,7 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
             ctrl->last_nact = last_n;
             ctrl->nblock += steps;
             ctrl->nsteps += psteps;
-            ctrl->interactions += (double)psteps * (double)n;
+            ctrl->interactions += (double)psteps * (double)n * d.n_iter;  // every pass evaluated the forces
             ctrl->epoch += (unsigned)steps;
         }
     }

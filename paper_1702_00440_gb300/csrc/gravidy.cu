@@ -310,10 +310,13 @@ void launch_cluster(gd_ctx *c, int handoff, int slot, int max_steps = CL_STEPS)
     cfg.numAttrs = 1;
     const ClArgs a{c->d, c->cl_P, c->cl_ns, max_steps, handoff, slot};
     c->launches += 1;
+    const bool extra = c->opt.n_iter > 1 || c->d.pn_terms;
     if (c->soft)
-        cudaLaunchKernelEx(&cfg, k_cluster_steps<true>, a);
+        extra ? cudaLaunchKernelEx(&cfg, k_cluster_steps<true, true>, a)
+              : cudaLaunchKernelEx(&cfg, k_cluster_steps<true, false>, a);
     else
-        cudaLaunchKernelEx(&cfg, k_cluster_steps<false>, a);
+        extra ? cudaLaunchKernelEx(&cfg, k_cluster_steps<false, true>, a)
+              : cudaLaunchKernelEx(&cfg, k_cluster_steps<false, false>, a);
 }
 
 // One cycle of gd_evolve: small steps in the cluster (when enabled) until a large
@@ -338,8 +341,10 @@ void launch_cycle(gd_ctx *c, int slot, cudaEvent_t e0, cudaEvent_t e1, bool capt
 void cluster_setup(gd_ctx *c)
 {
     c->cl_C = 0;
-    if (!c->mixed || !c->opt.cluster || c->opt.n_iter > 1) return;
-    const void *fn = c->soft ? (const void *)k_cluster_steps<true> : (const void *)k_cluster_steps<false>;
+    if (!c->mixed || !c->opt.cluster) return;
+    const bool extra = c->opt.n_iter > 1 || c->d.pn_terms;
+    const void *fn = c->soft ? (extra ? (const void *)k_cluster_steps<true, true> : (const void *)k_cluster_steps<true, false>)
+                             : (extra ? (const void *)k_cluster_steps<false, true> : (const void *)k_cluster_steps<false, false>);
     int maxdyn = 0;
     cudaDeviceGetAttribute(&maxdyn, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev);
     cudaFuncAttributes fa;
