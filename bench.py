@@ -74,6 +74,9 @@ TRAFFIC_PER_LAUNCH = {
     # e180922f with the cluster kernel's pair terms and P(EC)^n passes in a separate
     # template instance (the benchmark launches the plain one)
     "e618334d": {"k_cluster_steps": 1579264, "k_force_mixed": 722688},
+    # e618334d with the cluster's partial forces at a padded slot stride (shared memory
+    # only: the DRAM accesses are unchanged)
+    "fdc36443": {"k_cluster_steps": 1579264, "k_force_mixed": 722688},
 }
 
 

@@ -44,6 +44,7 @@ constexpr int CL_W = CL_T / 32;
 constexpr int CL_MAXC = 16;   // largest cluster
 constexpr int CL_NS = 128;    // most active particles a cluster step takes
 constexpr int CL_ROUNDS = 3;  // particles per thread at most (P <= CL_ROUNDS * CL_T)
+constexpr int CL_PS = CL_MAXC * 6 + 4;  // floats of one active's partials (padded: no bank conflicts)
 
 // Shared-memory layout of a CTA owning up to P particles (P a multiple of 32).
 struct ClLayout {
@@ -77,7 +78,7 @@ struct ClLayout {
         oB = take(sizeof(float4) * CL_NS);
         oC = take(sizeof(float2) * CL_NS);
         aloc = take(sizeof(int) * CL_NS);
-        part = take(sizeof(float) * CL_NS * CL_MAXC * 6);
+        part = take(sizeof(float) * CL_NS * CL_PS);
         tp = take(sizeof(float) * 2 * CL_W * 6);
         bytes = o;
     }
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
     float2 *oC = (float2 *)(smem + L.oC);                                 // particles' j-records
     float4 *iA = (float4 *)(smem + L.iA), *iB = (float4 *)(smem + L.iB);
     float2 *iC = (float2 *)(smem + L.iC);
-    float *part = (float *)(smem + L.part);  // [slot][rank][6]
+    float *part = (float *)(smem + L.part);  // [slot][rank][6], slot stride CL_PS
     float *tp = (float *)(smem + L.tp);      // [active][segment][6]
     // inboxes the other CTAs write (distributed shared memory) before a cluster barrier:
     // active counts of the step (before B1), minimum next time and fault bits (before B3)
@@ -360,7 +361,7 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
             if (store) {
                 if (Sw == 1) {
                     float *dst = cl.map_shared_rank(part, aown[k]);
-                    dst[(aloc[k] * CL_MAXC + r) * 6 + c] = mine_c;
+                    dst[aloc[k] * CL_PS + r * 6 + c] = mine_c;
                 } else {
                     tp[((k << lgS) + sg) * 6 + c] = mine_c;
                 }
@@ -382,7 +383,7 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
             for (int w = t; w < nact * 6; w += CL_T) {
                 const int k = w / 6, c = w % 6;
                 float *dst = cl.map_shared_rank(part, aown[k]);
-                dst[(aloc[k] * CL_MAXC + r) * 6 + c] = tp[((k << lgS) * 6) + c];
+                dst[aloc[k] * CL_PS + r * 6 + c] = tp[((k << lgS) * 6) + c];
             }
         }
         P7 = clock64();
@@ -406,8 +407,8 @@ __global__ void __launch_bounds__(CL_T, 1) k_cluster_steps(ClArgs a)
                 float pa[CL_MAXC], pj[CL_MAXC];
 #pragma unroll
                 for (int q = 0; q < CL_MAXC; q++) {
-                    pa[q] = q < C ? part[(kk * CL_MAXC + q) * 6 + c] : 0.f;
-                    pj[q] = q < C ? part[(kk * CL_MAXC + q) * 6 + 3 + c] : 0.f;
+                    pa[q] = q < C ? part[kk * CL_PS + q * 6 + c] : 0.f;
+                    pj[q] = q < C ? part[kk * CL_PS + q * 6 + 3 + c] : 0.f;
                 }
 #pragma unroll
                 for (int h = CL_MAXC / 2; h >= 1; h >>= 1)

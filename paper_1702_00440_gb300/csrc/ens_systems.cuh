@@ -37,6 +37,7 @@ constexpr int ES_NS = 128;          // active particles per batch (16 warps x 8 
 constexpr int ES_NO = 128;          // outbox records per CTA (later active ones are read from the j-records)
 constexpr int ES_MAXC = 16;         // largest cluster
 constexpr int ES_CLASSES = 5;       // cluster sizes 1, 2, 4, 8, 16
+constexpr int ES_PS = ES_MAXC * 6 + 4;  // floats of one batch slot's partials (padded: no bank conflicts)
 
 struct EsLayout {
     size_t jA, jB, jC, tau, dtau, xh, xl, vh, vl, af, jf, lact, oA, oB, oC, iA, iB, iC, aown, aloc, part, tp, bytes;
@@ -68,7 +69,7 @@ struct EsLayout {
         iC = take(sizeof(float2) * ES_NS);
         aown = take(sizeof(int) * ES_NS);
         aloc = take(sizeof(int) * ES_NS);
-        part = take(sizeof(float) * ES_NS * ES_MAXC * 6);
+        part = take(sizeof(float) * ES_NS * ES_PS);
         tp = take(sizeof(float) * 2 * ES_W * 6);
         bytes = o;
     }
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(ES_T, 1) k_ens_systems(EsArgs a)
     float4 *iA = (float4 *)(smem + L.iA), *iB = (float4 *)(smem + L.iB);  // the batch's records
     float2 *iC = (float2 *)(smem + L.iC);
     int *aown = (int *)(smem + L.aown), *aloc = (int *)(smem + L.aloc);   // the batch's owners
-    float *part = (float *)(smem + L.part);  // [batch slot][rank][6]
+    float *part = (float *)(smem + L.part);  // [batch slot][rank][6], slot stride ES_PS
     float *tp = (float *)(smem + L.tp);      // [active][segment][6]
     // inboxes the other CTAs write before a cluster barrier
     __shared__ int s_cnt_in[ES_MAXC];
@@ -318,7 +319,7 @@ __global__ void __launch_bounds__(ES_T, 1) k_ens_systems(EsArgs a)
                     const int k = lane < 6 ? k0 : k1, c = lane < 6 ? lane : lane - 6;
                     if (store) {
                         if (Sw == 1)
-                            cl.map_shared_rank(part, aown[k])[(k * ES_MAXC + r) * 6 + c] = mine_c;
+                            cl.map_shared_rank(part, aown[k])[k * ES_PS + r * 6 + c] = mine_c;
                         else
                             tp[((k << lgS) + sg) * 6 + c] = mine_c;
                     }
@@ -336,7 +337,7 @@ __global__ void __launch_bounds__(ES_T, 1) k_ens_systems(EsArgs a)
                     __syncthreads();
                     for (int w = t; w < nb * 6; w += ES_T) {
                         const int k = w / 6, c = w % 6;
-                        cl.map_shared_rank(part, aown[k])[(k * ES_MAXC + r) * 6 + c] = tp[((k << lgS) * 6) + c];
+                        cl.map_shared_rank(part, aown[k])[k * ES_PS + r * 6 + c] = tp[((k << lgS) * 6) + c];
                     }
                 }
                 cl.sync();  // B2: every partial of the batch has reached its owner
@@ -356,8 +357,8 @@ __global__ void __launch_bounds__(ES_T, 1) k_ens_systems(EsArgs a)
                         float pa[ES_MAXC], pj[ES_MAXC];
 #pragma unroll
                         for (int o = 0; o < ES_MAXC; o++) {
-                            pa[o] = o < C ? part[(kb * ES_MAXC + o) * 6 + c] : 0.f;
-                            pj[o] = o < C ? part[(kb * ES_MAXC + o) * 6 + 3 + c] : 0.f;
+                            pa[o] = o < C ? part[kb * ES_PS + o * 6 + c] : 0.f;
+                            pj[o] = o < C ? part[kb * ES_PS + o * 6 + 3 + c] : 0.f;
                         }
 #pragma unroll
                         for (int h = ES_MAXC / 2; h >= 1; h >>= 1)
