@@ -336,11 +336,11 @@ int gd_ens_init(gd_ens **out, int32_t nclusters, const int64_t *n_per, const dou
 
 /* Advance every cluster until no particle's next time is <= t_end.  With
  * opts.cluster = 1 (the default), opts.fused = 0 and every cluster small enough
- * (at most 16 x 1024 particles), each cluster is integrated on its own, without a
- * global block time: one launch whose thread-block clusters (the fewest CTAs of
- * 1024 particles that hold the largest cluster, up to 16) take whole clusters from
- * a work queue, largest first, and run all of a cluster's block steps in shared
- * memory; the same schedule and arithmetic per particle as the global steps, force
+ * (at most 16 x 1280 particles), each cluster is integrated on its own, without a
+ * global block time: one launch per size class of thread-block clusters (the
+ * fewest CTAs of up to 1280 particles that hold a cluster: 1, 2, 4, 8 or 16), whose
+ * thread-block clusters take whole clusters from the class's work queue, largest
+ * first, and run all of a cluster's block steps in shared memory; the same schedule and arithmetic per particle as the global steps, force
  * sums split over those CTAs.  Otherwise global block steps, as above. */
 int gd_ens_evolve(gd_ens *s, double t_end);
 

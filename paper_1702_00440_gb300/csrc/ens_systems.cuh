@@ -31,10 +31,11 @@ namespace cgx = cooperative_groups;
 
 constexpr int ES_T = 512;           // threads per CTA
 constexpr int ES_W = ES_T / 32;
-constexpr int ES_ROUNDS = 2;        // particles per thread at most
-constexpr int ES_P = ES_ROUNDS * ES_T;  // particles per CTA at most
-constexpr int ES_NS = 128;          // active particles per batch (16 warps x 8 in the correction)
-constexpr int ES_NO = 128;          // outbox records per CTA (later active ones are read from the j-records)
+constexpr int ES_ROUNDS = 3;        // particles per thread at most
+constexpr int ES_P = 1280;          // particles per CTA at most (fuller CTAs measured faster)
+constexpr int ES_NS = 96;           // active particles per batch (at most 16 warps x 8 in the correction)
+constexpr int ES_NO = 96;           // outbox records per CTA (later active ones are read from the j-records)
+static_assert(ES_P <= ES_ROUNDS * ES_T && ES_NS <= 16 * 8, "capacities");
 constexpr int ES_MAXC = 16;         // largest cluster
 constexpr int ES_CLASSES = 5;       // cluster sizes 1, 2, 4, 8, 16
 constexpr int ES_PS = ES_MAXC * 6 + 4;  // floats of one batch slot's partials (padded: no bank conflicts)
@@ -210,18 +211,26 @@ __global__ void __launch_bounds__(ES_T, 1) k_ens_systems(EsArgs a)
                 if (lane == 0) s_wc[rd * ES_W + warp] = __popc(bal[rd]);
             }
             __syncthreads();
-            if (warp == 0) {  // exclusive scan of the (round, warp) counts
-                static_assert(ES_ROUNDS * ES_W <= 32, "one count per lane");
-                const int c0 = lane < ES_ROUNDS * ES_W ? s_wc[lane] : 0;
+            if (warp == 0) {  // exclusive scan of the (round, warp) counts: entries 0-31, then 32-47
+                static_assert(ES_ROUNDS * ES_W <= 64, "two counts per lane");
+                const int c0 = s_wc[lane], c1 = lane + 32 < ES_ROUNDS * ES_W ? s_wc[lane + 32] : 0;
                 int e0 = c0;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
                     const int y = __shfl_up_sync(0xffffffffu, e0, o);
                     if (lane >= o) e0 += y;
                 }
+                const int tot0 = __shfl_sync(0xffffffffu, e0, 31);
+                int e1 = c1;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, e1, o);
+                    if (lane >= o) e1 += y;
+                }
                 __syncwarp();
-                if (lane < ES_ROUNDS * ES_W) s_wc[lane] = e0 - c0;
-                if (lane == 31) s_base = e0;
+                s_wc[lane] = e0 - c0;
+                if (lane + 32 < ES_ROUNDS * ES_W) s_wc[lane + 32] = tot0 + e1 - c1;
+                if (lane == 31) s_base = tot0 + e1;
             }
             __syncthreads();
 #pragma unroll

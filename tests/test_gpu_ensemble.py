@@ -169,9 +169,9 @@ def test_independent_systems_then_global_steps():
 
 
 def test_independent_systems_with_a_sixteen_cta_cluster():
-    """A cluster of 9000 particles needs the 16-CTA class (more than 8 x 1024), a
+    """A cluster of 11000 particles needs the 16-CTA class (more than 8 x 1280), a
     small one the 1-CTA class: both against the global two-kernel path."""
-    sizes = [9000, 500]
+    sizes = [11000, 500]
     ms, xs, vs = _clusters(sizes, seed0=700)
     out = []
     for opts in (dict(), dict(cluster=False)):
@@ -189,10 +189,10 @@ def test_independent_systems_with_a_sixteen_cta_cluster():
 
 
 def test_independent_systems_at_the_class_edges_and_the_size_limit():
-    """Clusters of exactly 1024, 1025 and 16384 particles (a full 1-CTA cluster, the
+    """Clusters of exactly 1280, 1281 and 20480 particles (a full 1-CTA cluster, the
     smallest 2-CTA one, a full 16-CTA one) against the global path; an ensemble with
-    a cluster above 16 x 1024 particles falls back to the global path as a whole."""
-    sizes = [1024, 1025, 16384]
+    a cluster above 16 x 1280 particles falls back to the global path as a whole."""
+    sizes = [1280, 1281, 20480]
     ms, xs, vs = _clusters(sizes, seed0=800)
     out = []
     for opts in (dict(), dict(cluster=False)):
@@ -205,7 +205,7 @@ def test_independent_systems_at_the_class_edges_and_the_size_limit():
     assert np.mean(a["dtau"] == b["dtau"]) > 0.99
     assert np.abs(a["x"] - b["x"]).max() < 1e-6
     assert abs(sa["particle_steps"] - sb["particle_steps"]) <= 0.01 * sb["particle_steps"]
-    sizes = [17000, 100]
+    sizes = [21000, 100]
     ms, xs, vs = _clusters(sizes, seed0=900)
     res = []
     for opts in (dict(), dict(cluster=False)):
