@@ -77,6 +77,9 @@ TRAFFIC_PER_LAUNCH = {
     # e618334d with the cluster's partial forces at a padded slot stride (shared memory
     # only: the DRAM accesses are unchanged)
     "fdc36443": {"k_cluster_steps": 1579264, "k_force_mixed": 722688},
+    # fdc36443 with host-side changes to the ensemble launches only: the captured
+    # kernels are unchanged
+    "5fc3df47": {"k_cluster_steps": 1579264, "k_force_mixed": 722688},
 }
 
 
